@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark of the PageRank hot path on GB300 (one JSON line on stdout).
+
+Workloads (synthetic, seeded; stand-ins for the paper's SuiteSparse graphs):
+
+* ``rmat22`` (default) — R-MAT scale 22 (N = 4,194,304; 67,108,864 sampled
+  edges; a/b/c/d = .57/.19/.19/.05; ids permuted; self-loops and duplicates
+  removed), alpha = 0.85, tau in {1e-6, 1e-10} x {L1, L2, Linf}: 6 instances
+  solved as one batch (one shared iterate sequence, six stopping rules).
+* ``sweep330`` — the 10k-vertex Erdos-Renyi graph, alpha 0.50..1.00 step .05
+  x tau 1e-1..1e-10 x {L1, L2, Linf} = 330 instances, max 500 iterations.
+* ``multi64`` — 64 R-MAT graphs of scale 12 + (i mod 9), edge factor 16,
+  alpha 0.85, tau 1e-10, L1, one batch.
+* ``rmat24mixed`` — R-MAT scale 24, alpha in {0.85, 0.95}, Linf, tau 1e-10,
+  FP32 phase to 1e-6 then DF64 refinement.
+
+A step is one solve of the whole workload with the graph resident in HBM
+(``value``); ``e2e`` repeats it through the public C ABI from pinned host
+arrays (graph creation, solve, ranks back to the host) every step.
+``--impl reference`` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "sweep solves/s and GTEPS (%HBM roofline), batched+warm vs plain, ≤10τ/(1−α) L1 err"
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- workloads
+
+def make_workload(name, gg):
+    """(graphs, instance specs [(graph index, alpha, tau, norm, max_iter)], precision, description)."""
+    if name == "rmat22":
+        g = gg.rmat(22, 16, seed=22)
+        specs = [(0, 0.85, t, nm, 500) for t in (1e-6, 1e-10) for nm in (1, 2, 3)]
+        return [g], specs, "df64", "rmat-s22 ef16 seed22, alpha .85, tau {1e-6,1e-10} x {L1,L2,Linf}"
+    if name == "sweep330":
+        g = gg.erdos_renyi_10k(seed=1)
+        alphas = [round(0.5 + 0.05 * i, 2) for i in range(11)]
+        specs = [(0, a, 10.0 ** -k, nm, 500) for a in alphas for k in range(1, 11) for nm in (1, 2, 3)]
+        return [g], specs, "df64", "er-10k (100k edges, 5% dangling), 11 alpha x 10 tau x 3 norms"
+    if name == "multi64":
+        gs = [gg.rmat(12 + (i % 9), 16, seed=1000 + i) for i in range(64)]
+        specs = [(i, 0.85, 1e-10, 1, 500) for i in range(64)]
+        return gs, specs, "df64", "64 rmat graphs scale 12..20 ef16, alpha .85, tau 1e-10, L1"
+    if name == "rmat24mixed":
+        g = gg.rmat(24, 16, seed=24)
+        specs = [(0, a, 1e-10, 3, 500) for a in (0.85, 0.95)]
+        return [g], specs, "mixed", "rmat-s24 ef16 seed24, alpha {.85,.95}, Linf, tau 1e-10, fp32->df64"
+    raise SystemExit(f"unknown workload {name}")
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- distributed
+
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.barrier()
+        torch.cuda.synchronize()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2108_02997_gb300 import binding as B
+    from paper_2108_02997_gb300 import graphgen as gg
+
+    torch.cuda.set_device(local)
+    B.lib()
+    graphs, specs, precision, desc = make_workload(args.workload, gg)
+    dgs = [B.Graph.from_csr(g) for g in graphs]
+    outs = [torch.empty(graphs[gi].n, dtype=torch.float64, device="cuda") for gi, *_ in specs]
+    stream = torch.cuda.current_stream()
+    sptr = int(stream.cuda_stream)
+    total_edges = sum(g.nnz for g in graphs)
+    l2_bytes = sum(4 * (g.n + 1) + 4 * g.nnz + 24 * g.n for g in graphs)
+    inputs_large = l2_bytes > 2 * 129e6
+    flush = None if inputs_large else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def insts():
+        return [B.Instance(dgs[gi], a, t, nm, mi, out=outs[k]) for k, (gi, a, t, nm, mi) in enumerate(specs)]
+
+    def step():
+        xs = insts()
+        B.pr_solve_batch(xs, precision=precision, outputs_on_device=True, stream=sptr)
+        return xs
+
+    for _ in range(args.warmup):
+        if flush is not None:
+            flush.zero_()
+        last = step()
+    torch.cuda.synchronize()
+    launches = 0
+    times = []
+    barrier(world)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            if flush is not None:
+                flush.zero_()
+            ev0.record(stream)
+            last = step()
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+            launches += B.pr_last_solve_stats()["launches"]
+        torch.cuda.synchronize()
+    barrier(world)
+    ms_step = sum(times) / len(times)
+    ms_step_max = max_over_ranks(ms_step, world)
+    solves = len(specs)
+    value = world * solves * 1000.0 / ms_step_max
+    inst_iters = [x.iters for x in last]
+    edges_inst = sum(graphs[gi].nnz * x.iters for (gi, *_), x in zip(specs, last))
+    # ---- roofline pass: the same solves with one launch per iteration, each
+    # launch bracketed by CUDA events on the launching stream
+    hbm, peak_kind = peaks()
+    k_ms, k_launches, bytes_per_launch = 0.0, 0, 0.0
+    per_graph = []
+    for gi, g in enumerate(graphs):
+        sel = [k for k, s in enumerate(specs) if s[0] == gi]
+        xs = [B.Instance(dgs[gi], specs[k][1], specs[k][2], specs[k][3], specs[k][4], out=outs[k]) for k in sel]
+        B.pr_solve_batch(xs, precision=precision, outputs_on_device=True, stream=sptr, loop="host")
+        st = B.pr_last_solve_stats()
+        n_src = int((g.outdeg > 0).sum())
+        b = 4.0 * (g.n + 1) + 4.0 * g.nnz + 8.0 * n_src + 8.0 * g.n + 8.0 * g.n + 4.0 * g.n
+        iters_launched = st["launches"] - 1 - (1 if precision == "mixed" else 0)
+        k_ms += st["kernel_ms"]
+        k_launches += iters_launched
+        bytes_per_launch += b * iters_launched
+        per_graph.append(b)
+    avg_launch_ms = k_ms / max(k_launches, 1)
+    bytes_avg = bytes_per_launch / max(k_launches, 1)
+    achieved = bytes_avg / (avg_launch_ms * 1e-3) / 1e9
+    gteps_device = total_edges * (k_launches / max(len(graphs), 1)) / (ms_step * 1e-3) / 1e9
+    # ---- e2e: graph creation from pinned host arrays + solve + ranks to host, every step
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        for g in graphs:
+            off = torch.from_numpy(g.offsets).pin_memory().numpy()
+            src = torch.from_numpy(g.sources).pin_memory().numpy()
+            od = torch.from_numpy(g.outdeg).pin_memory().numpy()
+            pinned.append((off, src, od))
+        host_outs = [torch.empty(graphs[gi].n, dtype=torch.float64).pin_memory().numpy() for gi, *_ in specs]
+        h2d = sum(a.nbytes + b.nbytes + c.nbytes for a, b, c in pinned)
+        d2h = sum(o.nbytes for o in host_outs)
+        et = []
+        for i in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hg = [B.Graph(*p) for p in pinned]
+            xs = [B.Instance(hg[gi], a, t, nm, mi, out=host_outs[k]) for k, (gi, a, t, nm, mi) in enumerate(specs)]
+            B.pr_solve_batch(xs, precision=precision, stream=sptr)
+            for h in hg:
+                h.close()
+            t1 = time.perf_counter()
+            if i >= args.warmup:
+                et.append((t1 - t0) * 1000.0)
+        e2e_ms = max_over_ranks(sum(et) / len(et), world)
+        e2e = {"value": world * solves * 1000.0 / e2e_ms, "unit": "solves/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    # ---- CPU baseline: the oracle on the host cores, bounded sample
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(graphs, specs, inst_iters, args.cpu_seconds)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"df64": "df64 (f32x2)", "mixed": "f32 -> df64", "fp64": "f64", "fp32": "f32"}[precision],
+        "data": "synthetic (seeded generators; paper's SuiteSparse graphs unavailable)",
+        "config": {"workload": desc, "instances": solves, "graphs": len(graphs),
+                   "edges": total_edges, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2" if inputs_large else "L2 flushed (256 MB write) between steps"},
+        "iterations": inst_iters,
+        "gteps_instances": edges_inst / (ms_step * 1e-3) / 1e9,
+        "gteps_device": gteps_device,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "pr_iter_kernel", "avg_launch_us": avg_launch_ms * 1e3,
+                     "algorithmic_bytes_per_launch": bytes_avg, "peak_source": peak_kind},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    for d in dgs:
+        d.close()
+
+
+def oracle_sample(graphs, specs, budget_s, cores):
+    """Time the CPU oracle on the workload within about budget_s seconds.
+
+    Instances sharing (graph, alpha) are one trajectory read at several stopping
+    rules (oracle.pagerank_taps). Trajectories are solved in workload order for
+    real while the estimated cost fits the budget; the rest are costed as
+    (iterations) x (measured time of one oracle update on that graph), with
+    iterations from the first solved trajectory of the same graph when there
+    is one, else Section 1's estimate round(log10 tau / log10 alpha)."""
+    import numpy as np
+
+    from oracle import oracle as orc
+    t_upd = {}
+    for gi, g in enumerate(graphs):
+        r = np.full(g.n, 1.0 / g.n)
+        t0 = time.perf_counter()
+        r, _ = orc.step(g, 0.85, r, threads=cores)
+        orc.norms(r, r)
+        t_upd[gi] = time.perf_counter() - t0
+    groups = {}
+    for k, (gi, a, t, nm, mi) in enumerate(specs):
+        groups.setdefault((gi, a), []).append(k)
+    spent, solved, modeled = 0.0, 0, 0.0
+    iters_seen = {}
+    for (gi, a), ks in groups.items():
+        taps = [(specs[k][2], specs[k][3], specs[k][4]) for k in ks]
+        est = max(min(mi, orc.estimate_iterations(t, a) if 0 < a < 1 else mi) for t, nm, mi in taps)
+        if spent + t_upd[gi] * est <= budget_s:
+            t0 = time.perf_counter()
+            res = orc.pagerank_taps(graphs[gi], a, taps, threads=cores)
+            spent += time.perf_counter() - t0
+            solved += len(ks)
+            iters_seen[(gi, a)] = [x.iters for x in res]
+        else:
+            for t, nm, mi in taps:
+                it = min(mi, orc.estimate_iterations(t, a)) if 0 < a < 1 else mi
+                modeled += t_upd[gi] * max(it, 1)
+    total_time = spent + modeled
+    value = len(specs) / total_time
+    kind = "measured" if modeled == 0 else ("mixed" if solved else "extrapolated")
+    sample = (f"{solved} of {len(specs)} instances solved by the oracle ({spent:.1f}s); "
+              f"{len(specs) - solved} costed as estimated iterations x measured update time ({kind})")
+    return {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+
+def cpu_baseline(graphs, specs, inst_iters, seconds):
+    from oracle import oracle as orc
+    return oracle_sample(graphs, specs, seconds, orc.default_threads())
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args, world, rank):
+    """The oracle, as it stands, on the host cores; rank 0 only."""
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_2108_02997_gb300 import graphgen as gg
+    orc.build()
+    graphs, specs, precision, desc = make_workload(args.workload, gg)
+    cores = orc.default_threads()
+    budget = max(5.0, args.cpu_seconds)
+    for _ in range(args.warmup):
+        oracle_sample(graphs, specs[:1], 1.0, cores)
+    vals = [oracle_sample(graphs, specs, budget, cores) for _ in range(args.steps)]
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": len(specs) / v * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "instances": len(specs), "graphs": len(graphs)},
+            "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v, "unit": "solves/s",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "sweep330", "multi64", "rmat24mixed"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        return
+    world, rank, local = dist_init(args.gpus)
+    run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * pagerank.h — C ABI of libpagerank.so: pull power-iteration PageRank with
+ * L1 / L2 / Linf convergence checks on one NVIDIA GB300 (sm_103a).
+ *
+ * The method (paper "Adjusting PageRank parameters and Comparing results"):
+ *   r^0       = 1/N (or a given start)
+ *   c0        = (1 - alpha)/N + alpha * (sum of r over dangling vertices)/N   (Section 2)
+ *   r^i[v]    = c0 + alpha * sum_{u -> v} r^{i-1}[u] / outdeg(u)             (Section 2)
+ *   err       = ||r^i - r^{i-1}||, L1 = sum|.|, L2 = sqrt(sum|.|^2),
+ *               Linf = max|.|                                                 (Section 3)
+ *   stop when err < tau (converged) or after max_iter updates (not converged;
+ *   the paper caps at 500, Section 2, and halts there, Section 4).
+ * The iteration count returned is the number of updates performed, including
+ * the one whose error passed the test.
+ *
+ * Conventions for every entry point:
+ *   - Return PR_OK (0) or an error code; on error pr_last_error() gives a
+ *     message (thread-local, valid until the next call on that thread) and no
+ *     caller-owned output buffer has been written.
+ *   - Non-convergence is not an error: PR_OK with converged = 0 and
+ *     iterations = max_iter.
+ *   - Host pointers are plain CPU memory. Device pointers are CUDA global
+ *     memory of the current device. Which one an argument is, is stated per
+ *     argument.
+ *   - The library allocates device memory with cudaMalloc and releases it
+ *     before returning (solves) or in pr_graph_destroy (graphs).
+ *   - A graph handle may be used by one solve at a time.
+ *   - Calls are synchronous with respect to the host unless stated otherwise;
+ *     device work is issued on the stream given in pr_options (NULL: the
+ *     legacy default stream).
+ */
+#ifndef PAGERANK_H
+#define PAGERANK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pr_graph pr_graph;   /* opaque device-resident graph */
+
+typedef enum pr_status {
+    PR_OK = 0,
+    PR_EINVAL = 1,    /* invalid argument or malformed graph */
+    PR_ENOMEM = 2,    /* host or device allocation failed */
+    PR_ECUDA = 3,     /* a CUDA runtime call failed */
+    PR_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+    PR_ESTATE = 5,    /* handle in the wrong state (e.g. destroyed) */
+    PR_ENOTSUP = 6    /* option combination not supported */
+} pr_status;
+
+/* Convergence norms of Section 3. */
+typedef enum pr_norm { PR_NORM_L1 = 1, PR_NORM_L2 = 2, PR_NORM_LINF = 3 } pr_norm;
+
+/* Arithmetic of the device iteration.
+ *  PR_PREC_DF64 : ranks and contributions stored as float pairs (hi + lo,
+ *                 about 48 significant bits); every per-edge and per-vertex
+ *                 operation runs on the FP32 pipes; block/grid reductions,
+ *                 c0 and the norms finish in FP64. Default: GB300 executes
+ *                 FP64 at about 1/69 of its FP32 rate, so this is the
+ *                 FP64-class path that stays memory-bound.
+ *  PR_PREC_FP64 : native IEEE double everywhere (FP64-pipe bound on GB300).
+ *  PR_PREC_MIXED: FP32 ranks, gathers and accumulation until the norm is at
+ *                 or below switch_tol, then DF64 refinement to tau. The
+ *                 dangling sum, c0 and the norms stay FP64-class throughout.
+ *  PR_PREC_FP32 : FP32 ranks/gathers/accumulation throughout (norms FP64-class).
+ */
+typedef enum pr_precision {
+    PR_PREC_DF64 = 0,
+    PR_PREC_FP64 = 1,
+    PR_PREC_MIXED = 2,
+    PR_PREC_FP32 = 3
+} pr_precision;
+
+/* Start vector r^0. */
+typedef enum pr_init {
+    PR_INIT_UNIFORM = 0,  /* 1/N everywhere */
+    PR_INIT_USER = 1,     /* caller's vector, used as given (not renormalised) */
+    PR_INIT_LEARNED = 2   /* MLP warm start (pr_mlp), renormalised to sum 1 */
+} pr_init;
+
+/* Device-side loop control. */
+typedef enum pr_loop {
+    PR_LOOP_GRAPH = 0,    /* default: one CUDA graph whose while-node repeats the
+                             iteration kernel until every instance has stopped;
+                             the stop decision is taken on the device */
+    PR_LOOP_HOST = 1      /* one launch per iteration and a device-to-host read
+                             of the stop flag after each (the plain per-instance
+                             baseline; also used to time single launches) */
+} pr_loop;
+
+typedef struct pr_mlp pr_mlp;   /* learned warm start, see pr_mlp_* below */
+
+typedef struct pr_options {
+    int32_t precision;          /* pr_precision; default PR_PREC_DF64 */
+    int32_t init;               /* pr_init; default PR_INIT_UNIFORM */
+    const double *init_vec;     /* PR_INIT_USER: n doubles in the caller's vertex
+                                   order (host, or device if init_on_device) */
+    int32_t init_on_device;     /* 1: init_vec is a device pointer */
+    int32_t outputs_on_device;  /* 1: every ranks_out is a device pointer */
+    double switch_tol;          /* PR_PREC_MIXED: FP32 phase ends when err <= this;
+                                   default 1e-6 */
+    void *stream;               /* cudaStream_t, or NULL for the default stream */
+    int32_t share_trajectories; /* pr_solve_batch: 1 (default) lets instances that
+                                   share (graph, alpha, start, precision) read their
+                                   answers off one iterate sequence; 0 gives every
+                                   instance its own column */
+    int32_t loop;               /* pr_loop; default PR_LOOP_GRAPH */
+    const pr_mlp *mlp;          /* PR_INIT_LEARNED: trained network */
+    double *err_history;        /* pr_solve only, optional host buffer of
+                                   3*max_iter doubles: row i-1 = (L1, L2, Linf)
+                                   of r^i - r^{i-1} */
+    int32_t reserved[8];        /* zero */
+} pr_options;
+
+/* Fill *opt with the defaults listed above. */
+void pr_options_default(pr_options *opt);
+
+/*
+ * Create a device-resident graph from an in-edge CSR (Section 2: the pull
+ * update reads, for each vertex v, its in-neighbours u and their out-degrees).
+ *   n           : vertices, 1 <= n < 2^31
+ *   nnz         : edges, 0 <= nnz < 2^31
+ *   in_offsets  : host, n+1 int32, in_offsets[0] = 0, non-decreasing,
+ *                 in_offsets[n] = nnz
+ *   in_sources  : host, nnz int32 in [0, n): the tails u of the edges u -> v,
+ *                 row v at in_offsets[v] .. in_offsets[v+1]-1 (NULL if nnz = 0)
+ *   out_degree  : host, n int32 >= 0; must equal the number of times each
+ *                 vertex occurs in in_sources (vertices with 0 are dangling)
+ *   out         : receives the handle
+ * The library copies the arrays; the caller keeps ownership. The device copy
+ * is relabelled by in-degree (hubs first) for load balance and gather
+ * locality; every rank vector crossing the ABI is in the caller's order.
+ * Errors: PR_EINVAL for a malformed CSR, PR_ENOMEM, PR_ECUDA.
+ */
+pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_offsets,
+                          const int32_t *in_sources, const int32_t *out_degree,
+                          pr_graph **out);
+
+/* Release a graph and its device memory. NULL is accepted. */
+pr_status pr_graph_destroy(pr_graph *g);
+
+/* Vertex, edge and dangling-vertex counts of a graph (any pointer may be NULL). */
+pr_status pr_graph_info(const pr_graph *g, int32_t *n, int64_t *nnz, int32_t *n_dangling);
+
+/*
+ * Solve one instance (Sections 2-4).
+ *   alpha     : damping factor in [0, 1] (1 allowed: the paper sweeps to 1.00)
+ *   tol       : tau > 0, finite
+ *   norm      : pr_norm
+ *   max_iter  : >= 1
+ *   opt       : NULL for defaults
+ *   ranks_out : n doubles, caller order (host, or device if
+ *               opt->outputs_on_device); the iterate at the stopping iteration
+ *   iters_out, err_out, converged_out : host, may be NULL
+ */
+pr_status pr_solve(const pr_graph *g, double alpha, double tol, int32_t norm, int32_t max_iter,
+                   const pr_options *opt, double *ranks_out, int32_t *iters_out, double *err_out,
+                   int32_t *converged_out);
+
+/* One instance of a batch. Inputs: g .. init_vec. Outputs: iters .. status. */
+typedef struct pr_instance {
+    const pr_graph *g;
+    double alpha;
+    double tol;
+    int32_t norm;
+    int32_t max_iter;
+    double *ranks_out;          /* n doubles (host, or device if outputs_on_device) */
+    const double *init_vec;     /* PR_INIT_USER: this instance's start (NULL: opt->init_vec) */
+    int32_t iters;
+    int32_t converged;
+    double err;                 /* the chosen norm at the stopping iteration */
+    double err_l1;              /* the L1 norm of the same step (error bound:
+                                   ||r - r*||_1 <= alpha/(1-alpha) * err_l1) */
+    int32_t status;             /* pr_status of this instance */
+    int32_t reserved;
+} pr_instance;
+
+/*
+ * Solve many (graph, alpha, tau, norm, max_iter) instances together: the
+ * alpha sweep of Section 2, the norm comparison of Section 3 and the tau sweep
+ * of Section 4 as one batched device loop. Instances on the same graph become
+ * columns of an N x k vertex-major rank matrix so that one index read serves
+ * k gathers; different graphs run side by side in the same launches. Every
+ * column stops and is retired on its own. Returns the first failing
+ * instance's status (others are still filled in).
+ */
+pr_status pr_solve_batch(pr_instance *inst, int32_t count, const pr_options *opt);
+
+/*
+ * Learned warm start (no counterpart in the paper). A 5-64-64-1 MLP with
+ * GELU activations on per-vertex features
+ *   [log(1+indeg), log(1+outdeg), mean and max of log(1+outdeg(u)) over
+ *    in-neighbours u, alpha]
+ * predicts log(N * r); the start is exp(prediction) renormalised to sum 1.
+ * Weights are held in FP32 (master) and BF16 (inference/training operands).
+ * params layout (host, 4673 floats): W1[64][5], b1[64], W2[64][64], b2[64],
+ * W3[1][64], b3[1].
+ */
+pr_status pr_mlp_create(const float *params, pr_mlp **out);
+pr_status pr_mlp_destroy(pr_mlp *m);
+pr_status pr_mlp_get_params(const pr_mlp *m, float *params_out);
+
+/* Features (n x 5 floats, caller order, device pointer) of graph g at alpha. */
+pr_status pr_features(const pr_graph *g, double alpha, float *d_feat_out, void *stream);
+
+/* Warm-start vector (n doubles, caller order; device pointer) for (g, alpha). */
+pr_status pr_mlp_warm_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_r0_out,
+                            void *stream);
+
+/*
+ * Train the MLP on the device with the library's own forward, backward and
+ * Adam kernels: minimise mean((y - log(N r*))^2) over all vertices of the
+ * given (graph, alpha, target) sets. targets[i] is a device pointer to n_i
+ * doubles r* in caller order. Runs `epochs` full-batch steps per set,
+ * round-robin, with learning rate lr. loss_out (host, may be NULL) receives
+ * the last epoch's mean loss over the sets.
+ */
+pr_status pr_mlp_train(pr_mlp *m, const pr_graph *const *graphs, const double *alphas,
+                       const double *const *targets, int32_t nsets, int32_t epochs, float lr,
+                       float *loss_out, void *stream);
+
+/*
+ * Counters of the last solve on any thread (host pointers, each may be NULL):
+ *   launches  : iteration-kernel launches (init passes included)
+ *   passes    : iteration passes executed on the device
+ *   kernel_ms : PR_LOOP_HOST only: sum over iteration launches of the CUDA-event
+ *               time between the events recorded just before and just after
+ *               each launch on the solve's stream; 0 for PR_LOOP_GRAPH
+ *   total_ms  : CUDA-event time of the whole device loop (all phases)
+ */
+pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms);
+
+/* Message for the last error on this thread ("" if none). */
+const char *pr_last_error(void);
+
+/* Static name of a status code. */
+const char *pr_status_string(pr_status s);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int32_t pr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAGERANK_H */

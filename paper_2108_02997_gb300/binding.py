@@ -1,0 +1,292 @@
+"""Python binding of ``libpagerank.so`` (argument marshalling only).
+
+Every function here forwards to the C ABI declared in ``include/pagerank.h``
+under the same name; all PageRank arithmetic runs in the library's CUDA
+kernels. There is no CPU fallback: if the library cannot be loaded, or no
+CUDA device is present, calls raise.
+
+Low level: ``lib()`` returns the ``ctypes.CDLL`` with typed entry points and
+the ``pr_options`` / ``pr_instance`` structures.
+
+High level: :class:`Graph` owns a ``pr_graph`` handle; :func:`pr_solve` and
+:func:`pr_solve_batch` accept numpy arrays (host buffers) or torch CUDA tensors
+(device buffers).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _build
+
+PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT, PR_ESTATE, PR_ENOTSUP = range(7)
+PR_NORM_L1, PR_NORM_L2, PR_NORM_LINF = 1, 2, 3
+PR_PREC_DF64, PR_PREC_FP64, PR_PREC_MIXED, PR_PREC_FP32 = 0, 1, 2, 3
+PR_INIT_UNIFORM, PR_INIT_USER, PR_INIT_LEARNED = 0, 1, 2
+PR_LOOP_GRAPH, PR_LOOP_HOST = 0, 1
+PRECISIONS = {"df64": PR_PREC_DF64, "fp64": PR_PREC_FP64, "mixed": PR_PREC_MIXED, "fp32": PR_PREC_FP32}
+NORMS = {"L1": 1, "L2": 2, "Linf": 3, 1: 1, 2: 2, 3: 3}
+MLP_PARAMS = 64 * 5 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+class pr_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("init", C.c_int32), ("init_vec", C.c_void_p),
+                ("init_on_device", C.c_int32), ("outputs_on_device", C.c_int32),
+                ("switch_tol", C.c_double), ("stream", C.c_void_p),
+                ("share_trajectories", C.c_int32), ("loop", C.c_int32), ("mlp", C.c_void_p),
+                ("err_history", C.c_void_p), ("reserved", C.c_int32 * 8)]
+
+
+class pr_instance(C.Structure):
+    _fields_ = [("g", C.c_void_p), ("alpha", C.c_double), ("tol", C.c_double), ("norm", C.c_int32),
+                ("max_iter", C.c_int32), ("ranks_out", C.c_void_p), ("init_vec", C.c_void_p),
+                ("iters", C.c_int32), ("converged", C.c_int32), ("err", C.c_double),
+                ("err_l1", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
+class PageRankError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({_STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+_STATUS = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOMEM", 3: "PR_ECUDA", 4: "PR_ETIMEOUT", 5: "PR_ESTATE",
+           6: "PR_ENOTSUP"}
+
+# Exported symbols and their (argtypes, restype); mirrors include/pagerank.h.
+_vp, _i32, _i64, _d, _f = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_float
+SIGNATURES = {
+    "pr_options_default": ([_vp], None),
+    "pr_graph_create": ([_i32, _i64, _vp, _vp, _vp, C.POINTER(_vp)], _i32),
+    "pr_graph_destroy": ([_vp], _i32),
+    "pr_graph_info": ([_vp, _vp, _vp, _vp], _i32),
+    "pr_solve": ([_vp, _d, _d, _i32, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
+    "pr_solve_batch": ([_vp, _i32, _vp], _i32),
+    "pr_mlp_create": ([_vp, C.POINTER(_vp)], _i32),
+    "pr_mlp_destroy": ([_vp], _i32),
+    "pr_mlp_get_params": ([_vp, _vp], _i32),
+    "pr_features": ([_vp, _d, _vp, _vp], _i32),
+    "pr_mlp_warm_start": ([_vp, _vp, _d, _vp, _vp], _i32),
+    "pr_mlp_train": ([_vp, _vp, _vp, _vp, _i32, _i32, _f, _vp, _vp], _i32),
+    "pr_last_solve_stats": ([_vp, _vp, _vp, _vp], _i32),
+    "pr_last_error": ([], C.c_char_p),
+    "pr_status_string": ([_i32], C.c_char_p),
+    "pr_version": ([], _i32),
+}
+
+_lib = None
+
+
+def lib(build: bool = True) -> C.CDLL:
+    """Load (building first if needed) libpagerank.so with typed entry points."""
+    global _lib
+    if _lib is None:
+        so = _build.build_pagerank() if build else _build.PAGERANK_SO
+        if not so.exists():
+            raise RuntimeError(f"{so} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(str(so))
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != PR_OK:
+        raise PageRankError(st, where, lib().pr_last_error().decode())
+
+
+def default_options(**kw) -> pr_options:
+    o = pr_options()
+    lib().pr_options_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def current_stream_ptr() -> int:
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr_of(buf):
+    """(address, on_device) of a numpy array or torch tensor."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous:
+            raise ValueError("buffers must be contiguous")
+        return buf.ctypes.data, False
+    import torch
+    if isinstance(buf, torch.Tensor):
+        if not buf.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return buf.data_ptr(), buf.is_cuda
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+class Graph:
+    """A ``pr_graph`` handle built from an in-edge CSR (host arrays)."""
+
+    def __init__(self, offsets, sources, outdeg):
+        off = np.ascontiguousarray(offsets, dtype=np.int32)
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        od = np.ascontiguousarray(outdeg, dtype=np.int32)
+        h = C.c_void_p()
+        st = lib().pr_graph_create(od.shape[0], src.shape[0], off.ctypes.data,
+                                   src.ctypes.data if src.size else None, od.ctypes.data, C.byref(h))
+        _check(st, "pr_graph_create")
+        self.handle = h
+        self.n = int(od.shape[0])
+        self.nnz = int(src.shape[0])
+
+    @classmethod
+    def from_csr(cls, g) -> "Graph":
+        return cls(g.offsets, g.sources, g.outdeg)
+
+    def info(self):
+        n, nnz, nd = C.c_int32(), C.c_int64(), C.c_int32()
+        _check(lib().pr_graph_info(self.handle, C.byref(n), C.byref(nnz), C.byref(nd)), "pr_graph_info")
+        return n.value, nnz.value, nd.value
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().pr_graph_destroy(self.handle), "pr_graph_destroy")
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+@dataclass
+class SolveResult:
+    ranks: object
+    iters: int
+    err: float
+    converged: bool
+    err_history: np.ndarray | None = None
+
+
+def _make_options(precision="df64", init=None, loop="graph", stream=None, share=True, switch_tol=1e-6,
+                  outputs_on_device=False, mlp=None):
+    o = default_options()
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.loop = PR_LOOP_HOST if loop == "host" else PR_LOOP_GRAPH
+    o.share_trajectories = 1 if share else 0
+    o.switch_tol = switch_tol
+    o.outputs_on_device = 1 if outputs_on_device else 0
+    o.stream = stream
+    keep = []
+    if init is not None and not (isinstance(init, str)):
+        addr, dev = _ptr_of(init)
+        o.init = PR_INIT_USER
+        o.init_vec = addr
+        o.init_on_device = 1 if dev else 0
+        keep.append(init)
+    elif init == "learned":
+        o.init = PR_INIT_LEARNED
+        o.mlp = mlp.handle if mlp is not None else None
+    return o, keep
+
+
+def pr_solve(g: Graph, alpha: float, tol: float, norm=PR_NORM_L1, max_iter: int = 500, *,
+             precision="df64", init=None, out=None, loop="graph", stream=None, history=False,
+             switch_tol=1e-6, mlp=None) -> SolveResult:
+    """Solve one instance. ``out``: numpy array (host) or torch CUDA tensor
+    (device) of n float64; allocated as numpy when omitted."""
+    if out is None:
+        out = np.empty(g.n, np.float64)
+    addr, dev = _ptr_of(out)
+    if stream is None and dev:
+        stream = current_stream_ptr()
+    o, keep = _make_options(precision, init, loop, stream, True, switch_tol, dev, mlp)
+    hist = np.zeros((max_iter, 3), np.float64) if history else None
+    if hist is not None:
+        o.err_history = hist.ctypes.data
+    it, err, conv = C.c_int32(), C.c_double(), C.c_int32()
+    st = lib().pr_solve(g.handle, float(alpha), float(tol), int(NORMS[norm]), int(max_iter), C.byref(o),
+                        addr, C.byref(it), C.byref(err), C.byref(conv))
+    _check(st, "pr_solve")
+    del keep
+    return SolveResult(out, it.value, err.value, bool(conv.value),
+                       hist[: it.value] if hist is not None else None)
+
+
+@dataclass
+class Instance:
+    graph: Graph
+    alpha: float
+    tol: float
+    norm: int = PR_NORM_L1
+    max_iter: int = 500
+    out: object = None
+    init: object = None
+    iters: int = 0
+    err: float = 0.0
+    err_l1: float = 0.0
+    converged: bool = False
+    status: int = 0
+
+
+def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=None, share=True,
+                   switch_tol=1e-6, outputs_on_device=False, mlp=None, check=True):
+    """Solve many instances together. Fills ``out`` (allocated as numpy, or as
+    torch CUDA tensors when ``outputs_on_device``), ``iters``, ``err``,
+    ``converged`` and ``status`` of every :class:`Instance`; returns the
+    library status."""
+    arr = (pr_instance * max(len(insts), 1))()
+    keep = []
+    any_dev = outputs_on_device
+    for i, x in enumerate(insts):
+        if x.out is None:
+            if outputs_on_device:
+                import torch
+                x.out = torch.empty(x.graph.n, dtype=torch.float64, device="cuda")
+            else:
+                x.out = np.empty(x.graph.n, np.float64)
+        addr, dev = _ptr_of(x.out)
+        if dev != bool(outputs_on_device):
+            raise ValueError("every out must live on the device iff outputs_on_device")
+        a = arr[i]
+        a.g = x.graph.handle
+        a.alpha = float(x.alpha)
+        a.tol = float(x.tol)
+        a.norm = int(NORMS[x.norm])
+        a.max_iter = int(x.max_iter)
+        a.ranks_out = addr
+        if x.init is not None:
+            ia, _ = _ptr_of(x.init)
+            a.init_vec = ia
+            keep.append(x.init)
+    if stream is None and any_dev:
+        stream = current_stream_ptr()
+    o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, outputs_on_device, mlp)
+    if any(x.init is not None for x in insts) and o.init == PR_INIT_UNIFORM:
+        o.init = PR_INIT_USER
+    st = lib().pr_solve_batch(arr, len(insts), C.byref(o))
+    for i, x in enumerate(insts):
+        x.iters = arr[i].iters
+        x.err = arr[i].err
+        x.err_l1 = arr[i].err_l1
+        x.converged = bool(arr[i].converged)
+        x.status = arr[i].status
+    if check:
+        _check(st, "pr_solve_batch")
+    return st
+
+
+def pr_last_solve_stats():
+    la, pa, km, tm = C.c_int32(), C.c_int32(), C.c_double(), C.c_double()
+    lib().pr_last_solve_stats(C.byref(la), C.byref(pa), C.byref(km), C.byref(tm))
+    return {"launches": la.value, "passes": pa.value, "kernel_ms": km.value, "total_ms": tm.value}

@@ -1,0 +1,258 @@
+// pr_api.cu — C-ABI entry points: argument checks, batching, error reporting.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <set>
+#include <tuple>
+
+#include "pr_internal.cuh"
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local std::string t_last_error;
+std::mutex g_reg_mu;
+std::set<const void *> g_registry;
+}  // namespace
+
+void pr_set_error(const std::string &msg) { t_last_error = msg; }
+void pr_clear_error() { t_last_error.clear(); }
+pr_status pr_fail(pr_status s, const std::string &msg) {
+    t_last_error = msg;
+    return s;
+}
+pr_status pr_cuda_fail(cudaError_t e, const char *what) {
+    t_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return PR_ENOMEM;
+    }
+    return PR_ECUDA;
+}
+
+void registry_add(const void *p) {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    g_registry.insert(p);
+}
+void registry_remove(const void *p) {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    g_registry.erase(p);
+}
+bool registry_has(const void *p) {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    return g_registry.count(p) != 0;
+}
+
+extern "C" const char *pr_last_error(void) { return t_last_error.c_str(); }
+
+extern "C" const char *pr_status_string(pr_status s) {
+    switch (s) {
+        case PR_OK: return "PR_OK";
+        case PR_EINVAL: return "PR_EINVAL";
+        case PR_ENOMEM: return "PR_ENOMEM";
+        case PR_ECUDA: return "PR_ECUDA";
+        case PR_ETIMEOUT: return "PR_ETIMEOUT";
+        case PR_ESTATE: return "PR_ESTATE";
+        case PR_ENOTSUP: return "PR_ENOTSUP";
+        default: return "PR_UNKNOWN";
+    }
+}
+
+extern "C" int32_t pr_version(void) { return 10000; }
+
+extern "C" void pr_options_default(pr_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = PR_PREC_DF64;
+    opt->init = PR_INIT_UNIFORM;
+    opt->switch_tol = 1e-6;
+    opt->share_trajectories = 1;
+    opt->loop = PR_LOOP_GRAPH;
+}
+
+// Implemented in pr_learn.cu.
+pr_status pr_learned_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_out, cudaStream_t st);
+bool pr_mlp_valid(const pr_mlp *m);
+
+namespace {
+
+pr_status check_options(const pr_options &o) {
+    if (o.precision < PR_PREC_DF64 || o.precision > PR_PREC_FP32) return pr_fail(PR_EINVAL, "unknown precision");
+    if (o.init < PR_INIT_UNIFORM || o.init > PR_INIT_LEARNED) return pr_fail(PR_EINVAL, "unknown init mode");
+    if (o.loop != PR_LOOP_GRAPH && o.loop != PR_LOOP_HOST) return pr_fail(PR_EINVAL, "unknown loop mode");
+    if (o.precision == PR_PREC_MIXED && !(o.switch_tol > 0.0 && std::isfinite(o.switch_tol)))
+        return pr_fail(PR_EINVAL, "switch_tol must be positive and finite");
+    if (o.init == PR_INIT_LEARNED && !pr_mlp_valid(o.mlp)) return pr_fail(PR_EINVAL, "PR_INIT_LEARNED needs a live pr_mlp");
+    return PR_OK;
+}
+
+pr_status check_instance(const pr_instance &in) {
+    if (!pr_graph_valid(in.g)) return pr_fail(PR_ESTATE, "not a live graph handle");
+    if (!(in.alpha >= 0.0 && in.alpha <= 1.0)) return pr_fail(PR_EINVAL, "alpha must be in [0, 1]");
+    if (!(in.tol > 0.0) || !std::isfinite(in.tol)) return pr_fail(PR_EINVAL, "tol must be positive and finite");
+    if (in.norm < PR_NORM_L1 || in.norm > PR_NORM_LINF) return pr_fail(PR_EINVAL, "norm must be 1 (L1), 2 (L2) or 3 (Linf)");
+    if (in.max_iter < 1) return pr_fail(PR_EINVAL, "max_iter must be >= 1");
+    if (!in.ranks_out) return pr_fail(PR_EINVAL, "ranks_out is NULL");
+    return PR_OK;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_options *opt_in, double *hist_host,
+                                       int32_t hist_cap) {
+    pr_clear_error();
+    if (count < 0) return pr_fail(PR_EINVAL, "count must be >= 0");
+    if (count > 0 && !inst) return pr_fail(PR_EINVAL, "inst is NULL");
+    pr_options opt;
+    if (opt_in) opt = *opt_in; else pr_options_default(&opt);
+    pr_status s = check_options(opt);
+    if (s != PR_OK) return s;
+    if (count == 0) return PR_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(opt.stream);
+    pr_status first = PR_OK;
+    std::string first_msg;
+    std::vector<int> ok;
+    for (int32_t i = 0; i < count; i++) {
+        s = check_instance(inst[i]);
+        if (s == PR_OK && opt.init == PR_INIT_USER && !inst[i].init_vec && !opt.init_vec)
+            s = pr_fail(PR_EINVAL, "PR_INIT_USER needs init_vec");
+        inst[i].status = s;
+        if (s != PR_OK) {
+            if (first == PR_OK) { first = s; first_msg = pr_last_error(); }
+            continue;
+        }
+        ok.push_back(i);
+    }
+    // ---- start vectors on the device (caller order)
+    std::vector<std::unique_ptr<DevBuf>> bufs;
+    std::map<std::pair<const void *, const void *>, const double *> init_dev;   // (graph, src) -> device copy
+    std::map<std::pair<const pr_graph *, uint64_t>, const double *> learned;
+    auto start_for = [&](const pr_instance &in, const double **out) -> pr_status {
+        *out = nullptr;
+        if (opt.init == PR_INIT_UNIFORM) return PR_OK;
+        size_t bytes = (size_t)in.g->n * sizeof(double);
+        if (opt.init == PR_INIT_USER) {
+            const double *src = in.init_vec ? in.init_vec : opt.init_vec;
+            if (opt.init_on_device) { *out = src; return PR_OK; }
+            auto key = std::make_pair((const void *)in.g, (const void *)src);
+            auto it = init_dev.find(key);
+            if (it != init_dev.end()) { *out = it->second; return PR_OK; }
+            bufs.emplace_back(new DevBuf());
+            PR_CUDA(cudaMalloc(&bufs.back()->p, bytes));
+            PR_CUDA(cudaMemcpyAsync(bufs.back()->p, src, bytes, cudaMemcpyHostToDevice, st));
+            *out = (const double *)bufs.back()->p;
+            init_dev[key] = *out;
+            return PR_OK;
+        }
+        uint64_t abits;
+        std::memcpy(&abits, &in.alpha, 8);
+        auto key = std::make_pair(in.g, abits);
+        auto it = learned.find(key);
+        if (it != learned.end()) { *out = it->second; return PR_OK; }
+        bufs.emplace_back(new DevBuf());
+        PR_CUDA(cudaMalloc(&bufs.back()->p, bytes));
+        pr_status ls = pr_learned_start(opt.mlp, in.g, in.alpha, (double *)bufs.back()->p, st);
+        if (ls != PR_OK) return ls;
+        *out = (const double *)bufs.back()->p;
+        learned[key] = *out;
+        return PR_OK;
+    };
+    // ---- columns: one per shared trajectory (graph, alpha, start), or one per instance
+    SolveRequest req;
+    req.precision = opt.precision;
+    req.loop = opt.loop;
+    req.switch_tol = opt.switch_tol;
+    req.stream = st;
+    std::map<std::tuple<const pr_graph *, uint64_t, const double *>, int> col_of;
+    std::vector<std::vector<std::pair<int, int>>> col_taps;   // (instance, tap index)
+    for (int i : ok) {
+        pr_instance &in = inst[i];
+        const double *start = nullptr;
+        s = start_for(in, &start);
+        if (s != PR_OK) {
+            in.status = s;
+            if (first == PR_OK) { first = s; first_msg = pr_last_error(); }
+            continue;
+        }
+        uint64_t abits;
+        std::memcpy(&abits, &in.alpha, 8);
+        auto key = std::make_tuple(in.g, abits, start);
+        int c;
+        auto it = col_of.find(key);
+        if (opt.share_trajectories && it != col_of.end()) {
+            c = it->second;
+        } else {
+            c = (int)req.cols.size();
+            req.cols.emplace_back();
+            SolveColumn &sc = req.cols.back();
+            sc.g = in.g;
+            sc.alpha = in.alpha;
+            sc.init_dev = start;
+            if (opt.share_trajectories) col_of[key] = c;
+        }
+        SolveColumn &sc = req.cols[c];
+        Tap t{};
+        t.tau = in.tol;
+        t.norm = in.norm;
+        t.max_iter = in.max_iter;
+        t.alias_of = -1;
+        t.out = opt.outputs_on_device ? in.ranks_out : nullptr;
+        sc.taps.push_back(t);
+        sc.inst.push_back(i);
+        sc.host_dst.push_back(opt.outputs_on_device ? nullptr : in.ranks_out);
+    }
+    if (hist_host && req.cols.size() == 1) {
+        req.cols[0].hist_host = hist_host;
+        req.cols[0].hist_cap = hist_cap;
+    }
+    std::vector<std::vector<Tap>> taps;
+    s = pr_run_solve(req, taps);
+    if (s != PR_OK) {
+        std::string msg = pr_last_error();
+        for (auto &c : req.cols)
+            for (int i : c.inst) inst[i].status = s;
+        return pr_fail(s, msg);
+    }
+    for (size_t c = 0; c < req.cols.size(); c++)
+        for (size_t q = 0; q < req.cols[c].inst.size(); q++) {
+            pr_instance &in = inst[req.cols[c].inst[q]];
+            const Tap &t = taps[c][q];
+            in.iters = t.iters;
+            in.err = t.err;
+            in.err_l1 = t.err_l1;
+            in.converged = t.converged;
+            in.status = PR_OK;
+        }
+    if (first != PR_OK) return pr_fail(first, first_msg);
+    return PR_OK;
+}
+
+extern "C" pr_status pr_solve_batch(pr_instance *inst, int32_t count, const pr_options *opt) {
+    return pr_solve_batch_ex(inst, count, opt, nullptr, 0);
+}
+
+extern "C" pr_status pr_solve(const pr_graph *g, double alpha, double tol, int32_t norm, int32_t max_iter,
+                              const pr_options *opt, double *ranks_out, int32_t *iters_out, double *err_out,
+                              int32_t *converged_out) {
+    pr_instance in{};
+    in.g = g;
+    in.alpha = alpha;
+    in.tol = tol;
+    in.norm = norm;
+    in.max_iter = max_iter;
+    in.ranks_out = ranks_out;
+    in.init_vec = nullptr;
+    double *hist = opt ? opt->err_history : nullptr;
+    pr_status s = pr_solve_batch_ex(&in, 1, opt, hist, max_iter);
+    if (s != PR_OK) return s;
+    if (iters_out) *iters_out = in.iters;
+    if (err_out) *err_out = in.err;
+    if (converged_out) *converged_out = in.converged;
+    return PR_OK;
+}

@@ -1,0 +1,300 @@
+// pr_graph.cu — device-resident graph: validation, relabelling, work units.
+//
+// The pull update of Section 2 needs, for every vertex v, its in-neighbours u
+// and their out-degrees d_u. The graph arrives as an in-edge CSR in the
+// caller's vertex order. It is relabelled so that vertices are grouped by
+// in-degree class (floor(log2(indeg)), largest first) and, inside a class, by
+// out-degree class (largest first), ties kept in caller order:
+//   * rows of one class have in-degrees within a factor of two, so one lane
+//     group size fits the whole class (load balance without per-row bins);
+//   * on skewed graphs the vertices with the largest out-degree, whose
+//     contributions are gathered most often, end up packed together at the
+//     low ids, so their cache lines are shared instead of scattered.
+// Rank vectors cross the ABI in caller order; the kernels map through perm.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "pr_internal.cuh"
+
+namespace {
+
+int deg_class(int32_t d) {   // 0 for d = 0, else 1 + floor(log2 d)
+    if (d <= 0) return 0;
+    int c = 0;
+    while (d) { c++; d >>= 1; }
+    return c;
+}
+
+template <typename T>
+pr_status dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return pr_fail(PR_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+        }
+        return pr_cuda_fail(e, "cudaMalloc");
+    }
+    return PR_OK;
+}
+
+void free_tables(pr_graph *g) {
+    for (auto &t : g->tables) {
+        cudaFree(t.d_units);
+        cudaFree(t.d_slot_base);
+        t = UnitTable();
+    }
+}
+
+void free_graph(pr_graph *g) {
+    if (!g) return;
+    cudaFree(g->d_off);
+    cudaFree(g->d_src);
+    cudaFree(g->d_outdeg);
+    cudaFree(g->d_perm);
+    cudaFree(g->d_inv);
+    free_tables(g);
+    g->magic = 0;
+    delete g;
+}
+
+}  // namespace
+
+int w_index(int W) {
+    switch (W) {
+        case 1: return 0;
+        case 2: return 1;
+        case 4: return 2;
+        case 8: return 3;
+        case 16: return 4;
+        case 32: return 5;
+        default: return -1;
+    }
+}
+
+bool pr_graph_valid(const pr_graph *g) { return g && registry_has(g) && g->magic == kGraphMagic; }
+
+// Work units of width W (see Unit in pr_internal.cuh). Lanes of a group split
+// a row's in-edges into `es` interleaved slots, each slot handling all W
+// columns of an edge with W adjacent lanes; rows whose per-lane share would
+// exceed kMaxPerLane gathers are split into chunks handled by a whole CTA.
+pr_status pr_graph_units(pr_graph *g, int W, const UnitTable **out) {
+    int wi = w_index(W);
+    if (wi < 0) return pr_fail(PR_EINVAL, "unsupported column width");
+    UnitTable &t = g->tables[wi];
+    if (t.d_units) {
+        *out = &t;
+        return PR_OK;
+    }
+    constexpr int kEdgesPerLane = 4;
+    constexpr int kMaxPerLane = 16;
+    const int max_es = 32 / W;
+    const int32_t chunk = (kBlock / W) * 8;
+    std::vector<Unit> units;
+    std::vector<int32_t> slot_base;
+    int32_t n_chunk_slots = 0;
+    double work = 0.0;
+    for (const ClassRange &cr : g->classes) {
+        if (cr.end <= cr.begin) continue;
+        int es = 1;
+        while (es < max_es && es * kEdgesPerLane < cr.max_deg) es <<= 1;
+        bool long_rows = cr.max_deg > es * kMaxPerLane;
+        if (!long_rows) {
+            int gsz = es * W;
+            int glog = 0;
+            while ((1 << glog) < gsz) glog++;
+            int32_t rows_per_unit = kBlock >> glog;
+            for (int32_t r = cr.begin; r < cr.end; r += rows_per_unit) {
+                int32_t e = std::min(cr.end, r + rows_per_unit);
+                units.push_back({r, e, -1, glog});
+                work += (double)(g->h_off[e] - g->h_off[r]) * W + (double)(e - r) * W * 4.0;
+            }
+        } else {
+            for (int32_t v = cr.begin; v < cr.end; v++) {
+                int32_t e0 = g->h_off[v], e1 = g->h_off[v + 1];
+                int32_t deg = e1 - e0;
+                int32_t nch = std::max<int32_t>(1, (deg + chunk - 1) / chunk);
+                if (nch == 1) {
+                    units.push_back({v, e0, e1, -1});
+                } else {
+                    int32_t slot = (int32_t)slot_base.size();
+                    slot_base.push_back(n_chunk_slots);
+                    n_chunk_slots += nch;
+                    for (int32_t k = 0; k < nch; k++) {
+                        int32_t a = e0 + k * chunk, b = std::min(e1, a + chunk);
+                        units.push_back({v, a, b, slot});
+                    }
+                }
+                work += (double)deg * W + W * 4.0;
+            }
+        }
+    }
+    UnitTable nt;
+    nt.W = W;
+    nt.nunits = (int32_t)units.size();
+    nt.n_long = (int32_t)slot_base.size();
+    nt.n_chunk_slots = n_chunk_slots;
+    nt.work = work;
+    pr_status s = dalloc(&nt.d_units, units.size());
+    if (s != PR_OK) return s;
+    s = dalloc(&nt.d_slot_base, slot_base.size());
+    if (s != PR_OK) { cudaFree(nt.d_units); return s; }
+    if (!units.empty()) {
+        cudaError_t e = cudaMemcpy(nt.d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(nt.d_units); cudaFree(nt.d_slot_base); return pr_cuda_fail(e, "cudaMemcpy units"); }
+    }
+    if (!slot_base.empty()) {
+        cudaError_t e = cudaMemcpy(nt.d_slot_base, slot_base.data(), slot_base.size() * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(nt.d_units); cudaFree(nt.d_slot_base); return pr_cuda_fail(e, "cudaMemcpy slots"); }
+    }
+    t = nt;
+    *out = &t;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_offsets,
+                                     const int32_t *in_sources, const int32_t *out_degree, pr_graph **out) {
+    pr_clear_error();
+    if (!out) return pr_fail(PR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1) return pr_fail(PR_EINVAL, "n must be >= 1");
+    if (nnz < 0 || nnz >= (int64_t)INT32_MAX) return pr_fail(PR_EINVAL, "nnz must be in [0, 2^31-1)");
+    if (!in_offsets || !out_degree) return pr_fail(PR_EINVAL, "in_offsets and out_degree are required");
+    if (nnz > 0 && !in_sources) return pr_fail(PR_EINVAL, "in_sources is NULL but nnz > 0");
+    // ---- validate (host; O(n + nnz))
+    if (in_offsets[0] != 0) return pr_fail(PR_EINVAL, "in_offsets[0] must be 0");
+    if ((int64_t)in_offsets[n] != nnz) return pr_fail(PR_EINVAL, "in_offsets[n] must equal nnz");
+    for (int32_t v = 0; v < n; v++)
+        if (in_offsets[v + 1] < in_offsets[v]) return pr_fail(PR_EINVAL, "in_offsets is not non-decreasing at row " + std::to_string(v));
+    std::vector<int32_t> count;
+    try {
+        count.assign((size_t)n, 0);
+    } catch (const std::bad_alloc &) {
+        return pr_fail(PR_ENOMEM, "host allocation failed");
+    }
+    for (int64_t e = 0; e < nnz; e++) {
+        int32_t u = in_sources[e];
+        if (u < 0 || u >= n) return pr_fail(PR_EINVAL, "in_sources[" + std::to_string(e) + "] out of range");
+        count[u]++;
+    }
+    int32_t n_dangling = 0;
+    for (int32_t v = 0; v < n; v++) {
+        if (out_degree[v] != count[v])
+            return pr_fail(PR_EINVAL, "out_degree[" + std::to_string(v) + "] does not match the edges in in_sources");
+        if (out_degree[v] == 0) n_dangling++;
+    }
+    // ---- relabel: stable counting sort by (in-class desc, out-class desc)
+    std::vector<int32_t> perm, inv, new_off, new_src, new_od, tmp;
+    try {
+        perm.resize((size_t)n);
+        inv.resize((size_t)n);
+        tmp.resize((size_t)n);
+        new_off.resize((size_t)n + 1);
+        new_src.resize((size_t)std::max<int64_t>(nnz, 1));
+        new_od.resize((size_t)n);
+    } catch (const std::bad_alloc &) {
+        return pr_fail(PR_ENOMEM, "host allocation failed");
+    }
+    {
+        size_t cnt[33];
+        for (int32_t v = 0; v < n; v++) tmp[v] = v;
+        // pass 1 (secondary key): out-degree class, descending
+        std::memset(cnt, 0, sizeof(cnt));
+        for (int32_t v = 0; v < n; v++) cnt[32 - deg_class(out_degree[v])]++;
+        size_t s = 0;
+        for (int b = 0; b < 33; b++) { size_t c = cnt[b]; cnt[b] = s; s += c; }
+        for (int32_t i = 0; i < n; i++) { int32_t v = tmp[i]; perm[cnt[32 - deg_class(out_degree[v])]++] = v; }
+        // pass 2 (primary key): in-degree class, descending
+        std::memset(cnt, 0, sizeof(cnt));
+        for (int32_t v = 0; v < n; v++) cnt[32 - deg_class(in_offsets[v + 1] - in_offsets[v])]++;
+        s = 0;
+        for (int b = 0; b < 33; b++) { size_t c = cnt[b]; cnt[b] = s; s += c; }
+        for (int32_t i = 0; i < n; i++) {
+            int32_t v = perm[i];
+            tmp[cnt[32 - deg_class(in_offsets[v + 1] - in_offsets[v])]++] = v;
+        }
+        perm.swap(tmp);
+    }
+    for (int32_t i = 0; i < n; i++) inv[perm[i]] = i;
+    new_off[0] = 0;
+    for (int32_t i = 0; i < n; i++) {
+        int32_t v = perm[i];
+        new_off[i + 1] = new_off[i] + (in_offsets[v + 1] - in_offsets[v]);
+        new_od[i] = out_degree[v];
+    }
+    for (int32_t i = 0; i < n; i++) {
+        int32_t v = perm[i];
+        int32_t o = new_off[i];
+        for (int32_t e = in_offsets[v]; e < in_offsets[v + 1]; e++) new_src[o++] = inv[in_sources[e]];
+    }
+    // ---- classes over the relabelled rows
+    pr_graph *g = new (std::nothrow) pr_graph();
+    if (!g) return pr_fail(PR_ENOMEM, "host allocation failed");
+    g->magic = kGraphMagic;
+    g->n = n;
+    g->nnz = nnz;
+    g->n_dangling = n_dangling;
+    cudaGetDevice(&g->device);
+    {
+        int32_t i = 0;
+        while (i < n) {
+            int c = deg_class(new_off[i + 1] - new_off[i]);
+            ClassRange cr{i, i, 0};
+            while (i < n && deg_class(new_off[i + 1] - new_off[i]) == c) {
+                cr.max_deg = std::max(cr.max_deg, new_off[i + 1] - new_off[i]);
+                i++;
+            }
+            cr.end = i;
+            g->classes.push_back(cr);
+        }
+    }
+    g->h_off = new_off;
+    // ---- device copies (sources padded to a multiple of 4 for vector loads)
+    size_t src_alloc = (size_t)((nnz + 3) / 4 * 4) + 4;
+    pr_status s;
+    if ((s = dalloc(&g->d_off, (size_t)n + 1)) != PR_OK ||
+        (s = dalloc(&g->d_src, src_alloc)) != PR_OK ||
+        (s = dalloc(&g->d_outdeg, (size_t)n)) != PR_OK ||
+        (s = dalloc(&g->d_perm, (size_t)n)) != PR_OK ||
+        (s = dalloc(&g->d_inv, (size_t)n)) != PR_OK) {
+        free_graph(g);
+        return s;
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_off, new_off.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(g->d_src, 0, sizeof(int32_t) * src_alloc);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(g->d_src, new_src.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_outdeg, new_od.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_inv, inv.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_graph(g);
+        return pr_cuda_fail(e, "cudaMemcpy graph");
+    }
+    registry_add(g);
+    *out = g;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_graph_destroy(pr_graph *g) {
+    pr_clear_error();
+    if (!g) return PR_OK;
+    if (!pr_graph_valid(g)) return pr_fail(PR_ESTATE, "not a live graph handle");
+    registry_remove(g);
+    free_graph(g);
+    return PR_OK;
+}
+
+extern "C" pr_status pr_graph_info(const pr_graph *g, int32_t *n, int64_t *nnz, int32_t *n_dangling) {
+    pr_clear_error();
+    if (!pr_graph_valid(g)) return pr_fail(PR_ESTATE, "not a live graph handle");
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (n_dangling) *n_dangling = g->n_dangling;
+    return PR_OK;
+}

@@ -1,0 +1,189 @@
+// pr_internal.cuh — shared definitions of libpagerank.so (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pagerank.h"
+
+// ------------------------------------------------------------------ launch geometry
+constexpr int kBlock = 256;          // threads per CTA of every iteration kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, sum of ranks
+
+// ------------------------------------------------------------------ work units
+// A unit is the work of one CTA for one pass: either up to kBlock/g rows of one
+// in-degree class, each row handled by a group of g lanes, or one chunk of the
+// in-edges of a long row, handled by the whole CTA.
+//   rows : a = first row, b = end row, c = -1,       d = log2(g)
+//   chunk: a = row,       b = first edge, c = end edge, d = long-row slot or -1
+struct Unit {
+    int32_t a, b, c, d;
+};
+
+// Per-long-row bookkeeping for rows split into several chunks.
+struct LongRows {
+    int32_t count = 0;          // rows with more than one chunk
+    int32_t chunks = 0;         // total chunks over those rows
+};
+
+// ------------------------------------------------------------------ graph
+struct UnitTable {
+    int W = 0;                   // column width this table was built for
+    Unit *d_units = nullptr;
+    int32_t nunits = 0;
+    int32_t n_long = 0;          // long rows with >1 chunk
+    int32_t n_chunk_slots = 0;   // chunk partial slots
+    int32_t *d_slot_base = nullptr;  // n_long: first chunk partial of each long row
+    double work = 0.0;           // relative work estimate
+};
+
+struct pr_graph_s;
+
+struct ClassRange {
+    int32_t begin, end;   // rows [begin, end) in the relabelled order
+    int32_t max_deg;      // largest in-degree in the range
+};
+
+// ------------------------------------------------------------------ device state
+// One column of a job: one iterate sequence (an instance, or a shared
+// trajectory feeding several instances).
+struct ColState {
+    double alpha;
+    double c0;            // teleport term of the next update (FP64)
+    double v_alpha[2];    // alpha in the job's value type (raw bits: 8 or 16 bytes used)
+    double v_c0[2];       // c0 in the job's value type
+    int32_t active;       // 1 while the column still updates
+    int32_t cur;          // buffer (0/1) holding the current iterate
+    int32_t iters;        // updates performed so far
+    int32_t tap_begin, tap_end;   // this column's taps in the tap array
+    double *copy_dst;     // tap output to fill from the current iterate in the next pass
+    double *hist;         // optional: 3 doubles per iteration (L1, L2, Linf)
+    int32_t hist_cap;
+    int32_t switch_norm;  // mixed precision: norm of the phase-switch test (0 = none)
+    double switch_tol;
+    int32_t switched;     // set when the phase-switch test has passed
+    int32_t pad;
+    double last_err[3];
+    double last_sum;      // sum of the latest iterate (diagnostic)
+    const double *init_src;   // init pass: start vector (nullptr = uniform)
+    int32_t init_order;   // 0: caller order (index by perm), 1: relabelled order
+    int32_t init_float;   // 1: init_src points to floats (phase switch from FP32)
+    int32_t init_col_stride;  // elements between consecutive vertices in init_src
+    int32_t init_col;     // column offset in init_src
+};
+
+// A stopping rule read off a column (Section 3 norm, Section 4 tau).
+struct Tap {
+    double tau;
+    int32_t norm;
+    int32_t max_iter;
+    int32_t fired;        // 0 pending, 1 fired
+    int32_t iters;
+    int32_t converged;
+    int32_t alias_of;     // -1, or the tap whose output this one copies (same iterate)
+    double err;
+    double err_l1;        // L1 norm of the deciding step
+    double *out;          // device, n doubles, caller order
+};
+
+struct JobDev {
+    const int32_t *off;
+    const int32_t *src;
+    const int32_t *outdeg;
+    const int32_t *perm;      // relabelled -> caller id
+    const Unit *units;
+    const int32_t *slot_base;
+    int32_t n;
+    int32_t nunits;
+    int32_t cta_begin, cta_count;
+    int32_t ncols;
+    int32_t alive;            // 1 while any column is active or a copy is pending
+    void *r[2];               // n x W value arrays
+    void *contrib[2];
+    void *chunk_part;         // n_chunk_slots x W values
+    uint32_t *chunk_cnt;      // n_long counters
+    double *cta_part;         // cta_count x W x kPartials
+    ColState *cols;           // W
+    Tap *taps;
+    uint32_t arrive;          // CTAs of this job that finished the pass
+    uint32_t pad;
+};
+
+struct GlobalDev {
+    uint32_t jobs_arrive;
+    int32_t njobs;
+    int32_t pass;             // body executions so far
+    int32_t pass_cap;         // hard cap on body executions
+    int32_t alive;            // set by the last job to finish a pass
+    int32_t error;            // nonzero: a device-side check failed
+    unsigned long long cond;  // cudaGraphConditionalHandle (0 in host-loop mode)
+    uint32_t body_count;      // iteration launches started (independent loop guard)
+    uint32_t pad;
+};
+
+// ------------------------------------------------------------------ graph object
+struct pr_graph {
+    uint32_t magic;
+    int32_t n;
+    int64_t nnz;
+    int32_t n_dangling;
+    int32_t device;
+    int32_t *d_off = nullptr;
+    int32_t *d_src = nullptr;
+    int32_t *d_outdeg = nullptr;
+    int32_t *d_perm = nullptr;       // relabelled -> caller
+    int32_t *d_inv = nullptr;        // caller -> relabelled
+    int32_t *d_indeg_orig = nullptr; // unused placeholder for future use
+    std::vector<ClassRange> classes; // in-degree classes in relabelled order
+    std::vector<int32_t> h_off;      // relabelled offsets (host copy, for unit tables)
+    UnitTable tables[6];             // W = 1, 2, 4, 8, 16, 32
+};
+constexpr uint32_t kGraphMagic = 0x50524731u;   // "PRG1"
+constexpr uint32_t kMlpMagic = 0x50524d31u;     // "PRM1"
+
+// ------------------------------------------------------------------ errors
+void pr_set_error(const std::string &msg);
+void pr_clear_error();
+pr_status pr_fail(pr_status s, const std::string &msg);
+pr_status pr_cuda_fail(cudaError_t e, const char *what);
+
+#define PR_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return pr_cuda_fail(_e, #call);          \
+    } while (0)
+
+// ------------------------------------------------------------------ internals
+int w_index(int W);   // 1,2,4,..,32 -> 0..5
+pr_status pr_graph_units(pr_graph *g, int W, const UnitTable **out);
+bool pr_graph_valid(const pr_graph *g);
+
+// Solve driver (pr_solve.cu)
+struct SolveColumn {
+    const pr_graph *g;
+    double alpha;
+    std::vector<Tap> taps;          // filled with out pointers (device, caller order)
+    std::vector<int32_t> inst;      // instance index of each tap
+    std::vector<double *> host_dst; // per tap: host buffer to receive the answer, or null
+    const double *init_dev = nullptr;   // device start vector in caller order, or null
+    double *hist_host = nullptr;
+    int32_t hist_cap = 0;
+};
+
+struct SolveRequest {
+    int precision = PR_PREC_DF64;
+    int loop = PR_LOOP_GRAPH;
+    double switch_tol = 1e-6;
+    cudaStream_t stream = nullptr;
+    std::vector<SolveColumn> cols;
+};
+
+pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out);
+
+// Live-handle registry: guards every entry point against stale handles.
+void registry_add(const void *p);
+void registry_remove(const void *p);
+bool registry_has(const void *p);

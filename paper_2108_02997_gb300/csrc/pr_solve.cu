@@ -1,0 +1,468 @@
+// pr_solve.cu — the solve driver: lays out jobs, runs the device loop.
+//
+// A request is a list of columns (iterate sequences) with their stopping taps.
+// Columns on the same graph are packed, up to 32 at a time, into jobs whose
+// rank matrices are N x W vertex-major (W = columns padded to a power of two),
+// so that one read of a row's in-edge indices serves W gathers. All jobs of a
+// request advance together, one fused kernel launch per iteration, inside a
+// CUDA graph whose while-node repeats the launch until the device reports that
+// every column has stopped and every answer has been copied out.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "pr_kernels.cuh"
+
+namespace {
+
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+    ~Arena() { if (base) cudaFree(base); }
+    size_t reserve(size_t bytes) {   // returns offset
+        size_t off = (size + 255) & ~size_t(255);
+        size = off + bytes;
+        return off;
+    }
+    pr_status alloc() {
+        if (size == 0) size = 256;
+        cudaError_t e = cudaMalloc((void **)&base, size);
+        if (e != cudaSuccess) {
+            base = nullptr;
+            cudaGetLastError();
+            return pr_fail(e == cudaErrorMemoryAllocation ? PR_ENOMEM : PR_ECUDA,
+                           "device workspace of " + std::to_string(size) + " bytes: " + cudaGetErrorString(e));
+        }
+        return PR_OK;
+    }
+    template <typename T> T *at(size_t off) { return reinterpret_cast<T *>(base + off); }
+};
+
+template <typename V>
+void *iter_kernel_ptr(int W) {
+    switch (W) {
+        case 1: return (void *)pr_iter_kernel<V, 1>;
+        case 2: return (void *)pr_iter_kernel<V, 2>;
+        case 4: return (void *)pr_iter_kernel<V, 4>;
+        case 8: return (void *)pr_iter_kernel<V, 8>;
+        case 16: return (void *)pr_iter_kernel<V, 16>;
+        default: return (void *)pr_iter_kernel<V, 32>;
+    }
+}
+
+void *kernel_for(int prec, int W) {
+    switch (prec) {
+        case PR_PREC_FP64: return iter_kernel_ptr<double>(W);
+        case PR_PREC_FP32: return iter_kernel_ptr<float>(W);
+        default: return iter_kernel_ptr<df64>(W);
+    }
+}
+
+size_t value_size(int prec) { return prec == PR_PREC_FP32 ? 4 : 8; }
+
+void store_value(double *dst, int prec, double x) {
+    dst[0] = 0.0;
+    dst[1] = 0.0;
+    if (prec == PR_PREC_FP64) {
+        std::memcpy(dst, &x, 8);
+    } else if (prec == PR_PREC_FP32) {
+        float f = (float)x;
+        std::memcpy(dst, &f, 4);
+    } else {
+        df64 d = df_from_double(x);
+        std::memcpy(dst, &d, 8);
+    }
+}
+
+int pow2_at_least(int k) {
+    int w = 1;
+    while (w < k) w <<= 1;
+    return w;
+}
+
+struct HostJob {
+    const pr_graph *g;
+    std::vector<int> cols;           // request column indices
+    const UnitTable *ut = nullptr;
+    int cta_count = 0;
+    size_t off_r[2], off_c[2], off_cp, off_cnt, off_part, off_cols, off_taps, off_hist;
+    int ntaps = 0;
+    int hist_total = 0;
+};
+
+struct LoopStats {
+    int launches = 0;
+    int passes = 0;
+    double kernel_ms = 0.0;
+    double total_ms = 0.0;
+};
+
+LoopStats g_last_stats;
+
+}  // namespace
+
+extern "C" pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms) {
+    if (launches) *launches = g_last_stats.launches;
+    if (passes) *passes = g_last_stats.passes;
+    if (kernel_ms) *kernel_ms = g_last_stats.kernel_ms;
+    if (total_ms) *total_ms = g_last_stats.total_ms;
+    return PR_OK;
+}
+
+namespace {
+
+// One phase of a solve in one value type: init pass + loop of iteration passes.
+pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size_t off_jobs, size_t off_glob,
+                    size_t off_ctajob, int total_ctas, int pass_cap, int loop, cudaStream_t st, LoopStats &stats) {
+    void *kern = kernel_for(prec, W);
+    JobDev *d_jobs = ar.at<JobDev>(off_jobs);
+    GlobalDev *d_glob = ar.at<GlobalDev>(off_glob);
+    const int32_t *d_ctajob = ar.at<int32_t>(off_ctajob);
+    GlobalDev hg{};
+    hg.njobs = (int32_t)jobs.size();
+    hg.pass_cap = pass_cap;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    PR_CUDA(cudaEventCreate(&ev0));
+    PR_CUDA(cudaEventCreate(&ev1));
+    struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{ev0, ev1};
+    int mode_init = kPassInit, mode_iter = kPassIterate;
+    void *args_init[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_ctajob, (void *)&mode_init};
+    void *args_iter[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_ctajob, (void *)&mode_iter};
+    dim3 grid(total_ctas), block(kBlock);
+    PR_CUDA(cudaEventRecord(ev0, st));
+    if (loop == PR_LOOP_HOST) {
+        hg.cond = 0;
+        PR_CUDA(cudaMemcpyAsync(d_glob, &hg, sizeof(hg), cudaMemcpyHostToDevice, st));
+        PR_CUDA(cudaLaunchKernel(kern, grid, block, args_init, 0, st));
+        stats.launches++;
+        cudaEvent_t k0 = nullptr, k1 = nullptr;
+        PR_CUDA(cudaEventCreate(&k0));
+        PR_CUDA(cudaEventCreate(&k1));
+        struct KGuard { cudaEvent_t a, b; ~KGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } kg{k0, k1};
+        GlobalDev back{};
+        for (int p = 0; p < pass_cap + 1; p++) {
+            PR_CUDA(cudaEventRecord(k0, st));
+            PR_CUDA(cudaLaunchKernel(kern, grid, block, args_iter, 0, st));
+            PR_CUDA(cudaEventRecord(k1, st));
+            stats.launches++;
+            PR_CUDA(cudaMemcpyAsync(&back, d_glob, sizeof(back), cudaMemcpyDeviceToHost, st));
+            PR_CUDA(cudaStreamSynchronize(st));
+            float ms = 0.f;
+            PR_CUDA(cudaEventElapsedTime(&ms, k0, k1));
+            stats.kernel_ms += ms;
+            if (!back.alive || back.error) break;
+        }
+        stats.passes += back.pass;
+        if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
+    } else {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        PR_CUDA(cudaGraphCreate(&graph, 0));
+        struct GGuard {
+            cudaGraph_t *g; cudaGraphExec_t *x;
+            ~GGuard() { if (*x) cudaGraphExecDestroy(*x); if (*g) cudaGraphDestroy(*g); }
+        } gg{&graph, &exec};
+        cudaGraphConditionalHandle h;
+        PR_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault));
+        hg.cond = (unsigned long long)h;
+        PR_CUDA(cudaMemcpyAsync(d_glob, &hg, sizeof(hg), cudaMemcpyHostToDevice, st));
+        cudaKernelNodeParams kp{};
+        kp.func = kern;
+        kp.gridDim = grid;
+        kp.blockDim = block;
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args_init;
+        cudaGraphNode_t n_init, n_cond, n_body;
+        PR_CUDA(cudaGraphAddKernelNode(&n_init, graph, nullptr, 0, &kp));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        PR_CUDA(cudaGraphAddNode(&n_cond, graph, &n_init, nullptr, 1, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        kp.kernelParams = args_iter;
+        PR_CUDA(cudaGraphAddKernelNode(&n_body, body, nullptr, 0, &kp));
+        PR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        PR_CUDA(cudaGraphLaunch(exec, st));
+        GlobalDev back{};
+        PR_CUDA(cudaMemcpyAsync(&back, d_glob, sizeof(back), cudaMemcpyDeviceToHost, st));
+        PR_CUDA(cudaStreamSynchronize(st));
+        stats.launches += 1 + back.pass;
+        stats.passes += back.pass;
+        if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
+    }
+    PR_CUDA(cudaEventRecord(ev1, st));
+    PR_CUDA(cudaEventSynchronize(ev1));
+    float ms = 0.f;
+    PR_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+    stats.total_ms += ms;
+    return PR_OK;
+}
+
+}  // namespace
+
+pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out) {
+    LoopStats stats;
+    g_last_stats = stats;
+    const int ncols = (int)req.cols.size();
+    if (ncols == 0) return PR_OK;
+    cudaStream_t st = req.stream;
+    const bool mixed = req.precision == PR_PREC_MIXED;
+    const int prec1 = mixed ? PR_PREC_FP32 : req.precision;
+    // ---- group columns into jobs (same graph, <= 32 columns)
+    std::vector<HostJob> jobs;
+    {
+        std::map<const pr_graph *, std::vector<int>> by_graph;
+        std::vector<const pr_graph *> order;
+        for (int c = 0; c < ncols; c++) {
+            if (!by_graph.count(req.cols[c].g)) order.push_back(req.cols[c].g);
+            by_graph[req.cols[c].g].push_back(c);
+        }
+        for (const pr_graph *g : order) {
+            const auto &v = by_graph[g];
+            for (size_t i = 0; i < v.size(); i += 32) {
+                HostJob j;
+                j.g = g;
+                j.cols.assign(v.begin() + i, v.begin() + std::min(v.size(), i + 32));
+                jobs.push_back(j);
+            }
+        }
+    }
+    int W = 1;
+    for (auto &j : jobs) W = std::max(W, pow2_at_least((int)j.cols.size()));
+    // ---- unit tables and CTA split
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    int sms = 0;
+    PR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int occ = 0;
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_for(prec1, W), kBlock, 0));
+    if (mixed) {
+        int occ2 = 0;
+        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kernel_for(PR_PREC_DF64, W), kBlock, 0));
+        occ = std::min(occ, occ2);
+    }
+    occ = std::max(occ, 1);
+    const int budget = sms * occ;
+    double total_work = 0.0;
+    for (auto &j : jobs) {
+        pr_status s = pr_graph_units(const_cast<pr_graph *>(j.g), W, &j.ut);
+        if (s != PR_OK) return s;
+        total_work += std::max(j.ut->work, 1.0);
+    }
+    int total_ctas = 0;
+    for (auto &j : jobs) {
+        int want = (int)std::lround(budget * std::max(j.ut->work, 1.0) / total_work);
+        j.cta_count = std::max(1, std::min(want, std::max(j.ut->nunits, 1)));
+        total_ctas += j.cta_count;
+    }
+    // ---- workspace layout
+    Arena ar;
+    const size_t vs_max = 8;
+    int max_iter_all = 1;
+    for (auto &c : req.cols)
+        for (auto &t : c.taps) max_iter_all = std::max(max_iter_all, t.max_iter);
+    for (auto &j : jobs) {
+        const size_t n = (size_t)j.g->n;
+        for (int b = 0; b < 2; b++) {
+            j.off_r[b] = ar.reserve(n * W * vs_max);
+            j.off_c[b] = ar.reserve(n * W * vs_max);
+        }
+        j.off_cp = ar.reserve((size_t)std::max(j.ut->n_chunk_slots, 1) * W * vs_max);
+        j.off_cnt = ar.reserve((size_t)std::max(j.ut->n_long, 1) * sizeof(uint32_t));
+        j.off_part = ar.reserve((size_t)j.cta_count * W * kPartials * sizeof(double));
+        j.off_cols = ar.reserve((size_t)W * sizeof(ColState));
+        for (int c : j.cols) j.ntaps += (int)req.cols[c].taps.size();
+        j.off_taps = ar.reserve((size_t)std::max(j.ntaps, 1) * sizeof(Tap));
+        for (int c : j.cols) j.hist_total += req.cols[c].hist_host ? req.cols[c].hist_cap : 0;
+        j.off_hist = ar.reserve((size_t)std::max(j.hist_total, 1) * 3 * sizeof(double));
+    }
+    // mixed precision keeps the FP32 phase buffers alive while the refinement
+    // phase starts from them
+    std::vector<size_t> off_r32;
+    if (mixed)
+        for (auto &j : jobs) {
+            off_r32.push_back(ar.reserve((size_t)j.g->n * W * 4));
+            off_r32.push_back(ar.reserve((size_t)j.g->n * W * 4));
+        }
+    // staging for host outputs: taps whose out is null get a device buffer
+    std::vector<size_t> stage_off;
+    for (auto &c : req.cols)
+        for (auto &t : c.taps)
+            if (!t.out) stage_off.push_back(ar.reserve((size_t)c.g->n * sizeof(double)));
+    const size_t off_jobs = ar.reserve(jobs.size() * sizeof(JobDev));
+    const size_t off_glob = ar.reserve(sizeof(GlobalDev));
+    const size_t off_ctajob = ar.reserve((size_t)total_ctas * sizeof(int32_t));
+    pr_status s = ar.alloc();
+    if (s != PR_OK) return s;
+    // ---- fill job and column state on the host
+    std::vector<JobDev> hjobs(jobs.size());
+    std::vector<int32_t> ctajob(total_ctas);
+    std::vector<std::vector<ColState>> hcols(jobs.size());
+    std::vector<std::vector<Tap>> htaps(jobs.size());
+    size_t stage_i = 0;
+    std::vector<std::vector<double *>> col_stage_ptrs(ncols);
+    int cta_at = 0;
+    for (size_t ji = 0; ji < jobs.size(); ji++) {
+        HostJob &j = jobs[ji];
+        JobDev &d = hjobs[ji];
+        std::memset(&d, 0, sizeof(d));
+        d.off = j.g->d_off;
+        d.src = j.g->d_src;
+        d.outdeg = j.g->d_outdeg;
+        d.perm = j.g->d_perm;
+        d.units = j.ut->d_units;
+        d.slot_base = j.ut->d_slot_base;
+        d.n = j.g->n;
+        d.nunits = j.ut->nunits;
+        d.cta_begin = cta_at;
+        d.cta_count = j.cta_count;
+        for (int q = 0; q < j.cta_count; q++) ctajob[cta_at + q] = (int32_t)ji;
+        cta_at += j.cta_count;
+        d.ncols = (int32_t)j.cols.size();
+        d.alive = 1;
+        if (mixed) {
+            d.r[0] = ar.at<void>(off_r32[2 * ji]);
+            d.r[1] = ar.at<void>(off_r32[2 * ji + 1]);
+        } else {
+            d.r[0] = ar.at<void>(j.off_r[0]);
+            d.r[1] = ar.at<void>(j.off_r[1]);
+        }
+        d.contrib[0] = ar.at<void>(j.off_c[0]);
+        d.contrib[1] = ar.at<void>(j.off_c[1]);
+        d.chunk_part = ar.at<void>(j.off_cp);
+        d.chunk_cnt = ar.at<uint32_t>(j.off_cnt);
+        d.cta_part = ar.at<double>(j.off_part);
+        d.cols = ar.at<ColState>(j.off_cols);
+        d.taps = ar.at<Tap>(j.off_taps);
+        hcols[ji].assign(W, ColState{});
+        int tap_at = 0, hist_at = 0;
+        for (size_t k = 0; k < j.cols.size(); k++) {
+            SolveColumn &sc = req.cols[j.cols[k]];
+            ColState &cs = hcols[ji][k];
+            std::memset(&cs, 0, sizeof(cs));
+            cs.alpha = sc.alpha;
+            store_value(cs.v_alpha, prec1, sc.alpha);
+            store_value(cs.v_c0, prec1, 1.0 / (double)j.g->n);   // init pass: uniform start value
+            cs.active = 1;
+            cs.cur = 0;
+            cs.tap_begin = tap_at;
+            for (auto &t : sc.taps) {
+                Tap tt = t;
+                tt.fired = 0;
+                tt.alias_of = -1;
+                if (!tt.out) {
+                    tt.out = ar.at<double>(stage_off[stage_i++]);
+                }
+                col_stage_ptrs[j.cols[k]].push_back(tt.out);
+                htaps[ji].push_back(tt);
+                tap_at++;
+            }
+            cs.tap_end = tap_at;
+            if (sc.hist_host) {
+                cs.hist = ar.at<double>(j.off_hist) + 3 * (size_t)hist_at;
+                cs.hist_cap = sc.hist_cap;
+                hist_at += sc.hist_cap;
+            }
+            cs.init_src = sc.init_dev;
+            cs.init_order = 0;
+            cs.init_col_stride = 1;
+            cs.init_col = 0;
+            if (mixed) {
+                // switch on the strictest norm among the column's taps (L1 >= L2 >= Linf)
+                int sn = 3;
+                for (auto &t : sc.taps) sn = std::min(sn, (int)t.norm);
+                cs.switch_norm = sn;
+                cs.switch_tol = req.switch_tol;
+            }
+        }
+        cudaError_t e = cudaMemcpyAsync(d.cols, hcols[ji].data(), W * sizeof(ColState), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !htaps[ji].empty())
+            e = cudaMemcpyAsync(d.taps, htaps[ji].data(), htaps[ji].size() * sizeof(Tap), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.chunk_cnt, 0, (size_t)std::max(j.ut->n_long, 1) * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return pr_cuda_fail(e, "workspace upload");
+    }
+    PR_CUDA(cudaMemcpyAsync(ar.at<JobDev>(off_jobs), hjobs.data(), hjobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice, st));
+    PR_CUDA(cudaMemcpyAsync(ar.at<int32_t>(off_ctajob), ctajob.data(), ctajob.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const int pass_cap = max_iter_all + 3;
+    // ---- phase 1 (or the only phase)
+    s = run_phase(prec1, W, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, pass_cap, req.loop, st, stats);
+    if (s != PR_OK) return s;
+    // ---- mixed precision: refinement phase in DF64 from the FP32 iterates
+    if (mixed) {
+        bool any = false;
+        for (size_t ji = 0; ji < jobs.size(); ji++) {
+            HostJob &j = jobs[ji];
+            std::vector<ColState> back(W);
+            PR_CUDA(cudaMemcpyAsync(back.data(), hjobs[ji].cols, W * sizeof(ColState), cudaMemcpyDeviceToHost, st));
+            std::vector<Tap> tback(htaps[ji].size());
+            if (!tback.empty())
+                PR_CUDA(cudaMemcpyAsync(tback.data(), hjobs[ji].taps, tback.size() * sizeof(Tap), cudaMemcpyDeviceToHost, st));
+            PR_CUDA(cudaStreamSynchronize(st));
+            for (size_t k = 0; k < j.cols.size(); k++) {
+                ColState &cs = back[k];
+                bool pending = false;
+                for (int q = cs.tap_begin; q < cs.tap_end; q++) pending |= !tback[q].fired;
+                cs.active = pending ? 1 : 0;
+                if (pending) any = true;
+                cs.switch_norm = 0;
+                cs.init_src = reinterpret_cast<const double *>(ar.at<float>(off_r32[2 * ji + cs.cur]));
+                cs.init_order = 1;
+                cs.init_float = 1;
+                cs.init_col_stride = W;
+                cs.init_col = (int32_t)k;
+                cs.cur = 0;
+                cs.copy_dst = nullptr;
+                store_value(cs.v_alpha, PR_PREC_DF64, cs.alpha);
+            }
+            hjobs[ji].r[0] = ar.at<void>(j.off_r[0]);
+            hjobs[ji].r[1] = ar.at<void>(j.off_r[1]);
+            hjobs[ji].alive = 1;
+            hjobs[ji].arrive = 0;
+            PR_CUDA(cudaMemcpyAsync(hjobs[ji].cols, back.data(), W * sizeof(ColState), cudaMemcpyHostToDevice, st));
+        }
+        if (any) {
+            PR_CUDA(cudaMemcpyAsync(ar.at<JobDev>(off_jobs), hjobs.data(), hjobs.size() * sizeof(JobDev),
+                                    cudaMemcpyHostToDevice, st));
+            s = run_phase(PR_PREC_DF64, W, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, pass_cap, req.loop, st, stats);
+            if (s != PR_OK) return s;
+        }
+    }
+    // ---- results: taps, aliases, histories
+    tap_out.assign(ncols, {});
+    for (size_t ji = 0; ji < jobs.size(); ji++) {
+        HostJob &j = jobs[ji];
+        std::vector<Tap> tback(htaps[ji].size());
+        if (!tback.empty())
+            PR_CUDA(cudaMemcpyAsync(tback.data(), hjobs[ji].taps, tback.size() * sizeof(Tap), cudaMemcpyDeviceToHost, st));
+        std::vector<ColState> back(W);
+        PR_CUDA(cudaMemcpyAsync(back.data(), hjobs[ji].cols, W * sizeof(ColState), cudaMemcpyDeviceToHost, st));
+        PR_CUDA(cudaStreamSynchronize(st));
+        for (auto &t : tback) {
+            if (!t.fired) return pr_fail(PR_ETIMEOUT, "a stopping rule never fired");
+            if (t.alias_of >= 0)
+                PR_CUDA(cudaMemcpyAsync(t.out, tback[t.alias_of].out, (size_t)j.g->n * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
+        }
+        for (size_t k = 0; k < j.cols.size(); k++) {
+            SolveColumn &sc = req.cols[j.cols[k]];
+            const ColState &cs = back[k];
+            std::vector<Tap> mine(tback.begin() + cs.tap_begin, tback.begin() + cs.tap_end);
+            for (size_t q = 0; q < mine.size() && q < sc.host_dst.size(); q++)
+                if (sc.host_dst[q])
+                    PR_CUDA(cudaMemcpyAsync(sc.host_dst[q], mine[q].out, (size_t)j.g->n * sizeof(double),
+                                            cudaMemcpyDeviceToHost, st));
+            tap_out[j.cols[k]] = mine;
+            if (sc.hist_host && cs.hist) {
+                int nh = std::min(cs.iters, sc.hist_cap);
+                if (nh > 0)
+                    PR_CUDA(cudaMemcpyAsync(sc.hist_host, cs.hist, (size_t)nh * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            }
+        }
+    }
+    PR_CUDA(cudaStreamSynchronize(st));
+    g_last_stats = stats;
+    return PR_OK;
+}

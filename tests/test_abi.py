@@ -1,0 +1,93 @@
+"""The C-ABI library builds, loads and exports every symbol the header declares;
+host-side argument checks answer with error codes (no GPU needed)."""
+import ctypes as C
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2108_02997_gb300 import binding
+    return binding.lib()
+
+
+def declared_functions():
+    names = []
+    for h in sorted((ROOT / "include").glob("*.h")):
+        text = h.read_text()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*\b(pr_[a-z0-9_]+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for need in ("pr_graph_create", "pr_graph_destroy", "pr_solve", "pr_solve_batch", "pr_last_error"):
+        assert need in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_2108_02997_gb300 import binding
+    for name in declared_functions():
+        assert hasattr(L, name), f"{name} declared in include/ but not exported"
+        assert name in binding.SIGNATURES, f"{name} has no binding signature"
+
+
+def test_version_and_status_strings(L):
+    assert L.pr_version() >= 10000
+    assert L.pr_status_string(1) == b"PR_EINVAL"
+
+
+def _create(L, n, off, src, od):
+    h = C.c_void_p()
+    off = np.ascontiguousarray(off, np.int32)
+    src = np.ascontiguousarray(src, np.int32)
+    od = np.ascontiguousarray(od, np.int32)
+    st = L.pr_graph_create(n, src.size, off.ctypes.data, src.ctypes.data if src.size else None,
+                           od.ctypes.data, C.byref(h))
+    return st, h
+
+
+def test_malformed_csr_is_rejected_before_any_device_work(L):
+    # non-monotone offsets
+    st, _ = _create(L, 3, [0, 2, 1, 3], [1, 2, 0], [1, 1, 1])
+    assert st == 1 and b"non-decreasing" in L.pr_last_error()
+    # out-of-range source
+    st, _ = _create(L, 2, [0, 1, 2], [0, 5], [1, 0])
+    assert st == 1 and b"out of range" in L.pr_last_error()
+    # out-degrees inconsistent with the edges
+    st, _ = _create(L, 2, [0, 1, 1], [1], [0, 0])
+    assert st == 1 and b"does not match" in L.pr_last_error()
+    # offsets[n] != nnz
+    st, _ = _create(L, 2, [0, 1, 3], [1], [0, 1])
+    assert st == 1
+    # n < 1
+    h = C.c_void_p()
+    assert L.pr_graph_create(0, 0, None, None, None, C.byref(h)) == 1
+
+
+def test_solve_rejects_bad_handles_and_arguments(L):
+    from paper_2108_02997_gb300 import binding
+    out = np.empty(4)
+    bogus = C.c_void_p(0x1234)
+    assert L.pr_solve(None, 0.85, 1e-6, 1, 500, None, out.ctypes.data, None, None, None) == 5
+    assert L.pr_solve(bogus, 0.85, 1e-6, 1, 500, None, out.ctypes.data, None, None, None) == 5
+    assert L.pr_graph_destroy(None) == 0
+    assert L.pr_graph_destroy(bogus) == 5
+    o = binding.default_options()
+    o.precision = 17
+    assert L.pr_solve_batch(None, 0, C.byref(o)) == 1
+    assert L.pr_solve_batch(None, -1, None) == 1
+
+
+def test_options_defaults(L):
+    from paper_2108_02997_gb300 import binding
+    o = binding.default_options()
+    assert o.precision == binding.PR_PREC_DF64 and o.switch_tol == 1e-6 and o.share_trajectories == 1
+    assert o.loop == binding.PR_LOOP_GRAPH and o.init == binding.PR_INIT_UNIFORM
