@@ -55,11 +55,11 @@ def test_er10k_plain_matches_oracle(B, orc, er10k, er10k_dev, precision):
     res = B.pr_solve(er10k_dev, 0.85, 1e-10, 1, 500, precision=precision, history=True)
     assert_fp64_parity(res.ranks, res.iters, res.err, ref, 1e-10, 1, f"er10k {precision}")
     assert res.converged == ref.converged
-    # per-iteration norms follow the oracle's
+    # per-iteration norms follow the oracle's within the bound that the rank
+    # tolerance implies (see tests/parity.py)
     h = res.err_history
     k = min(len(h), len(ref.err_hist))
-    rel = np.abs(h[:k] - ref.err_hist[:k]) / np.maximum(ref.err_hist[:k], 1e-300)
-    assert rel.max() < 1e-5, rel.max()
+    assert np.abs(h[:k] - ref.err_hist[:k]).max() <= 2e-12
 
 
 @pytest.mark.parametrize("norm", [1, 2, 3])
