@@ -49,10 +49,11 @@ def peaks():
 
 def make_workload(name, gg):
     """(graphs, instance specs [(graph index, alpha, tau, norm, max_iter)], precision, description)."""
-    if name == "rmat22":
-        g = gg.rmat(22, 16, seed=22)
+    if name in ("rmat22", "rmat21"):
+        scale = int(name[4:])
+        g = gg.rmat(scale, 16, seed=scale)
         specs = [(0, 0.85, t, nm, 500) for t in (1e-6, 1e-10) for nm in (1, 2, 3)]
-        return [g], specs, "df64", "rmat-s22 ef16 seed22, alpha .85, tau {1e-6,1e-10} x {L1,L2,Linf}"
+        return [g], specs, "df64", f"rmat-s{scale} ef16 seed{scale}, alpha .85, tau {{1e-6,1e-10}} x {{L1,L2,Linf}}"
     if name == "sweep330":
         g = gg.erdos_renyi_10k(seed=1)
         alphas = [round(0.5 + 0.05 * i, 2) for i in range(11)]
@@ -179,7 +180,7 @@ def run_ours(args, world, rank, local):
 
     def step():
         xs = insts()
-        B.pr_solve_batch(xs, precision=precision, outputs_on_device=True, stream=sptr)
+        B.pr_solve_batch(xs, precision=precision, outputs_on_device=True, stream=sptr, loop=args.loop)
         return xs
 
     for _ in range(args.warmup):
@@ -381,7 +382,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "sweep330", "multi64", "rmat24mixed"])
+    ap.add_argument("--workload", default="rmat22",
+                    choices=["rmat22", "rmat21", "sweep330", "multi64", "rmat24mixed"])
+    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
+                    help="device loop of the timed solves (host: one launch per iteration)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
