@@ -159,6 +159,39 @@ pr_status pr_solve(const pr_graph *g, double alpha, double tol, int32_t norm, in
                    const pr_options *opt, double *ranks_out, int32_t *iters_out, double *err_out,
                    int32_t *converged_out);
 
+/*
+ * pr_solve_noalloc — the same solve as pr_solve (DF64, uniform start), for
+ * callers that cannot let the library allocate device memory. The paper has
+ * no counterpart; this is a deployment variant.
+ *
+ * Who needs it: a process whose device memory belongs to its own pool or
+ * caching allocator (a cudaMalloc behind its back can fail or fragment the
+ * pool), a service held to a fixed device-memory budget, or a latency-bound
+ * loop that cannot take the implicit device synchronisation of
+ * cudaMalloc/cudaFree. This call makes no cudaMalloc, cudaFree or other
+ * allocating call: the iterates, contributions, per-CTA partials and loop
+ * state live in one file-scope device array of 40 MiB that every GPU loading
+ * the library holds until the process exits.
+ *
+ * Arguments as pr_solve, except:
+ *   d_ranks_out : device pointer, n doubles, caller order
+ *   stream      : cudaStream_t or NULL; the call returns after the stream
+ *                 has finished the solve
+ * Limits and behaviour:
+ *   - the working set is about 32 bytes per vertex plus small tables; a graph
+ *     that does not fit (about n > 1.2 million) is rejected with PR_EINVAL
+ *     and a message stating the bytes needed;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - every call shares the one array and overwrites what the previous call
+ *     left there: calls that overlap on the GPU (other streams, other host
+ *     threads) race and corrupt each other; serialise them.
+ */
+pr_status pr_solve_noalloc(const pr_graph *g, double alpha, double tol, int32_t norm, int32_t max_iter,
+                           double *d_ranks_out, void *stream, int32_t *iters_out, double *err_out,
+                           int32_t *converged_out);
+
 /* One instance of a batch. Inputs: g .. init_vec. Outputs: iters .. status. */
 typedef struct pr_instance {
     const pr_graph *g;

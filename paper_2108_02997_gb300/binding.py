@@ -71,6 +71,7 @@ SIGNATURES = {
     "pr_mlp_warm_start": ([_vp, _vp, _d, _vp, _vp], _i32),
     "pr_mlp_train": ([_vp, _vp, _vp, _vp, _i32, _i32, _f, _vp, _vp], _i32),
     "pr_last_solve_stats": ([_vp, _vp, _vp, _vp], _i32),
+    "pr_solve_noalloc": ([_vp, _d, _d, _i32, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "pr_last_error": ([], C.c_char_p),
     "pr_status_string": ([_i32], C.c_char_p),
     "pr_version": ([], _i32),

@@ -276,6 +276,13 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
         free_graph(g);
         return pr_cuda_fail(e, "cudaMemcpy graph");
     }
+    // the single-column work table is built now so that solves on this graph
+    // never need to allocate it later
+    const UnitTable *t1 = nullptr;
+    if ((s = pr_graph_units(g, 1, &t1)) != PR_OK) {
+        free_graph(g);
+        return s;
+    }
     registry_add(g);
     *out = g;
     return PR_OK;
