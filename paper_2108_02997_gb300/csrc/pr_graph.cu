@@ -44,9 +44,9 @@ pr_status dalloc(T **p, size_t count) {
 
 void free_tables(pr_graph *g) {
     for (auto &t : g->tables) {
-        cudaFree(t.d_units);
+        cudaFree(t.d_tiles);
         cudaFree(t.d_slot_base);
-        t = UnitTable();
+        t = TileTable();
     }
 }
 
@@ -78,79 +78,81 @@ int w_index(int W) {
 
 bool pr_graph_valid(const pr_graph *g) { return g && registry_has(g) && g->magic == kGraphMagic; }
 
-// Work units of width W (see Unit in pr_internal.cuh). Lanes of a group split
-// a row's in-edges into `es` interleaved slots, each slot handling all W
-// columns of an edge with W adjacent lanes; rows whose per-lane share would
-// exceed kMaxPerLane gathers are split into chunks handled by a whole CTA.
-pr_status pr_graph_units(pr_graph *g, int W, const UnitTable **out) {
+// Tiles of width W (see Tile in pr_internal.cuh). Rows of one in-degree class
+// are packed into tiles of at most tile_rows(W) rows and tile_edges(W)
+// in-edges; the lanes of a group (g = es * W lanes, es in-edge slots of W
+// columns each) share one row in the summation phase, es sized so that each
+// slot adds about four gathered values. Rows longer than tile_edges(W) are
+// split into chunks handled by a whole CTA.
+pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     int wi = w_index(W);
     if (wi < 0) return pr_fail(PR_EINVAL, "unsupported column width");
-    UnitTable &t = g->tables[wi];
-    if (t.d_units) {
+    TileTable &t = g->tables[wi];
+    if (t.d_tiles) {
         *out = &t;
         return PR_OK;
     }
-    constexpr int kEdgesPerLane = 4;
-    constexpr int kMaxPerLane = 16;
+    const int TE = tile_edges(W), TR = tile_rows(W);
     const int max_es = 32 / W;
-    const int32_t chunk = (kBlock / W) * 8;
-    std::vector<Unit> units;
+    std::vector<Tile> tiles;
     std::vector<int32_t> slot_base;
     int32_t n_chunk_slots = 0;
     double work = 0.0;
+    const std::vector<int32_t> &off = g->h_off;
     for (const ClassRange &cr : g->classes) {
         if (cr.end <= cr.begin) continue;
-        int es = 1;
-        while (es < max_es && es * kEdgesPerLane < cr.max_deg) es <<= 1;
-        bool long_rows = cr.max_deg > es * kMaxPerLane;
-        if (!long_rows) {
-            int gsz = es * W;
-            int glog = 0;
-            while ((1 << glog) < gsz) glog++;
-            int32_t rows_per_unit = kBlock >> glog;
-            for (int32_t r = cr.begin; r < cr.end; r += rows_per_unit) {
-                int32_t e = std::min(cr.end, r + rows_per_unit);
-                units.push_back({r, e, -1, glog});
-                work += (double)(g->h_off[e] - g->h_off[r]) * W + (double)(e - r) * W * 4.0;
-            }
-        } else {
+        if (cr.max_deg > TE) {
             for (int32_t v = cr.begin; v < cr.end; v++) {
-                int32_t e0 = g->h_off[v], e1 = g->h_off[v + 1];
+                int32_t e0 = off[v], e1 = off[v + 1];
                 int32_t deg = e1 - e0;
-                int32_t nch = std::max<int32_t>(1, (deg + chunk - 1) / chunk);
-                if (nch == 1) {
-                    units.push_back({v, e0, e1, -1});
-                } else {
-                    int32_t slot = (int32_t)slot_base.size();
+                int32_t nch = std::max<int32_t>(1, (deg + TE - 1) / TE);
+                int32_t slot = -1;
+                if (nch > 1) {
+                    slot = (int32_t)slot_base.size();
                     slot_base.push_back(n_chunk_slots);
                     n_chunk_slots += nch;
-                    for (int32_t k = 0; k < nch; k++) {
-                        int32_t a = e0 + k * chunk, b = std::min(e1, a + chunk);
-                        units.push_back({v, a, b, slot});
-                    }
+                }
+                for (int32_t k = 0; k < nch; k++) {
+                    int32_t a = e0 + k * TE, b = std::min(e1, a + TE);
+                    tiles.push_back({v, v + 1, a, b, -1, slot, k, nch});
                 }
                 work += (double)deg * W + W * 4.0;
             }
+            continue;
+        }
+        int es = 1;
+        while (es < max_es && es * 4 < cr.max_deg) es <<= 1;
+        int glog = 0;
+        while ((1 << glog) < es * W) glog++;
+        int32_t r = cr.begin;
+        while (r < cr.end) {
+            int32_t r1 = r;
+            while (r1 < cr.end && r1 - r < TR && off[r1 + 1] - off[r] <= TE) r1++;
+            if (r1 == r) r1 = r + 1;   // cannot happen (deg <= TE), kept for safety
+            tiles.push_back({r, r1, off[r], off[r1], glog, -1, 0, 0});
+            work += (double)(off[r1] - off[r]) * W + (double)(r1 - r) * W * 4.0;
+            r = r1;
         }
     }
-    UnitTable nt;
+    TileTable nt;
     nt.W = W;
-    nt.nunits = (int32_t)units.size();
+    nt.ntiles = (int32_t)tiles.size();
     nt.n_long = (int32_t)slot_base.size();
     nt.n_chunk_slots = n_chunk_slots;
     nt.work = work;
-    pr_status s = dalloc(&nt.d_units, units.size());
+    pr_status s = dalloc(&nt.d_tiles, tiles.size());
     if (s != PR_OK) return s;
     s = dalloc(&nt.d_slot_base, slot_base.size());
-    if (s != PR_OK) { cudaFree(nt.d_units); return s; }
-    if (!units.empty()) {
-        cudaError_t e = cudaMemcpy(nt.d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) { cudaFree(nt.d_units); cudaFree(nt.d_slot_base); return pr_cuda_fail(e, "cudaMemcpy units"); }
-    }
-    if (!slot_base.empty()) {
-        cudaError_t e = cudaMemcpy(nt.d_slot_base, slot_base.data(), slot_base.size() * sizeof(int32_t),
-                                   cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) { cudaFree(nt.d_units); cudaFree(nt.d_slot_base); return pr_cuda_fail(e, "cudaMemcpy slots"); }
+    if (s != PR_OK) { cudaFree(nt.d_tiles); return s; }
+    cudaError_t e = cudaSuccess;
+    if (!tiles.empty())
+        e = cudaMemcpy(nt.d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !slot_base.empty())
+        e = cudaMemcpy(nt.d_slot_base, slot_base.data(), slot_base.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(nt.d_tiles);
+        cudaFree(nt.d_slot_base);
+        return pr_cuda_fail(e, "cudaMemcpy tiles");
     }
     t = nt;
     *out = &t;
@@ -254,20 +256,23 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
         }
     }
     g->h_off = new_off;
-    // ---- device copies (sources padded to a multiple of 4 for vector loads)
-    size_t src_alloc = (size_t)((nnz + 3) / 4 * 4) + 4;
+    // ---- device copies, each padded with kPad zeroed elements so that tile
+    // copies rounded to 16 bytes stay inside the allocation
+    const size_t n_off = (size_t)n + 1 + kPad, n_src = (size_t)nnz + kPad, n_od = (size_t)n + kPad;
     pr_status s;
-    if ((s = dalloc(&g->d_off, (size_t)n + 1)) != PR_OK ||
-        (s = dalloc(&g->d_src, src_alloc)) != PR_OK ||
-        (s = dalloc(&g->d_outdeg, (size_t)n)) != PR_OK ||
+    if ((s = dalloc(&g->d_off, n_off)) != PR_OK ||
+        (s = dalloc(&g->d_src, n_src)) != PR_OK ||
+        (s = dalloc(&g->d_outdeg, n_od)) != PR_OK ||
         (s = dalloc(&g->d_perm, (size_t)n)) != PR_OK ||
         (s = dalloc(&g->d_inv, (size_t)n)) != PR_OK) {
         free_graph(g);
         return s;
     }
     cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemset(g->d_off, 0, sizeof(int32_t) * n_off);
+    if (e == cudaSuccess) e = cudaMemset(g->d_src, 0, sizeof(int32_t) * n_src);
+    if (e == cudaSuccess) e = cudaMemset(g->d_outdeg, 0, sizeof(int32_t) * n_od);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_off, new_off.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(g->d_src, 0, sizeof(int32_t) * src_alloc);
     if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(g->d_src, new_src.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_outdeg, new_od.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
@@ -278,8 +283,8 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     }
     // the single-column work table is built now so that solves on this graph
     // never need to allocate it later
-    const UnitTable *t1 = nullptr;
-    if ((s = pr_graph_units(g, 1, &t1)) != PR_OK) {
+    const TileTable *t1 = nullptr;
+    if ((s = pr_graph_tiles(g, 1, &t1)) != PR_OK) {
         free_graph(g);
         return s;
     }

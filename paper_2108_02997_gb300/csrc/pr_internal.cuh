@@ -12,35 +12,35 @@
 constexpr int kBlock = 256;          // threads per CTA of every iteration kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, sum of ranks
+constexpr int kStages = 2;           // shared-memory stages of the tile pipeline
 
-// ------------------------------------------------------------------ work units
-// A unit is the work of one CTA for one pass: either up to kBlock/g rows of one
-// in-degree class, each row handled by a group of g lanes, or one chunk of the
-// in-edges of a long row, handled by the whole CTA.
-//   rows : a = first row, b = end row, c = -1,       d = log2(g)
-//   chunk: a = row,       b = first edge, c = end edge, d = long-row slot or -1
-struct Unit {
-    int32_t a, b, c, d;
+// Tile capacity for column width W: edges x columns <= 2048 gathered values,
+// rows x columns <= 512 staged rows.
+__host__ __device__ constexpr int tile_edges(int W) { return 2048 / W; }
+__host__ __device__ constexpr int tile_rows(int W) { return 512 / W; }
+
+// ------------------------------------------------------------------ work tiles
+// A tile is one CTA's work item of one pass: either a run of consecutive rows
+// of one in-degree class (at most tile_rows rows and tile_edges in-edges in
+// total), or one chunk of the in-edges of a row longer than tile_edges.
+//   rows : [r0, r1) rows, [e0, e1) = their in-edges, glog = log2(lanes per row)
+//   chunk: r0 = the row, r1 = r0 + 1, [e0, e1) = this chunk, glog = -1,
+//          slot = long-row slot (-1 when the row has one chunk), k = chunk index,
+//          nch = chunks of the row
+struct Tile {
+    int32_t r0, r1, e0, e1;
+    int32_t glog, slot, k, nch;
 };
 
-// Per-long-row bookkeeping for rows split into several chunks.
-struct LongRows {
-    int32_t count = 0;          // rows with more than one chunk
-    int32_t chunks = 0;         // total chunks over those rows
-};
-
-// ------------------------------------------------------------------ graph
-struct UnitTable {
+struct TileTable {
     int W = 0;                   // column width this table was built for
-    Unit *d_units = nullptr;
-    int32_t nunits = 0;
-    int32_t n_long = 0;          // long rows with >1 chunk
+    Tile *d_tiles = nullptr;
+    int32_t ntiles = 0;
+    int32_t n_long = 0;          // rows split into more than one chunk
     int32_t n_chunk_slots = 0;   // chunk partial slots
     int32_t *d_slot_base = nullptr;  // n_long: first chunk partial of each long row
     double work = 0.0;           // relative work estimate
 };
-
-struct pr_graph_s;
 
 struct ClassRange {
     int32_t begin, end;   // rows [begin, end) in the relabelled order
@@ -53,8 +53,8 @@ struct ClassRange {
 struct ColState {
     double alpha;
     double c0;            // teleport term of the next update (FP64)
-    double v_alpha[2];    // alpha in the job's value type (raw bits: 8 or 16 bytes used)
-    double v_c0[2];       // c0 in the job's value type
+    double v_alpha[2];    // alpha in the job's value type (raw bits: 4 or 8 bytes used)
+    double v_c0[2];       // c0 in the job's value type (init pass: the uniform start 1/N)
     int32_t active;       // 1 while the column still updates
     int32_t cur;          // buffer (0/1) holding the current iterate
     int32_t iters;        // updates performed so far
@@ -94,10 +94,10 @@ struct JobDev {
     const int32_t *src;
     const int32_t *outdeg;
     const int32_t *perm;      // relabelled -> caller id
-    const Unit *units;
+    const Tile *tiles;
     const int32_t *slot_base;
     int32_t n;
-    int32_t nunits;
+    int32_t ntiles;
     int32_t cta_begin, cta_count;
     int32_t ncols;
     int32_t alive;            // 1 while any column is active or a copy is pending
@@ -109,7 +109,7 @@ struct JobDev {
     ColState *cols;           // W
     Tap *taps;
     uint32_t arrive;          // CTAs of this job that finished the pass
-    uint32_t pad;
+    int32_t cur;              // buffer parity shared by the job's active columns
 };
 
 struct GlobalDev {
@@ -124,6 +124,9 @@ struct GlobalDev {
     uint32_t pad;
 };
 
+// Error codes a kernel can leave in GlobalDev::error.
+enum DeviceError { kErrNone = 0, kErrPassCap = 2, kErrLoopGuard = 3, kErrCopyTimeout = 4 };
+
 // ------------------------------------------------------------------ graph object
 struct pr_graph {
     uint32_t magic;
@@ -131,18 +134,21 @@ struct pr_graph {
     int64_t nnz;
     int32_t n_dangling;
     int32_t device;
-    int32_t *d_off = nullptr;
-    int32_t *d_src = nullptr;
-    int32_t *d_outdeg = nullptr;
+    int32_t *d_off = nullptr;        // n+1 (padded for 16-byte bulk copies)
+    int32_t *d_src = nullptr;        // nnz (padded)
+    int32_t *d_outdeg = nullptr;     // n (padded)
     int32_t *d_perm = nullptr;       // relabelled -> caller
     int32_t *d_inv = nullptr;        // caller -> relabelled
-    int32_t *d_indeg_orig = nullptr; // unused placeholder for future use
     std::vector<ClassRange> classes; // in-degree classes in relabelled order
-    std::vector<int32_t> h_off;      // relabelled offsets (host copy, for unit tables)
-    UnitTable tables[6];             // W = 1, 2, 4, 8, 16, 32
+    std::vector<int32_t> h_off;      // relabelled offsets (host copy, for tile tables)
+    TileTable tables[6];             // W = 1, 2, 4, 8, 16, 32
 };
 constexpr uint32_t kGraphMagic = 0x50524731u;   // "PRG1"
 constexpr uint32_t kMlpMagic = 0x50524d31u;     // "PRM1"
+
+// Elements of padding after each graph array and value buffer, so that
+// 16-byte-rounded bulk copies of any tile stay inside the allocation.
+constexpr int kPad = 8;
 
 // ------------------------------------------------------------------ errors
 void pr_set_error(const std::string &msg);
@@ -158,7 +164,7 @@ pr_status pr_cuda_fail(cudaError_t e, const char *what);
 
 // ------------------------------------------------------------------ internals
 int w_index(int W);   // 1,2,4,..,32 -> 0..5
-pr_status pr_graph_units(pr_graph *g, int W, const UnitTable **out);
+pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out);
 bool pr_graph_valid(const pr_graph *g);
 
 // Solve driver (pr_solve.cu)
@@ -182,6 +188,12 @@ struct SolveRequest {
 };
 
 pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out);
+
+// Kernel selection and launch geometry (pr_solve.cu)
+void *pr_iter_kernel_for(int precision, int W);
+void *pr_init_kernel_for(int precision, int W);
+size_t pr_tile_smem_bytes(int precision, int W);
+pr_status pr_kernel_setup(int precision, int W, int *blocks_per_sm);
 
 // Live-handle registry: guards every entry point against stale handles.
 void registry_add(const void *p);

@@ -61,15 +61,18 @@ extern "C" pr_status pr_solve_noalloc(const pr_graph *g, double alpha, double to
     if (norm < PR_NORM_L1 || norm > PR_NORM_LINF) return pr_fail(PR_EINVAL, "norm must be 1 (L1), 2 (L2) or 3 (Linf)");
     if (max_iter < 1) return pr_fail(PR_EINVAL, "max_iter must be >= 1");
     if (!d_ranks_out) return pr_fail(PR_EINVAL, "d_ranks_out is NULL");
-    const UnitTable &ut = g->tables[0];
-    if (!ut.d_units) return pr_fail(PR_ESTATE, "graph has no single-column work table");
+    const TileTable &ut = g->tables[0];
+    if (!ut.d_tiles) return pr_fail(PR_ESTATE, "graph has no single-column work table");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    void *kern = (void *)pr_iter_kernel<df64, 1>;
-    int dev = 0, sms = 0, occ = 0;
+    void *kiter = pr_iter_kernel_for(PR_PREC_DF64, 1);
+    void *kinit = pr_init_kernel_for(PR_PREC_DF64, 1);
+    const size_t smem = pr_tile_smem_bytes(PR_PREC_DF64, 1);
+    int dev = 0, sms = 0, occ = 1;
     PR_CUDA(cudaGetDevice(&dev));
     PR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, 0));
-    const int ctas = std::max(1, std::min(sms * std::max(occ, 1), std::max(ut.nunits, 1)));
+    pr_status s = pr_kernel_setup(PR_PREC_DF64, 1, &occ);
+    if (s != PR_OK) return s;
+    const int ctas = std::max(1, std::min(sms * occ, std::max(ut.ntiles, 1)));
     // ---- layout inside the scratch array
     const size_t n = (size_t)g->n;
     size_t at = 0;
@@ -82,12 +85,12 @@ extern "C" pr_status pr_solve_noalloc(const pr_graph *g, double alpha, double to
     const size_t o_cp = at; at = align256(at + sizeof(df64) * std::max(ut.n_chunk_slots, 1));
     const size_t o_cnt = at; at = align256(at + sizeof(uint32_t) * std::max(ut.n_long, 1));
     size_t o_vec[4];
-    for (int b = 0; b < 4; b++) { o_vec[b] = at; at = align256(at + sizeof(df64) * n); }
+    for (int b = 0; b < 4; b++) { o_vec[b] = at; at = align256(at + sizeof(df64) * (n + kPad)); }
     if (at > kNoAllocBytes)
         return pr_fail(PR_EINVAL, "graph needs " + std::to_string(at) + " bytes of working memory; the no-alloc scratch holds " +
                                       std::to_string(kNoAllocBytes) + " (about 32 bytes per vertex: n <= ~1.2 million)");
     void *base_v = nullptr;
-    pr_status s = noalloc_scratch(&base_v);
+    s = noalloc_scratch(&base_v);
     if (s != PR_OK) return s;
     char *base = static_cast<char *>(base_v);
     // ---- state (host structures copied into the scratch array)
@@ -97,10 +100,11 @@ extern "C" pr_status pr_solve_noalloc(const pr_graph *g, double alpha, double to
     job.src = g->d_src;
     job.outdeg = g->d_outdeg;
     job.perm = g->d_perm;
-    job.units = ut.d_units;
+    job.tiles = ut.d_tiles;
     job.slot_base = ut.d_slot_base;
     job.n = g->n;
-    job.nunits = ut.nunits;
+    job.ntiles = ut.ntiles;
+    job.cur = 0;
     job.cta_begin = 0;
     job.cta_count = ctas;
     job.ncols = 1;
@@ -146,14 +150,12 @@ extern "C" pr_status pr_solve_noalloc(const pr_graph *g, double alpha, double to
     JobDev *d_job = reinterpret_cast<JobDev *>(base + o_job);
     GlobalDev *d_glob = reinterpret_cast<GlobalDev *>(base + o_glob);
     const int32_t *d_ctajob = reinterpret_cast<const int32_t *>(base + o_ctajob);
-    int mode_init = kPassInit, mode_iter = kPassIterate;
-    void *args_init[] = {(void *)&d_job, (void *)&d_glob, (void *)&d_ctajob, (void *)&mode_init};
-    void *args_iter[] = {(void *)&d_job, (void *)&d_glob, (void *)&d_ctajob, (void *)&mode_iter};
-    PR_CUDA(cudaLaunchKernel(kern, dim3(ctas), dim3(kBlock), args_init, 0, st));
+    void *args[] = {(void *)&d_job, (void *)&d_glob, (void *)&d_ctajob};
+    PR_CUDA(cudaLaunchKernel(kinit, dim3(ctas), dim3(kBlock), args, 0, st));
     GlobalDev back;
     std::memset(&back, 0, sizeof(back));
     for (int p = 0; p < glob.pass_cap + 1; p++) {
-        PR_CUDA(cudaLaunchKernel(kern, dim3(ctas), dim3(kBlock), args_iter, 0, st));
+        PR_CUDA(cudaLaunchKernel(kiter, dim3(ctas), dim3(kBlock), args, smem, st));
         PR_CUDA(cudaMemcpyAsync(&back, d_glob, sizeof(back), cudaMemcpyDeviceToHost, st));
         PR_CUDA(cudaStreamSynchronize(st));
         if (!back.alive || back.error) break;

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 
 #include "pr_kernels.cuh"
 
@@ -18,7 +19,7 @@ namespace {
 
 struct Arena {
     char *base = nullptr;
-    size_t size = 0, used = 0;
+    size_t size = 0;
     ~Arena() { if (base) cudaFree(base); }
     size_t reserve(size_t bytes) {   // returns offset
         size_t off = (size + 255) & ~size_t(255);
@@ -40,7 +41,7 @@ struct Arena {
 };
 
 template <typename V>
-void *iter_kernel_ptr(int W) {
+void *iter_ptr(int W) {
     switch (W) {
         case 1: return (void *)pr_iter_kernel<V, 1>;
         case 2: return (void *)pr_iter_kernel<V, 2>;
@@ -50,16 +51,28 @@ void *iter_kernel_ptr(int W) {
         default: return (void *)pr_iter_kernel<V, 32>;
     }
 }
-
-void *kernel_for(int prec, int W) {
-    switch (prec) {
-        case PR_PREC_FP64: return iter_kernel_ptr<double>(W);
-        case PR_PREC_FP32: return iter_kernel_ptr<float>(W);
-        default: return iter_kernel_ptr<df64>(W);
+template <typename V>
+void *init_ptr(int W) {
+    switch (W) {
+        case 1: return (void *)pr_init_kernel<V, 1>;
+        case 2: return (void *)pr_init_kernel<V, 2>;
+        case 4: return (void *)pr_init_kernel<V, 4>;
+        case 8: return (void *)pr_init_kernel<V, 8>;
+        case 16: return (void *)pr_init_kernel<V, 16>;
+        default: return (void *)pr_init_kernel<V, 32>;
     }
 }
-
-size_t value_size(int prec) { return prec == PR_PREC_FP32 ? 4 : 8; }
+template <typename V>
+size_t smem_of(int W) {
+    switch (W) {
+        case 1: return StageLayout<V, 1>::total;
+        case 2: return StageLayout<V, 2>::total;
+        case 4: return StageLayout<V, 4>::total;
+        case 8: return StageLayout<V, 8>::total;
+        case 16: return StageLayout<V, 16>::total;
+        default: return StageLayout<V, 32>::total;
+    }
+}
 
 void store_value(double *dst, int prec, double x) {
     dst[0] = 0.0;
@@ -84,7 +97,7 @@ int pow2_at_least(int k) {
 struct HostJob {
     const pr_graph *g;
     std::vector<int> cols;           // request column indices
-    const UnitTable *ut = nullptr;
+    const TileTable *tt = nullptr;
     int cta_count = 0;
     size_t off_r[2], off_c[2], off_cp, off_cnt, off_part, off_cols, off_taps, off_hist;
     int ntaps = 0;
@@ -98,11 +111,56 @@ struct LoopStats {
     double total_ms = 0.0;
 };
 
+std::mutex g_stats_mu;
 LoopStats g_last_stats;
 
 }  // namespace
 
+void *pr_iter_kernel_for(int prec, int W) {
+    switch (prec) {
+        case PR_PREC_FP64: return iter_ptr<double>(W);
+        case PR_PREC_FP32: return iter_ptr<float>(W);
+        default: return iter_ptr<df64>(W);
+    }
+}
+void *pr_init_kernel_for(int prec, int W) {
+    switch (prec) {
+        case PR_PREC_FP64: return init_ptr<double>(W);
+        case PR_PREC_FP32: return init_ptr<float>(W);
+        default: return init_ptr<df64>(W);
+    }
+}
+size_t pr_tile_smem_bytes(int prec, int W) {
+    switch (prec) {
+        case PR_PREC_FP64: return smem_of<double>(W);
+        case PR_PREC_FP32: return smem_of<float>(W);
+        default: return smem_of<df64>(W);
+    }
+}
+
+// Opt the iteration kernel into its dynamic shared memory (once per process
+// and instantiation) and report its resident CTAs per SM.
+pr_status pr_kernel_setup(int prec, int W, int *blocks_per_sm) {
+    static std::mutex mu;
+    static bool done[4][6] = {};
+    void *k = pr_iter_kernel_for(prec, W);
+    const size_t smem = pr_tile_smem_bytes(prec, W);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        int pi = prec & 3, wi = w_index(W);
+        if (!done[pi][wi]) {
+            PR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            done[pi][wi] = true;
+        }
+    }
+    int occ = 0;
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBlock, smem));
+    *blocks_per_sm = std::max(occ, 1);
+    return PR_OK;
+}
+
 extern "C" pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms) {
+    std::lock_guard<std::mutex> lk(g_stats_mu);
     if (launches) *launches = g_last_stats.launches;
     if (passes) *passes = g_last_stats.passes;
     if (kernel_ms) *kernel_ms = g_last_stats.kernel_ms;
@@ -115,35 +173,40 @@ namespace {
 // One phase of a solve in one value type: init pass + loop of iteration passes.
 pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size_t off_jobs, size_t off_glob,
                     size_t off_ctajob, int total_ctas, int pass_cap, int loop, cudaStream_t st, LoopStats &stats) {
-    void *kern = kernel_for(prec, W);
+    void *kiter = pr_iter_kernel_for(prec, W);
+    void *kinit = pr_init_kernel_for(prec, W);
+    const size_t smem = pr_tile_smem_bytes(prec, W);
+    int occ = 0;
+    pr_status s0 = pr_kernel_setup(prec, W, &occ);
+    if (s0 != PR_OK) return s0;
     JobDev *d_jobs = ar.at<JobDev>(off_jobs);
     GlobalDev *d_glob = ar.at<GlobalDev>(off_glob);
     const int32_t *d_ctajob = ar.at<int32_t>(off_ctajob);
-    GlobalDev hg{};
+    GlobalDev hg;
+    std::memset(&hg, 0, sizeof(hg));
     hg.njobs = (int32_t)jobs.size();
     hg.pass_cap = pass_cap;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     PR_CUDA(cudaEventCreate(&ev0));
     PR_CUDA(cudaEventCreate(&ev1));
     struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{ev0, ev1};
-    int mode_init = kPassInit, mode_iter = kPassIterate;
-    void *args_init[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_ctajob, (void *)&mode_init};
-    void *args_iter[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_ctajob, (void *)&mode_iter};
+    void *args[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_ctajob};
     dim3 grid(total_ctas), block(kBlock);
     PR_CUDA(cudaEventRecord(ev0, st));
     if (loop == PR_LOOP_HOST) {
         hg.cond = 0;
         PR_CUDA(cudaMemcpyAsync(d_glob, &hg, sizeof(hg), cudaMemcpyHostToDevice, st));
-        PR_CUDA(cudaLaunchKernel(kern, grid, block, args_init, 0, st));
+        PR_CUDA(cudaLaunchKernel(kinit, grid, block, args, 0, st));
         stats.launches++;
         cudaEvent_t k0 = nullptr, k1 = nullptr;
         PR_CUDA(cudaEventCreate(&k0));
         PR_CUDA(cudaEventCreate(&k1));
         struct KGuard { cudaEvent_t a, b; ~KGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } kg{k0, k1};
-        GlobalDev back{};
+        GlobalDev back;
+        std::memset(&back, 0, sizeof(back));
         for (int p = 0; p < pass_cap + 1; p++) {
             PR_CUDA(cudaEventRecord(k0, st));
-            PR_CUDA(cudaLaunchKernel(kern, grid, block, args_iter, 0, st));
+            PR_CUDA(cudaLaunchKernel(kiter, grid, block, args, smem, st));
             PR_CUDA(cudaEventRecord(k1, st));
             stats.launches++;
             PR_CUDA(cudaMemcpyAsync(&back, d_glob, sizeof(back), cudaMemcpyDeviceToHost, st));
@@ -154,6 +217,7 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
             if (!back.alive || back.error) break;
         }
         stats.passes += back.pass;
+        if (back.error == kErrCopyTimeout) return pr_fail(PR_ETIMEOUT, "a staged tile copy did not complete in time");
         if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
     } else {
         cudaGraph_t graph = nullptr;
@@ -168,11 +232,11 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
         hg.cond = (unsigned long long)h;
         PR_CUDA(cudaMemcpyAsync(d_glob, &hg, sizeof(hg), cudaMemcpyHostToDevice, st));
         cudaKernelNodeParams kp{};
-        kp.func = kern;
+        kp.func = kinit;
         kp.gridDim = grid;
         kp.blockDim = block;
         kp.sharedMemBytes = 0;
-        kp.kernelParams = args_init;
+        kp.kernelParams = args;
         cudaGraphNode_t n_init, n_cond, n_body;
         PR_CUDA(cudaGraphAddKernelNode(&n_init, graph, nullptr, 0, &kp));
         cudaGraphNodeParams cp{};
@@ -182,15 +246,18 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
         cp.conditional.size = 1;
         PR_CUDA(cudaGraphAddNode(&n_cond, graph, &n_init, nullptr, 1, &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
-        kp.kernelParams = args_iter;
+        kp.func = kiter;
+        kp.sharedMemBytes = (unsigned int)smem;
         PR_CUDA(cudaGraphAddKernelNode(&n_body, body, nullptr, 0, &kp));
         PR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
         PR_CUDA(cudaGraphLaunch(exec, st));
-        GlobalDev back{};
+        GlobalDev back;
+        std::memset(&back, 0, sizeof(back));
         PR_CUDA(cudaMemcpyAsync(&back, d_glob, sizeof(back), cudaMemcpyDeviceToHost, st));
         PR_CUDA(cudaStreamSynchronize(st));
-        stats.launches += 1 + back.pass;
+        stats.launches += 1 + (int)back.body_count;
         stats.passes += back.pass;
+        if (back.error == kErrCopyTimeout) return pr_fail(PR_ETIMEOUT, "a staged tile copy did not complete in time");
         if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
     }
     PR_CUDA(cudaEventRecord(ev1, st));
@@ -205,7 +272,6 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
 
 pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out) {
     LoopStats stats;
-    g_last_stats = stats;
     const int ncols = (int)req.cols.size();
     if (ncols == 0) return PR_OK;
     cudaStream_t st = req.stream;
@@ -232,33 +298,33 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     }
     int W = 1;
     for (auto &j : jobs) W = std::max(W, pow2_at_least((int)j.cols.size()));
-    // ---- unit tables and CTA split
+    // ---- tile tables and CTA split
     int dev = 0;
     PR_CUDA(cudaGetDevice(&dev));
     int sms = 0;
     PR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int occ = 0;
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_for(prec1, W), kBlock, 0));
+    int occ = 1;
+    pr_status s = pr_kernel_setup(prec1, W, &occ);
+    if (s != PR_OK) return s;
     if (mixed) {
-        int occ2 = 0;
-        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kernel_for(PR_PREC_DF64, W), kBlock, 0));
+        int occ2 = 1;
+        if ((s = pr_kernel_setup(PR_PREC_DF64, W, &occ2)) != PR_OK) return s;
         occ = std::min(occ, occ2);
     }
-    occ = std::max(occ, 1);
     const int budget = sms * occ;
     double total_work = 0.0;
     for (auto &j : jobs) {
-        pr_status s = pr_graph_units(const_cast<pr_graph *>(j.g), W, &j.ut);
+        s = pr_graph_tiles(const_cast<pr_graph *>(j.g), W, &j.tt);
         if (s != PR_OK) return s;
-        total_work += std::max(j.ut->work, 1.0);
+        total_work += std::max(j.tt->work, 1.0);
     }
     int total_ctas = 0;
     for (auto &j : jobs) {
-        int want = (int)std::lround(budget * std::max(j.ut->work, 1.0) / total_work);
-        j.cta_count = std::max(1, std::min(want, std::max(j.ut->nunits, 1)));
+        int want = (int)std::lround(budget * std::max(j.tt->work, 1.0) / total_work);
+        j.cta_count = std::max(1, std::min(want, std::max(j.tt->ntiles, 1)));
         total_ctas += j.cta_count;
     }
-    // ---- workspace layout
+    // ---- workspace layout (value buffers padded for 16-byte tile copies)
     Arena ar;
     const size_t vs_max = 8;
     int max_iter_all = 1;
@@ -267,11 +333,11 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     for (auto &j : jobs) {
         const size_t n = (size_t)j.g->n;
         for (int b = 0; b < 2; b++) {
-            j.off_r[b] = ar.reserve(n * W * vs_max);
-            j.off_c[b] = ar.reserve(n * W * vs_max);
+            j.off_r[b] = ar.reserve((n * W + kPad) * vs_max);
+            j.off_c[b] = ar.reserve((n * W + kPad) * vs_max);
         }
-        j.off_cp = ar.reserve((size_t)std::max(j.ut->n_chunk_slots, 1) * W * vs_max);
-        j.off_cnt = ar.reserve((size_t)std::max(j.ut->n_long, 1) * sizeof(uint32_t));
+        j.off_cp = ar.reserve((size_t)std::max(j.tt->n_chunk_slots, 1) * W * vs_max);
+        j.off_cnt = ar.reserve((size_t)std::max(j.tt->n_long, 1) * sizeof(uint32_t));
         j.off_part = ar.reserve((size_t)j.cta_count * W * kPartials * sizeof(double));
         j.off_cols = ar.reserve((size_t)W * sizeof(ColState));
         for (int c : j.cols) j.ntaps += (int)req.cols[c].taps.size();
@@ -284,8 +350,8 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     std::vector<size_t> off_r32;
     if (mixed)
         for (auto &j : jobs) {
-            off_r32.push_back(ar.reserve((size_t)j.g->n * W * 4));
-            off_r32.push_back(ar.reserve((size_t)j.g->n * W * 4));
+            off_r32.push_back(ar.reserve(((size_t)j.g->n * W + kPad) * 4));
+            off_r32.push_back(ar.reserve(((size_t)j.g->n * W + kPad) * 4));
         }
     // staging for host outputs: taps whose out is null get a device buffer
     std::vector<size_t> stage_off;
@@ -295,7 +361,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     const size_t off_jobs = ar.reserve(jobs.size() * sizeof(JobDev));
     const size_t off_glob = ar.reserve(sizeof(GlobalDev));
     const size_t off_ctajob = ar.reserve((size_t)total_ctas * sizeof(int32_t));
-    pr_status s = ar.alloc();
+    s = ar.alloc();
     if (s != PR_OK) return s;
     // ---- fill job and column state on the host
     std::vector<JobDev> hjobs(jobs.size());
@@ -303,7 +369,6 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     std::vector<std::vector<ColState>> hcols(jobs.size());
     std::vector<std::vector<Tap>> htaps(jobs.size());
     size_t stage_i = 0;
-    std::vector<std::vector<double *>> col_stage_ptrs(ncols);
     int cta_at = 0;
     for (size_t ji = 0; ji < jobs.size(); ji++) {
         HostJob &j = jobs[ji];
@@ -313,16 +378,17 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         d.src = j.g->d_src;
         d.outdeg = j.g->d_outdeg;
         d.perm = j.g->d_perm;
-        d.units = j.ut->d_units;
-        d.slot_base = j.ut->d_slot_base;
+        d.tiles = j.tt->d_tiles;
+        d.slot_base = j.tt->d_slot_base;
         d.n = j.g->n;
-        d.nunits = j.ut->nunits;
+        d.ntiles = j.tt->ntiles;
         d.cta_begin = cta_at;
         d.cta_count = j.cta_count;
         for (int q = 0; q < j.cta_count; q++) ctajob[cta_at + q] = (int32_t)ji;
         cta_at += j.cta_count;
         d.ncols = (int32_t)j.cols.size();
         d.alive = 1;
+        d.cur = 0;
         if (mixed) {
             d.r[0] = ar.at<void>(off_r32[2 * ji]);
             d.r[1] = ar.at<void>(off_r32[2 * ji + 1]);
@@ -353,10 +419,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
                 Tap tt = t;
                 tt.fired = 0;
                 tt.alias_of = -1;
-                if (!tt.out) {
-                    tt.out = ar.at<double>(stage_off[stage_i++]);
-                }
-                col_stage_ptrs[j.cols[k]].push_back(tt.out);
+                if (!tt.out) tt.out = ar.at<double>(stage_off[stage_i++]);
                 htaps[ji].push_back(tt);
                 tap_at++;
             }
@@ -381,7 +444,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         cudaError_t e = cudaMemcpyAsync(d.cols, hcols[ji].data(), W * sizeof(ColState), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess && !htaps[ji].empty())
             e = cudaMemcpyAsync(d.taps, htaps[ji].data(), htaps[ji].size() * sizeof(Tap), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(d.chunk_cnt, 0, (size_t)std::max(j.ut->n_long, 1) * sizeof(uint32_t), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.chunk_cnt, 0, (size_t)std::max(j.tt->n_long, 1) * sizeof(uint32_t), st);
         if (e != cudaSuccess) return pr_cuda_fail(e, "workspace upload");
     }
     PR_CUDA(cudaMemcpyAsync(ar.at<JobDev>(off_jobs), hjobs.data(), hjobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice, st));
@@ -421,6 +484,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             hjobs[ji].r[1] = ar.at<void>(j.off_r[1]);
             hjobs[ji].alive = 1;
             hjobs[ji].arrive = 0;
+            hjobs[ji].cur = 0;
             PR_CUDA(cudaMemcpyAsync(hjobs[ji].cols, back.data(), W * sizeof(ColState), cudaMemcpyHostToDevice, st));
         }
         if (any) {
@@ -430,7 +494,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             if (s != PR_OK) return s;
         }
     }
-    // ---- results: taps, aliases, histories
+    // ---- results: taps, aliases, host copies, histories
     tap_out.assign(ncols, {});
     for (size_t ji = 0; ji < jobs.size(); ji++) {
         HostJob &j = jobs[ji];
@@ -463,6 +527,9 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         }
     }
     PR_CUDA(cudaStreamSynchronize(st));
-    g_last_stats = stats;
+    {
+        std::lock_guard<std::mutex> lk(g_stats_mu);
+        g_last_stats = stats;
+    }
     return PR_OK;
 }
