@@ -12,12 +12,12 @@
 constexpr int kBlock = 256;          // threads per CTA of every iteration kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, sum of ranks
-constexpr int kStages = 2;           // shared-memory stages of the tile pipeline
+constexpr int kStages = 3;           // shared-memory stages of the tile pipeline
 
-// Tile capacity for column width W: edges x columns <= 2048 gathered values,
-// rows x columns <= 512 staged rows.
-__host__ __device__ constexpr int tile_edges(int W) { return 2048 / W; }
-__host__ __device__ constexpr int tile_rows(int W) { return 512 / W; }
+// Tile capacity for column width W: edges x columns <= 1024 gathered values,
+// rows x columns <= 256 staged rows.
+__host__ __device__ constexpr int tile_edges(int W) { return 1024 / W; }
+__host__ __device__ constexpr int tile_rows(int W) { return 256 / W; }
 
 // ------------------------------------------------------------------ work tiles
 // A tile is one CTA's work item of one pass: either a run of consecutive rows

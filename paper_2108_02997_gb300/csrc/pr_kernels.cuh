@@ -81,6 +81,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Element-wise asynchronous copies global -> shared (LDGSTS): the random
+// gathers of a tile are issued this way so that a whole tile's worth stays in
+// flight without occupying registers. .ca keeps the lines in L1.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_ca(void *dst, const void *src) {
+    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -113,7 +125,7 @@ struct StageLayout {
     static constexpr size_t bytes_rp = ((size_t)(TR * W + 8) * sizeof(V) + 15) / 16 * 16;
     static constexpr size_t stage_bytes = bytes_src + bytes_off + bytes_od + bytes_rp;
     static constexpr size_t vals_bytes = (size_t)TE * W * sizeof(V);
-    static constexpr size_t total = kStages * stage_bytes + vals_bytes + 8 * kStages;
+    static constexpr size_t total = kStages * stage_bytes + 2 * vals_bytes + 8 * kStages;
 };
 
 template <typename V>
@@ -385,8 +397,12 @@ __global__ void __launch_bounds__(kBlock) pr_init_kernel(JobDev *jobs, GlobalDev
 }
 
 // ---------------------------------------------------------------- the iteration kernel
+// Per CTA, tiles flow through three steps, each one tile ahead of the next:
+//   k+2 : bulk copy of indices/offsets/out-degrees/previous ranks (TMA engine)
+//   k+1 : random gathers contrib[src] -> vals[(k+1) % 2] with cp.async
+//   k   : row sums from vals[k % 2], new ranks, norms (this tile)
 template <typename V, int W>
-__global__ void __launch_bounds__(kBlock) pr_iter_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
+__global__ void __launch_bounds__(kBlock, 4) pr_iter_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
     using N = Num<V>;
     using L = StageLayout<V, W>;
     static_assert(32 % W == 0, "W must divide the warp");
@@ -397,8 +413,8 @@ __global__ void __launch_bounds__(kBlock) pr_iter_kernel(JobDev *jobs, GlobalDev
     const int local = blockIdx.x - job.cta_begin;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    V *vals = reinterpret_cast<V *>(smem + kStages * L::stage_bytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * L::stage_bytes + L::vals_bytes);
+    V *vals0 = reinterpret_cast<V *>(smem + kStages * L::stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * L::stage_bytes + 2 * L::vals_bytes);
     __shared__ Tile s_tile[kStages];
     __shared__ int s_fail;
     __shared__ V s_chunk[kWarps][W];
@@ -430,7 +446,7 @@ __global__ void __launch_bounds__(kBlock) pr_iter_kernel(JobDev *jobs, GlobalDev
     __syncthreads();
 
     // Thread 0 stages the CTA's k-th tile into stage k % kStages.
-    auto issue = [&](int k) {
+    auto stage_tile = [&](int k) {
         const int s = k % kStages;
         const Tile T = job.tiles[local + (size_t)k * job.cta_count];
         s_tile[s] = T;
@@ -449,47 +465,47 @@ __global__ void __launch_bounds__(kBlock) pr_iter_kernel(JobDev *jobs, GlobalDev
         bulk_copy_g2s(st + L::bytes_src + L::bytes_off, job.outdeg + da, b_od, &bars[s]);
         bulk_copy_g2s(st + L::bytes_src + L::bytes_off + L::bytes_od, rp_base + ra, b_rp, &bars[s]);
     };
+    // All threads: wait for tile k's staged data, then issue its gathers.
+    auto gather_tile = [&](int k) -> bool {
+        const int s = k % kStages;
+        if (!mbar_wait_bounded(&bars[s], (uint32_t)((k / kStages) & 1))) return false;
+        const Tile &T = s_tile[s];
+        const int32_t *s_src = reinterpret_cast<const int32_t *>(smem + s * L::stage_bytes) + (T.e0 & 3);
+        V *vals = vals0 + (size_t)(k & 1) * (L::vals_bytes / sizeof(V));
+        const int nv = (T.e1 - T.e0) * W;
+        if (cv.active) {
+            const V *cp = cv.c_prev;
+            for (int idx = tid; idx < nv; idx += kBlock)
+                cp_async_ca<sizeof(V)>(vals + idx, cp + (size_t)s_src[idx / W] * W + col);
+        }
+        cp_async_commit();
+        return true;
+    };
 
     if (tid == 0)
-        for (int k = 0; k < kStages - 1 && k < ntl; k++) issue(k);
+        for (int k = 0; k < 2 && k < ntl; k++) stage_tile(k);
+    if (ntl > 0 && !gather_tile(0)) s_fail = 1;
 
     int k = 0;
     for (; k < ntl; k++) {
-        const int s = k % kStages;
-        if (tid == 0 && k + kStages - 1 < ntl) issue(k + kStages - 1);
-        if (!mbar_wait_bounded(&bars[s], (uint32_t)((k / kStages) & 1))) s_fail = 1;
+        if (tid == 0 && k + 2 < ntl) stage_tile(k + 2);
+        if (k + 1 < ntl) {
+            if (!gather_tile(k + 1)) s_fail = 1;
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();
         if (s_fail) break;
+        const int s = k % kStages;
         const Tile T = s_tile[s];
         const unsigned char *st = smem + s * L::stage_bytes;
-        const int32_t *s_src = reinterpret_cast<const int32_t *>(st) + (T.e0 & 3);
         const int32_t *s_off = reinterpret_cast<const int32_t *>(st + L::bytes_src) + (T.r0 & 3);
         const int32_t *s_od = reinterpret_cast<const int32_t *>(st + L::bytes_src + L::bytes_off) + (T.r0 & 3);
         const V *s_rp = reinterpret_cast<const V *>(st + L::bytes_src + L::bytes_off + L::bytes_od) +
                         ((long long)T.r0 * W - ((long long)T.r0 * W) / E16 * E16);
-        // ---- gather phase: every in-edge value of the tile into vals[edge * W + col]
+        const V *vals = vals0 + (size_t)(k & 1) * (L::vals_bytes / sizeof(V));
         const int nv = (T.e1 - T.e0) * W;
-        if (cv.active) {
-            const V *cp = cv.c_prev;
-            constexpr int kBatch = 8;
-            for (int base = tid; base < nv; base += kBlock * kBatch) {
-                int32_t u[kBatch];
-#pragma unroll
-                for (int j = 0; j < kBatch; j++) {
-                    const int idx = base + j * kBlock;
-                    u[j] = idx < nv ? s_src[idx / W] : -1;
-                }
-                V x[kBatch];
-#pragma unroll
-                for (int j = 0; j < kBatch; j++) x[j] = u[j] >= 0 ? cp[(size_t)u[j] * W + col] : N::zero();
-#pragma unroll
-                for (int j = 0; j < kBatch; j++) {
-                    const int idx = base + j * kBlock;
-                    if (idx < nv) vals[idx] = x[j];
-                }
-            }
-        }
-        __syncthreads();
         if (T.glog >= 0) {
             // ---- rows: g lanes per row add the row's values from shared memory
             const int g = 1 << T.glog;
@@ -549,14 +565,15 @@ __global__ void __launch_bounds__(kBlock) pr_iter_kernel(JobDev *jobs, GlobalDev
                 }
             }
         }
-        __syncthreads();   // stage s and vals are free again
+        __syncthreads();   // stage k % kStages and vals[k % 2] are free again
     }
     if (s_fail) {
-        // a staged copy did not arrive in time: wait (bounded) for this CTA's
-        // other copies in flight, record the error, skip the remaining tiles
-        // and still take part in the pass bookkeeping
+        // a staged copy did not arrive in time: let this CTA's element copies
+        // land, wait (bounded) for its bulk copies in flight, record the error,
+        // skip the remaining tiles and still take part in the pass bookkeeping
+        cp_async_wait<0>();
         if (tid == 0) {
-            for (int j = k + 1; j < ntl && j < k + kStages; j++)
+            for (int j = k + 1; j < ntl && j < k + 3; j++)
                 mbar_wait_bounded(&bars[j % kStages], (uint32_t)((j / kStages) & 1));
             glob->error = kErrCopyTimeout;
         }

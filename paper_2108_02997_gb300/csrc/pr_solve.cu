@@ -353,11 +353,13 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             off_r32.push_back(ar.reserve(((size_t)j.g->n * W + kPad) * 4));
             off_r32.push_back(ar.reserve(((size_t)j.g->n * W + kPad) * 4));
         }
-    // staging for host outputs: taps whose out is null get a device buffer
+    // staging for host outputs: taps whose out is null get a device buffer,
+    // reserved in the order the job loop below hands them out
     std::vector<size_t> stage_off;
-    for (auto &c : req.cols)
-        for (auto &t : c.taps)
-            if (!t.out) stage_off.push_back(ar.reserve((size_t)c.g->n * sizeof(double)));
+    for (auto &j : jobs)
+        for (int c : j.cols)
+            for (auto &t : req.cols[c].taps)
+                if (!t.out) stage_off.push_back(ar.reserve((size_t)j.g->n * sizeof(double)));
     const size_t off_jobs = ar.reserve(jobs.size() * sizeof(JobDev));
     const size_t off_glob = ar.reserve(sizeof(GlobalDev));
     const size_t off_ctajob = ar.reserve((size_t)total_ctas * sizeof(int32_t));

@@ -1,0 +1,124 @@
+"""GPU parity of the batched paths: the alpha x tau x norm sweep (Sections 2-4)
+as one batch, with and without shared trajectories; many graphs in one batch;
+mixed precision and FP32 against the error bound of the L1 contraction."""
+import numpy as np
+import pytest
+
+from tests.parity import assert_fp64_parity, bound_l1, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2108_02997_gb300 import binding
+    binding.lib()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def er(gg):
+    return gg.erdos_renyi_10k(seed=1)
+
+
+def _sweep_specs(alphas, taus):
+    return [(a, t, nm) for a in alphas for t in taus for nm in (1, 2, 3)]
+
+
+def _oracle_sweep(orc, g, specs, max_iter=500):
+    out = {}
+    for a in sorted({s[0] for s in specs}):
+        mine = [s for s in specs if s[0] == a]
+        res = orc.pagerank_taps(g, a, [(t, nm, max_iter) for _, t, nm in mine])
+        for s, r in zip(mine, res):
+            out[s] = r
+    return out
+
+
+@pytest.mark.parametrize("share", [True, False])
+def test_sweep_matches_oracle(B, orc, er, share):
+    specs = _sweep_specs([0.5, 0.85, 1.0], [1e-2, 1e-6, 1e-10])
+    ref = _oracle_sweep(orc, er, specs)
+    with B.Graph.from_csr(er) as dg:
+        insts = [B.Instance(dg, a, t, nm, 500) for a, t, nm in specs]
+        B.pr_solve_batch(insts, share=share)
+        for (a, t, nm), x in zip(specs, insts):
+            assert x.status == 0
+            assert_fp64_parity(x.out, x.iters, x.err, ref[(a, t, nm)], t, nm, f"alpha {a} tau {t} norm {nm} share {share}")
+
+
+def test_full_330_sweep(B, orc, er):
+    """The paper's alpha sweep (0.50..1.00 step .05) x tau 1e-1..1e-10 x three
+    norms: 330 instances in one call, cap 500."""
+    alphas = [round(0.5 + 0.05 * i, 2) for i in range(11)]
+    specs = _sweep_specs(alphas, [10.0 ** -k for k in range(1, 11)])
+    ref = _oracle_sweep(orc, er, specs)
+    with B.Graph.from_csr(er) as dg:
+        insts = [B.Instance(dg, a, t, nm, 500) for a, t, nm in specs]
+        B.pr_solve_batch(insts)
+        for (a, t, nm), x in zip(specs, insts):
+            assert_fp64_parity(x.out, x.iters, x.err, ref[(a, t, nm)], t, nm, f"alpha {a} tau {t} norm {nm}")
+        # the paper's trends (Sections 2-4) hold on this graph
+        it = {s: x.iters for s, x in zip(specs, insts)}
+        for a in alphas:
+            for t in [10.0 ** -k for k in range(1, 11)]:
+                assert it[(a, t, 3)] <= it[(a, t, 2)] <= it[(a, t, 1)]
+
+
+def test_many_graphs_one_batch(B, orc, gg):
+    graphs = [gg.rmat(9 + (i % 5), 16, seed=500 + i) for i in range(10)]
+    dgs = [B.Graph.from_csr(g) for g in graphs]
+    insts = [B.Instance(d, 0.85, 1e-10, 1, 500) for d in dgs]
+    B.pr_solve_batch(insts)
+    for g, x in zip(graphs, insts):
+        ref = orc.pagerank(g, 0.85, 1e-10, 1, 500, history=True)
+        assert_fp64_parity(x.out, x.iters, x.err, ref, 1e-10, 1, g.name)
+    for d in dgs:
+        d.close()
+
+
+def test_mixed_graphs_and_columns(B, orc, gg):
+    g1 = gg.rmat(12, 16, seed=31)
+    g2 = gg.erdos_renyi(3000, 20000, 100, 32)
+    d1, d2 = B.Graph.from_csr(g1), B.Graph.from_csr(g2)
+    specs = [(d1, g1, 0.7, 1e-8, 2), (d2, g2, 0.9, 1e-9, 1), (d1, g1, 0.85, 1e-7, 3), (d2, g2, 0.6, 1e-6, 3)]
+    insts = [B.Instance(d, a, t, nm, 500) for d, _, a, t, nm in specs]
+    B.pr_solve_batch(insts)
+    for (d, g, a, t, nm), x in zip(specs, insts):
+        ref = orc.pagerank(g, a, t, nm, 500, history=True)
+        assert_fp64_parity(x.out, x.iters, x.err, ref, t, nm, f"{g.name} alpha {a}")
+    d1.close(); d2.close()
+
+
+@pytest.mark.parametrize("alpha", [0.85, 0.95])
+def test_mixed_precision_error_bound(B, orc, gg, alpha):
+    g = gg.rmat(16, 16, seed=24)
+    ref = orc.pagerank(g, alpha, 1e-13, 1, 10000, threads=orc.default_threads())
+    with B.Graph.from_csr(g) as dg:
+        insts = [B.Instance(dg, alpha, t, nm, 500) for t in (1e-4, 1e-8, 1e-10) for nm in (1, 2, 3)]
+        B.pr_solve_batch(insts, precision="mixed")
+        for x in insts:
+            assert x.converged
+            err = np.abs(x.out - ref.ranks).sum()
+            assert err <= bound_l1(alpha, x.tol, x.norm, x.err_l1), (x.tol, x.norm, err)
+        # a tight tau is reached by the refinement phase: close to the FP64 answer
+        tight = [x for x in insts if x.tol == 1e-10 and x.norm == 1][0]
+        assert rel_l1(tight.out, ref.ranks) < 1e-8
+
+
+def test_fp32_error_bound(B, orc, er):
+    ref = orc.pagerank(er, 0.85, 1e-13, 1, 10000)
+    with B.Graph.from_csr(er) as dg:
+        x = B.Instance(dg, 0.85, 1e-5, 1, 500)
+        B.pr_solve_batch([x], precision="fp32")
+        assert x.converged
+        assert np.abs(x.out - ref.ranks).sum() <= bound_l1(0.85, 1e-5, 1, x.err_l1)
+
+
+def test_invalid_instance_reports_its_status(B, er):
+    with B.Graph.from_csr(er) as dg:
+        good = B.Instance(dg, 0.85, 1e-6, 1, 500)
+        bad = B.Instance(dg, 1.5, 1e-6, 1, 500)
+        st = B.pr_solve_batch([good, bad], check=False)
+        assert st == B.PR_EINVAL and bad.status == B.PR_EINVAL
+        assert good.status == 0 and good.converged
