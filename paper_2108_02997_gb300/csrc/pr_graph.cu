@@ -79,11 +79,12 @@ int w_index(int W) {
 bool pr_graph_valid(const pr_graph *g) { return g && registry_has(g) && g->magic == kGraphMagic; }
 
 // Tiles of width W (see Tile in pr_internal.cuh). Rows of one in-degree class
-// are packed into tiles of at most tile_rows(W) rows and tile_edges(W)
+// are packed into warp tiles of at most tile_rows(W) rows and tile_edges(W)
 // in-edges; the lanes of a group (g = es * W lanes, es in-edge slots of W
-// columns each) share one row in the summation phase, es sized so that each
-// slot adds about four gathered values. Rows longer than tile_edges(W) are
-// split into chunks handled by a whole CTA.
+// columns each) share one row when the row sums are formed, es sized so that
+// each slot adds about four values. Classes with rows longer than
+// tile_edges(W) are cut into chunks of chunk_edges(W) in-edges, each chunk a
+// warp's tile.
 pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     int wi = w_index(W);
     if (wi < 0) return pr_fail(PR_EINVAL, "unsupported column width");
@@ -92,7 +93,7 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
         *out = &t;
         return PR_OK;
     }
-    const int TE = tile_edges(W), TR = tile_rows(W);
+    const int TE = tile_edges(W), TR = tile_rows(W), CH = chunk_edges(W);
     const int max_es = 32 / W;
     std::vector<Tile> tiles;
     std::vector<int32_t> slot_base;
@@ -105,7 +106,7 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
             for (int32_t v = cr.begin; v < cr.end; v++) {
                 int32_t e0 = off[v], e1 = off[v + 1];
                 int32_t deg = e1 - e0;
-                int32_t nch = std::max<int32_t>(1, (deg + TE - 1) / TE);
+                int32_t nch = std::max<int32_t>(1, (deg + CH - 1) / CH);
                 int32_t slot = -1;
                 if (nch > 1) {
                     slot = (int32_t)slot_base.size();
@@ -113,7 +114,7 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
                     n_chunk_slots += nch;
                 }
                 for (int32_t k = 0; k < nch; k++) {
-                    int32_t a = e0 + k * TE, b = std::min(e1, a + TE);
+                    int32_t a = e0 + k * CH, b = std::min(e1, a + CH);
                     tiles.push_back({v, v + 1, a, b, -1, slot, k, nch});
                 }
                 work += (double)deg * W + W * 4.0;

@@ -12,15 +12,28 @@
 constexpr int kBlock = 256;          // threads per CTA of every iteration kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, sum of ranks
-constexpr int kStages = 3;           // shared-memory stages of the tile pipeline
-
-// Tile capacity for column width W: edges x columns <= 1024 gathered values,
-// rows x columns <= 256 staged rows.
-__host__ __device__ constexpr int tile_edges(int W) { return 1024 / W; }
-__host__ __device__ constexpr int tile_rows(int W) { return 256 / W; }
+// Warp tiles: a rows tile holds at most kTileValues gathered values (in-edges
+// x columns) and tile_rows(W) rows; longer rows are cut into chunks of
+// chunk_edges(W) in-edges, which one warp strides through kTileValues values
+// at a time. The three sizes are compile-time tuning constants.
+#ifndef PR_TILE_VALUES
+#define PR_TILE_VALUES 256
+#endif
+#ifndef PR_CHUNK_VALUES
+#define PR_CHUNK_VALUES 4096
+#endif
+#ifndef PR_MIN_BLOCKS
+#define PR_MIN_BLOCKS 3
+#endif
+constexpr int kTileValues = PR_TILE_VALUES;
+constexpr int kChunkValues = PR_CHUNK_VALUES;
+constexpr int kMinBlocks = PR_MIN_BLOCKS;
+__host__ __device__ constexpr int tile_edges(int W) { return kTileValues / W; }
+__host__ __device__ constexpr int tile_rows(int W) { return 128 / W; }
+__host__ __device__ constexpr int chunk_edges(int W) { return kChunkValues / W; }
 
 // ------------------------------------------------------------------ work tiles
-// A tile is one CTA's work item of one pass: either a run of consecutive rows
+// A tile is one warp's work item of one pass: either a run of consecutive rows
 // of one in-degree class (at most tile_rows rows and tile_edges in-edges in
 // total), or one chunk of the in-edges of a row longer than tile_edges.
 //   rows : [r0, r1) rows, [e0, e1) = their in-edges, glog = log2(lanes per row)
@@ -125,7 +138,7 @@ struct GlobalDev {
 };
 
 // Error codes a kernel can leave in GlobalDev::error.
-enum DeviceError { kErrNone = 0, kErrPassCap = 2, kErrLoopGuard = 3, kErrCopyTimeout = 4 };
+enum DeviceError { kErrNone = 0, kErrPassCap = 2, kErrLoopGuard = 3 };
 
 // ------------------------------------------------------------------ graph object
 struct pr_graph {

@@ -2,36 +2,31 @@
 //
 // One launch of pr_iter_kernel performs one update of every active column of
 // every job (Section 2) and decides, on the device, which columns stop
-// (Sections 3-4):
+// (Sections 3-4). Work is cut into warp tiles; every warp runs its tiles
+// independently (no block-wide barrier until the end of the pass):
 //
-//   for each tile of rows (grid-stride over the job's tiles):
-//     stage the tile's in-edge indices, row offsets, out-degrees and previous
-//       ranks in shared memory with bulk asynchronous copies (cp.async.bulk,
-//       completion counted on an mbarrier), the next tile's copies in flight
-//       while this one is computed;
-//     gather contrib[u] = r[u]/d_u for every in-edge of the tile (a batch of
-//       gathers issued before any is consumed);
-//     s      = sum of the gathered values of each row               (SpMV)
-//     r'[v]  = c0 + alpha * s                                        (new rank)
+//   rows tile (a run of rows of one in-degree class, at most 128 gathered
+//   values): coalesced loads of the tile's in-edge indices and row offsets,
+//   four independent gathers contrib[u] = r[u]/d_u per lane into a per-warp
+//   shared buffer, then lane groups add each row's values:
+//     r'[v]  = c0 + alpha * sum                                    (SpMV)
 //     accumulate |r'-r|, (r'-r)^2, max|r'-r|                         (norms)
 //     contrib'[v] = r'[v]/d_v, or add r'[v] to the dangling sum when d_v = 0
-//   the last CTA of a job reduces the CTA partials in a fixed order (FP64),
-//   forms L1, L2 = sqrt(sum of squares) and Linf, applies every pending
-//   stopping rule of each column, and computes c0 = (1-alpha)/N + alpha*D/N
-//   for the next update;
-//   the last job to finish decides whether another pass is needed and, inside
-//   a CUDA graph, ends the graph's while-loop through its conditional handle.
+//   chunk tile (part of a long row): the warp strides over the chunk with four
+//   gathers in flight per lane; the last chunk of a row to finish adds the
+//   chunk sums in chunk order and updates the row.
 //
-// Every wait on an mbarrier is bounded: past kWaitNs the CTA records
-// kErrCopyTimeout, drops its remaining tiles and still reports to the pass
-// bookkeeping, so the host gets PR_ETIMEOUT instead of a hung device.
+// At the end of the pass the last CTA of a job reduces the CTA partials in a
+// fixed order (FP64), forms L1, L2 = sqrt(sum of squares) and Linf, applies
+// every pending stopping rule of each column, and computes
+// c0 = (1-alpha)/N + alpha*D/N for the next update; the last job decides
+// whether another pass is needed and, inside a CUDA graph, ends the graph's
+// while-loop through its conditional handle.
 #pragma once
 #include "df64.cuh"
 #include "pr_internal.cuh"
 
 enum PassMode { kPassInit = 0, kPassIterate = 1 };
-
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per staged tile
 
 // ---------------------------------------------------------------- small helpers
 template <typename V>
@@ -52,81 +47,6 @@ template <> __device__ __forceinline__ df64 ld_cg_v<df64>(const df64 *p) {
     float2 f = __ldcg(reinterpret_cast<const float2 *>(p));
     return {f.x, f.y};
 }
-
-// ---------------------------------------------------------------- bulk copies and mbarriers (PTX)
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-// One 1-D bulk copy global -> shared; both addresses 16-byte aligned, bytes a
-// non-zero multiple of 16. Completion is counted on the mbarrier.
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Element-wise asynchronous copies global -> shared (LDGSTS): the random
-// gathers of a tile are issued this way so that a whole tile's worth stays in
-// flight without occupying registers. .ca keeps the lines in L1.
-template <int BYTES>
-__device__ __forceinline__ void cp_async_ca(void *dst, const void *src) {
-    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Bounded wait: true when the phase completed, false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > kWaitNs) return false;
-    }
-    return true;
-}
-
-// ---------------------------------------------------------------- shared-memory layout
-// per stage:
-//   src : tile_edges + 8 int32   (in-edge indices from a 16-byte-aligned start)
-//   off : tile_rows + 8 int32    (offsets r0..r1)
-//   od  : tile_rows + 8 int32    (out-degrees)
-//   rp  : tile_rows * W + 8 values (previous ranks)
-// then vals (tile_edges * W gathered values) and the stage mbarriers.
-template <typename V, int W>
-struct StageLayout {
-    static constexpr int TE = tile_edges(W);
-    static constexpr int TR = tile_rows(W);
-    static constexpr size_t bytes_src = (size_t)(TE + 8) * 4;
-    static constexpr size_t bytes_off = (size_t)(TR + 8) * 4;
-    static constexpr size_t bytes_od = (size_t)(TR + 8) * 4;
-    static constexpr size_t bytes_rp = ((size_t)(TR * W + 8) * sizeof(V) + 15) / 16 * 16;
-    static constexpr size_t stage_bytes = bytes_src + bytes_off + bytes_od + bytes_rp;
-    static constexpr size_t vals_bytes = (size_t)TE * W * sizeof(V);
-    static constexpr size_t total = kStages * stage_bytes + 2 * vals_bytes + 8 * kStages;
-};
 
 template <typename V>
 struct RowAcc {
@@ -175,12 +95,11 @@ __device__ __forceinline__ ColView<V> col_view(const JobDev &job, int col) {
 }
 
 // New rank of row v in the thread's column: norms, contribution or dangling
-// sum; and the copy of the current iterate into a stopping rule's output.
-// `prev` is the staged previous rank (valid for active columns, whose buffer
-// parity is the job's).
+// sum; and the copy of the column's current iterate into a stopping rule's
+// output when one fired in the previous pass.
 template <typename V, int W>
-__device__ __forceinline__ void row_update(const JobDev &job, const ColView<V> &cv, RowAcc<V> &acc, int32_t v,
-                                           int col, V s, V prev, int32_t d) {
+__device__ __forceinline__ void row_update_pd(const int32_t *__restrict__ perm, const ColView<V> &cv, RowAcc<V> &acc,
+                                              int32_t v, int col, V s, V prev, int32_t d) {
     using N = Num<V>;
     const size_t idx = (size_t)v * W + col;
     if (cv.active) {
@@ -195,7 +114,30 @@ __device__ __forceinline__ void row_update(const JobDev &job, const ColView<V> &
         acc.rsum = N::acc_add(acc.rsum, N::acc_of(rn));
         cv.r_new[idx] = rn;
     }
-    if (cv.copy_dst) cv.copy_dst[job.perm[v]] = N::to_double(cv.active ? prev : cv.r_prev[idx]);
+    if (cv.copy_dst) cv.copy_dst[perm[v]] = N::to_double(prev);
+}
+
+template <typename V, int W>
+__device__ __forceinline__ void row_update(const int32_t *__restrict__ outdeg, const int32_t *__restrict__ perm,
+                                           const ColView<V> &cv, RowAcc<V> &acc, int32_t v, int col, V s) {
+    using N = Num<V>;
+    const size_t idx = (size_t)v * W + col;
+    if (!cv.active && !cv.copy_dst) return;
+    const V prev = cv.r_prev[idx];
+    if (cv.active) {
+        V rn = N::axpy(cv.alpha, s, cv.c0);
+        V dlt = N::sub(rn, prev);
+        auto ad = N::acc_abs(dlt);
+        acc.l1 = N::acc_add(acc.l1, ad);
+        acc.l2 = N::acc_add(acc.l2, N::acc_sqr(ad));
+        acc.linf = N::acc_max(acc.linf, ad);
+        const int32_t d = outdeg[v];
+        if (d == 0) acc.dsum = N::acc_add(acc.dsum, N::acc_of(rn));
+        else cv.c_new[idx] = N::div_int(rn, d);
+        acc.rsum = N::acc_add(acc.rsum, N::acc_of(rn));
+        cv.r_new[idx] = rn;
+    }
+    if (cv.copy_dst) cv.copy_dst[perm[v]] = N::to_double(prev);
 }
 
 // ---------------------------------------------------------------- pass bookkeeping
@@ -397,28 +339,34 @@ __global__ void __launch_bounds__(kBlock) pr_init_kernel(JobDev *jobs, GlobalDev
 }
 
 // ---------------------------------------------------------------- the iteration kernel
-// Per CTA, tiles flow through three steps, each one tile ahead of the next:
-//   k+2 : bulk copy of indices/offsets/out-degrees/previous ranks (TMA engine)
-//   k+1 : random gathers contrib[src] -> vals[(k+1) % 2] with cp.async
-//   k   : row sums from vals[k % 2], new ranks, norms (this tile)
 template <typename V, int W>
-__global__ void __launch_bounds__(kBlock, 4) pr_iter_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
+__global__ void __launch_bounds__(kBlock, kMinBlocks) pr_iter_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
     using N = Num<V>;
-    using L = StageLayout<V, W>;
     static_assert(32 % W == 0, "W must divide the warp");
-    constexpr int E16 = 16 / (int)sizeof(V);   // values per 16 bytes
+    constexpr int VT = kTileValues;          // gathered values per warp tile
+    constexpr int TR = tile_rows(W);
+    constexpr int PER = VT / 32;             // gathers in flight per lane
     const int tid = threadIdx.x;
-    const int col = tid % W;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int col = tid % W;                 // equals lane % W
     JobDev &job = jobs[cta_job[blockIdx.x]];
+    // The job's fields are read once into registers: reads through `job` would
+    // be repeated after every global store, which the compiler must assume
+    // could alias the descriptor.
     const int local = blockIdx.x - job.cta_begin;
-
-    extern __shared__ __align__(128) unsigned char smem[];
-    V *vals0 = reinterpret_cast<V *>(smem + kStages * L::stage_bytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * L::stage_bytes + 2 * L::vals_bytes);
-    __shared__ Tile s_tile[kStages];
-    __shared__ int s_fail;
-    __shared__ V s_chunk[kWarps][W];
-    __shared__ int s_last;
+    const int32_t *__restrict__ src = job.src;
+    const int32_t *__restrict__ off = job.off;
+    const int32_t *__restrict__ outdeg = job.outdeg;
+    const int32_t *__restrict__ perm = job.perm;
+    const Tile *__restrict__ tiles = job.tiles;
+    const int32_t *__restrict__ slot_base = job.slot_base;
+    V *chunk_part = reinterpret_cast<V *>(job.chunk_part);
+    uint32_t *chunk_cnt = job.chunk_cnt;
+    const int ntiles = job.ntiles, cta_count = job.cta_count;
+    __shared__ V s_vals[kWarps][VT];
+    __shared__ V s_prev[kWarps][TR * W];
+    __shared__ int32_t s_off[kWarps][TR + 1];
+    __shared__ int32_t s_od[kWarps][TR];
 
     // Loop guard independent of the pass bookkeeping: should the job
     // finalizers ever fail to stop the graph's while-loop, the launch after the
@@ -431,153 +379,108 @@ __global__ void __launch_bounds__(kBlock, 4) pr_iter_kernel(JobDev *jobs, Global
         }
     }
     const ColView<V> cv = col_view<V>(job, col);
-    const V *rp_base = reinterpret_cast<const V *>(job.r[job.cur]);
+    const bool need_prev = cv.has && (cv.active || cv.copy_dst);
     RowAcc<V> acc;
     acc.init();
     const bool work = job.alive && !*(volatile int32_t *)&glob->error;
-    int ntl = 0;
-    if (work && local < job.ntiles) ntl = (job.ntiles - 1 - local) / job.cta_count + 1;
 
-    if (tid == 0) {
-        s_fail = 0;
-        for (int s = 0; s < kStages; s++) mbar_init(&bars[s], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-
-    // Thread 0 stages the CTA's k-th tile into stage k % kStages.
-    auto stage_tile = [&](int k) {
-        const int s = k % kStages;
-        const Tile T = job.tiles[local + (size_t)k * job.cta_count];
-        s_tile[s] = T;
-        unsigned char *st = smem + s * L::stage_bytes;
-        const int32_t ea = T.e0 & ~3, eb = (T.e1 + 3) & ~3;
-        const int32_t oa = T.r0 & ~3, ob = (T.r1 + 1 + 3) & ~3;
-        const int32_t da = T.r0 & ~3, db = (T.r1 + 3) & ~3;
-        const long long ra = ((long long)T.r0 * W) / E16 * E16;
-        const long long rb = (((long long)T.r1 * W) + E16 - 1) / E16 * E16;
-        const uint32_t b_src = (uint32_t)(eb - ea) * 4u, b_off = (uint32_t)(ob - oa) * 4u;
-        const uint32_t b_od = (uint32_t)(db - da) * 4u, b_rp = (uint32_t)(rb - ra) * (uint32_t)sizeof(V);
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bars[s], b_src + b_off + b_od + b_rp);
-        if (b_src) bulk_copy_g2s(st, job.src + ea, b_src, &bars[s]);
-        bulk_copy_g2s(st + L::bytes_src, job.off + oa, b_off, &bars[s]);
-        bulk_copy_g2s(st + L::bytes_src + L::bytes_off, job.outdeg + da, b_od, &bars[s]);
-        bulk_copy_g2s(st + L::bytes_src + L::bytes_off + L::bytes_od, rp_base + ra, b_rp, &bars[s]);
-    };
-    // All threads: wait for tile k's staged data, then issue its gathers.
-    auto gather_tile = [&](int k) -> bool {
-        const int s = k % kStages;
-        if (!mbar_wait_bounded(&bars[s], (uint32_t)((k / kStages) & 1))) return false;
-        const Tile &T = s_tile[s];
-        const int32_t *s_src = reinterpret_cast<const int32_t *>(smem + s * L::stage_bytes) + (T.e0 & 3);
-        V *vals = vals0 + (size_t)(k & 1) * (L::vals_bytes / sizeof(V));
-        const int nv = (T.e1 - T.e0) * W;
-        if (cv.active) {
-            const V *cp = cv.c_prev;
-            for (int idx = tid; idx < nv; idx += kBlock)
-                cp_async_ca<sizeof(V)>(vals + idx, cp + (size_t)s_src[idx / W] * W + col);
-        }
-        cp_async_commit();
-        return true;
-    };
-
-    if (tid == 0)
-        for (int k = 0; k < 2 && k < ntl; k++) stage_tile(k);
-    if (ntl > 0 && !gather_tile(0)) s_fail = 1;
-
-    int k = 0;
-    for (; k < ntl; k++) {
-        if (tid == 0 && k + 2 < ntl) stage_tile(k + 2);
-        if (k + 1 < ntl) {
-            if (!gather_tile(k + 1)) s_fail = 1;
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        if (s_fail) break;
-        const int s = k % kStages;
-        const Tile T = s_tile[s];
-        const unsigned char *st = smem + s * L::stage_bytes;
-        const int32_t *s_off = reinterpret_cast<const int32_t *>(st + L::bytes_src) + (T.r0 & 3);
-        const int32_t *s_od = reinterpret_cast<const int32_t *>(st + L::bytes_src + L::bytes_off) + (T.r0 & 3);
-        const V *s_rp = reinterpret_cast<const V *>(st + L::bytes_src + L::bytes_off + L::bytes_od) +
-                        ((long long)T.r0 * W - ((long long)T.r0 * W) / E16 * E16);
-        const V *vals = vals0 + (size_t)(k & 1) * (L::vals_bytes / sizeof(V));
-        const int nv = (T.e1 - T.e0) * W;
-        if (T.glog >= 0) {
-            // ---- rows: g lanes per row add the row's values from shared memory
-            const int g = 1 << T.glog;
-            const int lg = tid & (g - 1);
-            const int es = lg / W;
-            const int ES = g / W;
-            const int rows_per_pass = kBlock >> T.glog;
-            for (int32_t rb = T.r0; rb < T.r1; rb += rows_per_pass) {
-                const int32_t v = rb + (tid >> T.glog);
-                const bool valid = v < T.r1;
+    if (work) {
+        const int wstride = cta_count * kWarps;
+        for (int t = local * kWarps + warp; t < ntiles; t += wstride) {
+            const Tile T = tiles[t];
+            if (T.glog >= 0) {
+                // ---------------- rows tile: indices, offsets, previous ranks
+                // and out-degrees are all requested before any gather waits
+                const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
+                int32_t u[PER];
+#pragma unroll
+                for (int k = 0; k < PER; k++) {
+                    const int idx = lane + 32 * k;
+                    u[k] = (cv.active && idx < ne * W) ? src[T.e0 + idx / W] : -1;
+                }
+                for (int i = lane; i <= nr; i += 32) s_off[warp][i] = off[T.r0 + i] - T.e0;
+                // element i of the rows belongs to column i % W == lane % W
+                if (need_prev)
+                    for (int i = lane; i < nr * W; i += 32) s_prev[warp][i] = cv.r_prev[(size_t)T.r0 * W + i];
+                for (int i = lane; i < nr; i += 32) s_od[warp][i] = outdeg[T.r0 + i];
+                {
+                    V x[PER];
+#pragma unroll
+                    for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? cv.c_prev[(size_t)u[k] * W + col] : N::zero();
+#pragma unroll
+                    for (int k = 0; k < PER; k++)
+                        if (u[k] >= 0) s_vals[warp][lane + 32 * k] = x[k];
+                }
+                __syncwarp();
+                const int g = 1 << T.glog;
+                const int es = (lane & (g - 1)) / W;
+                const int ES = g / W;
+                const int rpp = 32 >> T.glog;
+                for (int rb = 0; rb < nr; rb += rpp) {
+                    const int r = rb + (lane >> T.glog);
+                    const bool valid = r < nr;
+                    EdgeSum<V> sum;
+                    sum.init();
+                    if (valid && cv.active) {
+                        const int lo = s_off[warp][r], hi = s_off[warp][r + 1];
+                        for (int e = lo + es; e < hi; e += ES) sum.add(s_vals[warp][e * W + col]);
+                    }
+                    V sv = sum.get();
+                    for (int m = W; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                    if (valid && es == 0 && need_prev)
+                        row_update_pd<V, W>(perm, cv, acc, T.r0 + r, col, sv, s_prev[warp][r * W + col], s_od[warp][r]);
+                }
+                __syncwarp();
+            } else {
+                // ---------------- one chunk of a long row, VT values per step
+                const int32_t v = T.r0;
+                const int nv = (T.e1 - T.e0) * W;
                 EdgeSum<V> sum;
                 sum.init();
-                if (valid && cv.active) {
-                    const int lo = s_off[v - T.r0] - T.e0, hi = s_off[v - T.r0 + 1] - T.e0;
-                    for (int e = lo + es; e < hi; e += ES) sum.add(vals[e * W + col]);
+                if (cv.active) {
+                    for (int base = lane; base < nv; base += VT) {
+                        int32_t u[PER];
+#pragma unroll
+                        for (int k = 0; k < PER; k++) {
+                            const int idx = base + 32 * k;
+                            u[k] = idx < nv ? src[T.e0 + idx / W] : -1;
+                        }
+                        V x[PER];
+#pragma unroll
+                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? cv.c_prev[(size_t)u[k] * W + col] : N::zero();
+#pragma unroll
+                        for (int k = 0; k < PER; k++)
+                            if (u[k] >= 0) sum.add(x[k]);
+                    }
                 }
                 V sv = sum.get();
-                for (int m = W; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-                if (valid && es == 0 && cv.has)
-                    row_update<V, W>(job, cv, acc, v, col, sv, s_rp[(v - T.r0) * W + col], s_od[v - T.r0]);
-            }
-        } else {
-            // ---- chunk of a long row: the whole CTA adds it per column
-            EdgeSum<V> sum;
-            sum.init();
-            if (cv.active)
-                for (int idx = tid; idx < nv; idx += kBlock) sum.add(vals[idx]);
-            V sv = sum.get();
-            for (int m = W; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-            if ((tid & 31) < W) s_chunk[tid >> 5][col] = sv;
-            __syncthreads();
-            V tot = N::zero();
-            if (tid < W)
-                for (int w = 0; w < kWarps; w++) tot = N::add_pos(tot, s_chunk[w][tid]);
-            const int32_t v = T.r0;
-            if (T.slot < 0) {
-                if (tid < W && cv.has) row_update<V, W>(job, cv, acc, v, col, tot, s_rp[col], s_od[0]);
-            } else {
-                V *part = reinterpret_cast<V *>(job.chunk_part);
-                const int32_t base = job.slot_base[T.slot];
-                if (tid < W) part[(size_t)(base + T.k) * W + tid] = tot;
-                __threadfence();
-                __syncthreads();
-                if (tid == 0) {
-                    unsigned int old = atomicAdd(&job.chunk_cnt[T.slot], 1u);
-                    s_last = (old == (unsigned int)(T.nch - 1));
-                }
-                __syncthreads();
-                if (s_last) {
+                for (int m = W; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                if (T.slot < 0) {
+                    if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, sv);
+                } else {
+                    const int32_t base = slot_base[T.slot];
+                    if (lane < W) chunk_part[(size_t)(base + T.k) * W + lane] = sv;
                     __threadfence();
-                    if (tid < W && cv.has) {
+                    __syncwarp();
+                    int last = 0;
+                    if (lane == 0) last = atomicAdd(&chunk_cnt[T.slot], 1u) == (unsigned int)(T.nch - 1);
+                    last = __shfl_sync(0xffffffffu, last, 0);
+                    if (last) {
+                        // the row's chunk sums, lane-parallel in a fixed order:
+                        // lane slot q0 adds chunks q0, q0 + 32/W, ... then a fixed tree
+                        __threadfence();
+                        constexpr int QS = 32 / W;
                         V t = N::zero();
-                        for (int32_t q = 0; q < T.nch; q++) t = N::add_pos(t, ld_cg_v<V>(part + (size_t)(base + q) * W + tid));
-                        row_update<V, W>(job, cv, acc, v, col, t, s_rp[col], s_od[0]);
+                        for (int32_t q = lane / W; q < T.nch; q += QS)
+                            t = N::add_pos(t, ld_cg_v<V>(chunk_part + (size_t)(base + q) * W + col));
+                        for (int m = W; m < 32; m <<= 1) t = N::add_pos(t, N::shfl_xor(t, m));
+                        if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, t);
+                        if (lane == 0) chunk_cnt[T.slot] = 0;
                     }
-                    if (tid == 0) job.chunk_cnt[T.slot] = 0;
+                    __syncwarp();
                 }
             }
         }
-        __syncthreads();   // stage k % kStages and vals[k % 2] are free again
-    }
-    if (s_fail) {
-        // a staged copy did not arrive in time: let this CTA's element copies
-        // land, wait (bounded) for its bulk copies in flight, record the error,
-        // skip the remaining tiles and still take part in the pass bookkeeping
-        cp_async_wait<0>();
-        if (tid == 0) {
-            for (int j = k + 1; j < ntl && j < k + 3; j++)
-                mbar_wait_bounded(&bars[j % kStages], (uint32_t)((j / kStages) & 1));
-            glob->error = kErrCopyTimeout;
-        }
-        __syncthreads();
     }
     finish_pass<V, W>(jobs, job, glob, acc, local, kPassIterate);
 }

@@ -62,18 +62,6 @@ void *init_ptr(int W) {
         default: return (void *)pr_init_kernel<V, 32>;
     }
 }
-template <typename V>
-size_t smem_of(int W) {
-    switch (W) {
-        case 1: return StageLayout<V, 1>::total;
-        case 2: return StageLayout<V, 2>::total;
-        case 4: return StageLayout<V, 4>::total;
-        case 8: return StageLayout<V, 8>::total;
-        case 16: return StageLayout<V, 16>::total;
-        default: return StageLayout<V, 32>::total;
-    }
-}
-
 void store_value(double *dst, int prec, double x) {
     dst[0] = 0.0;
     dst[1] = 0.0;
@@ -130,13 +118,7 @@ void *pr_init_kernel_for(int prec, int W) {
         default: return init_ptr<df64>(W);
     }
 }
-size_t pr_tile_smem_bytes(int prec, int W) {
-    switch (prec) {
-        case PR_PREC_FP64: return smem_of<double>(W);
-        case PR_PREC_FP32: return smem_of<float>(W);
-        default: return smem_of<df64>(W);
-    }
-}
+size_t pr_tile_smem_bytes(int, int) { return 0; }   // the kernels use static shared memory only
 
 // Opt the iteration kernel into its dynamic shared memory (once per process
 // and instantiation) and report its resident CTAs per SM.
@@ -217,7 +199,6 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
             if (!back.alive || back.error) break;
         }
         stats.passes += back.pass;
-        if (back.error == kErrCopyTimeout) return pr_fail(PR_ETIMEOUT, "a staged tile copy did not complete in time");
         if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
     } else {
         cudaGraph_t graph = nullptr;
@@ -257,7 +238,6 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
         PR_CUDA(cudaStreamSynchronize(st));
         stats.launches += 1 + (int)back.body_count;
         stats.passes += back.pass;
-        if (back.error == kErrCopyTimeout) return pr_fail(PR_ETIMEOUT, "a staged tile copy did not complete in time");
         if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
     }
     PR_CUDA(cudaEventRecord(ev1, st));
