@@ -228,7 +228,7 @@ pr_status pr_solve_batch(pr_instance *inst, int32_t count, const pr_options *opt
  *    in-neighbours u, alpha]
  * predicts log(N * r); the start is exp(prediction) renormalised to sum 1.
  * Weights are held in FP32 (master) and BF16 (inference/training operands).
- * params layout (host, 4673 floats): W1[64][5], b1[64], W2[64][64], b2[64],
+ * params layout (host, 4609 floats): W1[64][5], b1[64], W2[64][64], b2[64],
  * W3[1][64], b3[1].
  */
 pr_status pr_mlp_create(const float *params, pr_mlp **out);
@@ -241,6 +241,15 @@ pr_status pr_features(const pr_graph *g, double alpha, float *d_feat_out, void *
 /* Warm-start vector (n doubles, caller order; device pointer) for (g, alpha). */
 pr_status pr_mlp_warm_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_r0_out,
                             void *stream);
+
+/*
+ * Mean squared error of the network on one set, L = mean over vertices of
+ * (y - log(N r*))^2, and its gradient with respect to every parameter (host
+ * outputs: loss_out one float, grad_out 4609 floats in the params layout;
+ * either may be NULL). d_target_r: device, n doubles r* in caller order.
+ */
+pr_status pr_mlp_loss_grad(const pr_mlp *m, const pr_graph *g, double alpha, const double *d_target_r,
+                           float *loss_out, float *grad_out, void *stream);
 
 /*
  * Train the MLP on the device with the library's own forward, backward and

@@ -70,6 +70,7 @@ SIGNATURES = {
     "pr_features": ([_vp, _d, _vp, _vp], _i32),
     "pr_mlp_warm_start": ([_vp, _vp, _d, _vp, _vp], _i32),
     "pr_mlp_train": ([_vp, _vp, _vp, _vp, _i32, _i32, _f, _vp, _vp], _i32),
+    "pr_mlp_loss_grad": ([_vp, _vp, _d, _vp, _vp, _vp, _vp], _i32),
     "pr_last_solve_stats": ([_vp, _vp, _vp, _vp], _i32),
     "pr_solve_noalloc": ([_vp, _d, _d, _i32, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "pr_last_error": ([], C.c_char_p),
@@ -291,3 +292,91 @@ def pr_last_solve_stats():
     la, pa, km, tm = C.c_int32(), C.c_int32(), C.c_double(), C.c_double()
     lib().pr_last_solve_stats(C.byref(la), C.byref(pa), C.byref(km), C.byref(tm))
     return {"launches": la.value, "passes": pa.value, "kernel_ms": km.value, "total_ms": tm.value}
+
+
+class MLP:
+    """A ``pr_mlp`` handle: the learned warm start (5-64-64-1 GELU MLP)."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        if p.size != MLP_PARAMS:
+            raise ValueError(f"need {MLP_PARAMS} parameters")
+        h = C.c_void_p()
+        _check(lib().pr_mlp_create(p.ctypes.data, C.byref(h)), "pr_mlp_create")
+        self.handle = h
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        _check(lib().pr_mlp_get_params(self.handle, out.ctypes.data), "pr_mlp_get_params")
+        return out
+
+    def warm_start(self, g: "Graph", alpha: float, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        if stream is None:
+            stream = current_stream_ptr()
+        _check(lib().pr_mlp_warm_start(self.handle, g.handle, float(alpha), out.data_ptr(), stream),
+               "pr_mlp_warm_start")
+        return out
+
+    def loss_grad(self, g: "Graph", alpha: float, target_r, stream=None):
+        """(loss, gradient) on one set; target_r: torch CUDA float64 tensor (caller order)."""
+        if stream is None:
+            stream = current_stream_ptr()
+        loss = C.c_float()
+        grad = np.empty(MLP_PARAMS, np.float32)
+        _check(lib().pr_mlp_loss_grad(self.handle, g.handle, float(alpha), target_r.data_ptr(), C.byref(loss),
+                                      grad.ctypes.data, stream), "pr_mlp_loss_grad")
+        return float(loss.value), grad
+
+    def train(self, sets, epochs: int, lr: float, stream=None) -> float:
+        """sets: list of (Graph, alpha, target_r CUDA float64 tensor). Returns
+        the mean loss of the last epoch."""
+        if stream is None:
+            stream = current_stream_ptr()
+        n = len(sets)
+        gs = (C.c_void_p * n)(*[s[0].handle.value for s in sets])
+        al = (C.c_double * n)(*[float(s[1]) for s in sets])
+        tg = (C.c_void_p * n)(*[s[2].data_ptr() for s in sets])
+        loss = C.c_float()
+        _check(lib().pr_mlp_train(self.handle, gs, al, tg, n, int(epochs), float(lr), C.byref(loss), stream),
+               "pr_mlp_train")
+        return float(loss.value)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().pr_mlp_destroy(self.handle), "pr_mlp_destroy")
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pr_features(g: "Graph", alpha: float, out=None, stream=None):
+    """(n, 5) float32 features on the device, caller order."""
+    import torch
+    if out is None:
+        out = torch.empty((g.n, 5), dtype=torch.float32, device="cuda")
+    if stream is None:
+        stream = current_stream_ptr()
+    _check(lib().pr_features(g.handle, float(alpha), out.data_ptr(), stream), "pr_features")
+    return out
+
+
+def init_mlp_params(seed: int = 7) -> np.ndarray:
+    """Seeded initial parameters: weights N(0, 1/fan_in) from the counter-based
+    generator, zero biases."""
+    from . import graphgen
+    z = graphgen.normal(seed, 9, MLP_PARAMS)
+    p = np.zeros(MLP_PARAMS, np.float64)
+    o = 0
+    for shape, fan_in in (((64, 5), 5), ((64,), 0), ((64, 64), 64), ((64,), 0), ((1, 64), 64), ((1,), 0)):
+        k = int(np.prod(shape))
+        if fan_in:
+            p[o:o + k] = z[o:o + k] / np.sqrt(fan_in)
+        o += k
+    return p.astype(np.float32)
