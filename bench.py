@@ -252,6 +252,22 @@ def run_ours(args, world, rank, local):
     bytes_avg = bytes_per_launch / max(k_launches, 1)
     achieved = bytes_avg / (avg_launch_ms * 1e-3) / 1e9
     gteps_device = total_edges * (k_launches / max(len(graphs), 1)) / (ms_step * 1e-3) / 1e9
+    # ---- plain per-instance GPU solver on the same resident graphs: every
+    # instance alone through pr_solve, one launch per iteration and a host read
+    # of the stop flag after each (the baseline the batched path is measured against)
+    plain = None
+    if not args.no_plain:
+        t_plain = 0.0
+        for k, (gi, a, t, nm, mi) in enumerate(specs):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.pr_solve(dgs[gi], a, t, nm, mi, out=outs[k], loop="host", stream=sptr,
+                       precision="df64" if precision == "mixed" else precision)
+            torch.cuda.synchronize()
+            t_plain += time.perf_counter() - t0
+        plain = {"solves_per_s": solves / t_plain, "ms_per_step": t_plain * 1000.0,
+                 "what": "each instance alone, pr_solve with one launch per iteration and a host read of the stop flag",
+                 "speedup_of_value": (solves * 1000.0 / ms_step) / (solves / t_plain)}
     # ---- e2e: graph creation from pinned host arrays + solve + ranks to host, every step
     e2e = None
     if not args.no_e2e:
@@ -310,6 +326,7 @@ def run_ours(args, world, rank, local):
                      "kernel": "pr_iter_kernel", "avg_launch_us": avg_launch_ms * 1e3,
                      "algorithmic_bytes_per_launch": bytes_avg, "peak_source": peak_kind},
         "e2e": e2e,
+        "plain_gpu": plain,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": launches,
@@ -409,6 +426,7 @@ def main():
                     help="device loop of the timed solves (host: one launch per iteration)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain per-instance GPU solver comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -160,6 +160,57 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     return PR_OK;
 }
 
+namespace {
+
+// Device validation of the in-edge sources: every source in [0, n), and the
+// number of times each vertex occurs equal to its out-degree. Records the
+// smallest offending edge / vertex index (or INT64_MAX when none).
+__global__ void count_sources_kernel(const int32_t *__restrict__ src, int64_t nnz, int32_t n, int32_t *count,
+                                     unsigned long long *bad_edge) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = src[e];
+        if (u < 0 || u >= n) atomicMin(bad_edge, (unsigned long long)e);
+        else atomicAdd(&count[u], 1);
+    }
+}
+__global__ void check_outdeg_kernel(const int32_t *__restrict__ count, const int32_t *__restrict__ outdeg, int32_t n,
+                                    unsigned long long *bad_vertex) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if (count[v] != outdeg[v]) atomicMin(bad_vertex, (unsigned long long)v);
+}
+// Relabelled rows: row i of the new CSR is caller row perm[i], its sources
+// mapped through inv. One warp per row.
+__global__ void remap_rows_kernel(const int32_t *__restrict__ old_off, const int32_t *__restrict__ old_src,
+                                  const int32_t *__restrict__ new_off, const int32_t *__restrict__ perm,
+                                  const int32_t *__restrict__ inv, int32_t n, int32_t *__restrict__ new_src) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n; i += nw) {
+        const int32_t v = perm[i];
+        const int32_t a = old_off[v], len = old_off[v + 1] - a, o = new_off[i];
+        for (int32_t k = lane; k < len; k += 32) new_src[o + k] = inv[old_src[a + k]];
+    }
+}
+
+int blocks_for(int64_t work, int threads) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t want = (work + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 16));
+}
+
+struct DevTmp {
+    void *p = nullptr;
+    ~DevTmp() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+// Graph creation. The host does the O(n) work (offset checks, the
+// relabelling sort, new offsets, class ranges and tile tables); the device does
+// the O(nnz) work (validation of every source and the remapped copy of the rows).
 extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_offsets,
                                      const int32_t *in_sources, const int32_t *out_degree, pr_graph **out) {
     pr_clear_error();
@@ -169,73 +220,22 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     if (nnz < 0 || nnz >= (int64_t)INT32_MAX) return pr_fail(PR_EINVAL, "nnz must be in [0, 2^31-1)");
     if (!in_offsets || !out_degree) return pr_fail(PR_EINVAL, "in_offsets and out_degree are required");
     if (nnz > 0 && !in_sources) return pr_fail(PR_EINVAL, "in_sources is NULL but nnz > 0");
-    // ---- validate (host; O(n + nnz))
+    // ---- O(n) checks on the host
     if (in_offsets[0] != 0) return pr_fail(PR_EINVAL, "in_offsets[0] must be 0");
     if ((int64_t)in_offsets[n] != nnz) return pr_fail(PR_EINVAL, "in_offsets[n] must equal nnz");
-    for (int32_t v = 0; v < n; v++)
-        if (in_offsets[v + 1] < in_offsets[v]) return pr_fail(PR_EINVAL, "in_offsets is not non-decreasing at row " + std::to_string(v));
-    std::vector<int32_t> count;
-    try {
-        count.assign((size_t)n, 0);
-    } catch (const std::bad_alloc &) {
-        return pr_fail(PR_ENOMEM, "host allocation failed");
-    }
-    for (int64_t e = 0; e < nnz; e++) {
-        int32_t u = in_sources[e];
-        if (u < 0 || u >= n) return pr_fail(PR_EINVAL, "in_sources[" + std::to_string(e) + "] out of range");
-        count[u]++;
-    }
+    int64_t deg_sum = 0;
     int32_t n_dangling = 0;
     for (int32_t v = 0; v < n; v++) {
-        if (out_degree[v] != count[v])
-            return pr_fail(PR_EINVAL, "out_degree[" + std::to_string(v) + "] does not match the edges in in_sources");
+        if (in_offsets[v + 1] < in_offsets[v]) return pr_fail(PR_EINVAL, "in_offsets is not non-decreasing at row " + std::to_string(v));
+        if (out_degree[v] < 0) return pr_fail(PR_EINVAL, "out_degree[" + std::to_string(v) + "] is negative");
+        deg_sum += out_degree[v];
         if (out_degree[v] == 0) n_dangling++;
     }
-    // ---- relabel: stable counting sort by (in-class desc, out-class desc)
-    std::vector<int32_t> perm, inv, new_off, new_src, new_od, tmp;
-    try {
-        perm.resize((size_t)n);
-        inv.resize((size_t)n);
-        tmp.resize((size_t)n);
-        new_off.resize((size_t)n + 1);
-        new_src.resize((size_t)std::max<int64_t>(nnz, 1));
-        new_od.resize((size_t)n);
-    } catch (const std::bad_alloc &) {
-        return pr_fail(PR_ENOMEM, "host allocation failed");
-    }
-    {
-        size_t cnt[33];
-        for (int32_t v = 0; v < n; v++) tmp[v] = v;
-        // pass 1 (secondary key): out-degree class, descending
-        std::memset(cnt, 0, sizeof(cnt));
-        for (int32_t v = 0; v < n; v++) cnt[32 - deg_class(out_degree[v])]++;
-        size_t s = 0;
-        for (int b = 0; b < 33; b++) { size_t c = cnt[b]; cnt[b] = s; s += c; }
-        for (int32_t i = 0; i < n; i++) { int32_t v = tmp[i]; perm[cnt[32 - deg_class(out_degree[v])]++] = v; }
-        // pass 2 (primary key): in-degree class, descending
-        std::memset(cnt, 0, sizeof(cnt));
-        for (int32_t v = 0; v < n; v++) cnt[32 - deg_class(in_offsets[v + 1] - in_offsets[v])]++;
-        s = 0;
-        for (int b = 0; b < 33; b++) { size_t c = cnt[b]; cnt[b] = s; s += c; }
-        for (int32_t i = 0; i < n; i++) {
-            int32_t v = perm[i];
-            tmp[cnt[32 - deg_class(in_offsets[v + 1] - in_offsets[v])]++] = v;
-        }
-        perm.swap(tmp);
-    }
-    for (int32_t i = 0; i < n; i++) inv[perm[i]] = i;
-    new_off[0] = 0;
-    for (int32_t i = 0; i < n; i++) {
-        int32_t v = perm[i];
-        new_off[i + 1] = new_off[i] + (in_offsets[v + 1] - in_offsets[v]);
-        new_od[i] = out_degree[v];
-    }
-    for (int32_t i = 0; i < n; i++) {
-        int32_t v = perm[i];
-        int32_t o = new_off[i];
-        for (int32_t e = in_offsets[v]; e < in_offsets[v + 1]; e++) new_src[o++] = inv[in_sources[e]];
-    }
-    // ---- classes over the relabelled rows
+    if (deg_sum != nnz) return pr_fail(PR_EINVAL, "out_degree does not sum to nnz (it must match the edges in in_sources)");
+    // ---- caller arrays on the device, sources validated there
+    DevTmp d_old_off, d_old_src, d_cnt, d_bad;
+    cudaError_t e = cudaSuccess;
+    const size_t n_off = (size_t)n + 1 + kPad, n_src = (size_t)nnz + kPad, n_od = (size_t)n + kPad;
     pr_graph *g = new (std::nothrow) pr_graph();
     if (!g) return pr_fail(PR_ENOMEM, "host allocation failed");
     g->magic = kGraphMagic;
@@ -243,10 +243,86 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     g->nnz = nnz;
     g->n_dangling = n_dangling;
     cudaGetDevice(&g->device);
+    pr_status s;
+    if ((s = dalloc(&g->d_off, n_off)) != PR_OK || (s = dalloc(&g->d_src, n_src)) != PR_OK ||
+        (s = dalloc(&g->d_outdeg, n_od)) != PR_OK || (s = dalloc(&g->d_perm, (size_t)n)) != PR_OK ||
+        (s = dalloc(&g->d_inv, (size_t)n)) != PR_OK) {
+        free_graph(g);
+        return s;
+    }
+    e = cudaMalloc(&d_old_off.p, sizeof(int32_t) * ((size_t)n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_old_src.p, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_cnt.p, sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_bad.p, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(d_old_off.p, in_offsets, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_old_src.p, in_sources, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d_cnt.p, 0, sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemset(d_bad.p, 0xFF, 2 * sizeof(unsigned long long));
+    // the caller's out-degrees go straight into the final array's scratch use: copy to d_outdeg first
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_outdeg, out_degree, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_graph(g);
+        return pr_cuda_fail(e, "graph upload");
+    }
+    unsigned long long *bad = static_cast<unsigned long long *>(d_bad.p);
+    if (nnz > 0)
+        count_sources_kernel<<<blocks_for(nnz, 256), 256>>>(static_cast<const int32_t *>(d_old_src.p), nnz, n,
+                                                            static_cast<int32_t *>(d_cnt.p), bad);
+    check_outdeg_kernel<<<blocks_for(n, 256), 256>>>(static_cast<const int32_t *>(d_cnt.p), g->d_outdeg, n, bad + 1);
+    unsigned long long hbad[2] = {~0ull, ~0ull};
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        free_graph(g);
+        return pr_cuda_fail(e, "graph validation");
+    }
+    if (hbad[0] != ~0ull) {
+        free_graph(g);
+        return pr_fail(PR_EINVAL, "in_sources[" + std::to_string(hbad[0]) + "] out of range");
+    }
+    if (hbad[1] != ~0ull) {
+        free_graph(g);
+        return pr_fail(PR_EINVAL, "out_degree[" + std::to_string(hbad[1]) + "] does not match the edges in in_sources");
+    }
+    // ---- relabel on the host: stable counting sort by (in-class desc, out-class desc), O(n)
+    std::vector<int32_t> perm, inv, new_off, new_od, tmp;
+    try {
+        perm.resize((size_t)n);
+        inv.resize((size_t)n);
+        tmp.resize((size_t)n);
+        new_off.resize((size_t)n + 1);
+        new_od.resize((size_t)n);
+    } catch (const std::bad_alloc &) {
+        free_graph(g);
+        return pr_fail(PR_ENOMEM, "host allocation failed");
+    }
+    {
+        size_t cnt[33];
+        std::memset(cnt, 0, sizeof(cnt));
+        for (int32_t v = 0; v < n; v++) cnt[32 - deg_class(out_degree[v])]++;
+        size_t acc = 0;
+        for (int b = 0; b < 33; b++) { size_t c = cnt[b]; cnt[b] = acc; acc += c; }
+        for (int32_t v = 0; v < n; v++) tmp[cnt[32 - deg_class(out_degree[v])]++] = v;
+        std::memset(cnt, 0, sizeof(cnt));
+        for (int32_t v = 0; v < n; v++) cnt[32 - deg_class(in_offsets[v + 1] - in_offsets[v])]++;
+        acc = 0;
+        for (int b = 0; b < 33; b++) { size_t c = cnt[b]; cnt[b] = acc; acc += c; }
+        for (int32_t i = 0; i < n; i++) {
+            const int32_t v = tmp[i];
+            perm[cnt[32 - deg_class(in_offsets[v + 1] - in_offsets[v])]++] = v;
+        }
+    }
+    new_off[0] = 0;
+    for (int32_t i = 0; i < n; i++) {
+        const int32_t v = perm[i];
+        inv[v] = i;
+        new_off[i + 1] = new_off[i] + (in_offsets[v + 1] - in_offsets[v]);
+        new_od[i] = out_degree[v];
+    }
     {
         int32_t i = 0;
         while (i < n) {
-            int c = deg_class(new_off[i + 1] - new_off[i]);
+            const int c = deg_class(new_off[i + 1] - new_off[i]);
             ClassRange cr{i, i, 0};
             while (i < n && deg_class(new_off[i + 1] - new_off[i]) == c) {
                 cr.max_deg = std::max(cr.max_deg, new_off[i + 1] - new_off[i]);
@@ -256,32 +332,26 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
             g->classes.push_back(cr);
         }
     }
-    g->h_off = new_off;
-    // ---- device copies, each padded with kPad zeroed elements so that tile
-    // copies rounded to 16 bytes stay inside the allocation
-    const size_t n_off = (size_t)n + 1 + kPad, n_src = (size_t)nnz + kPad, n_od = (size_t)n + kPad;
-    pr_status s;
-    if ((s = dalloc(&g->d_off, n_off)) != PR_OK ||
-        (s = dalloc(&g->d_src, n_src)) != PR_OK ||
-        (s = dalloc(&g->d_outdeg, n_od)) != PR_OK ||
-        (s = dalloc(&g->d_perm, (size_t)n)) != PR_OK ||
-        (s = dalloc(&g->d_inv, (size_t)n)) != PR_OK) {
-        free_graph(g);
-        return s;
-    }
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemset(g->d_off, 0, sizeof(int32_t) * n_off);
+    // ---- relabelled arrays on the device (padding zeroed), rows remapped there
+    e = cudaMemset(g->d_off, 0, sizeof(int32_t) * n_off);
     if (e == cudaSuccess) e = cudaMemset(g->d_src, 0, sizeof(int32_t) * n_src);
     if (e == cudaSuccess) e = cudaMemset(g->d_outdeg, 0, sizeof(int32_t) * n_od);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_off, new_off.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(g->d_src, new_src.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_outdeg, new_od.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_inv, inv.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz > 0) {
+        remap_rows_kernel<<<blocks_for((int64_t)n * 32, 256), 256>>>(static_cast<const int32_t *>(d_old_off.p),
+                                                                     static_cast<const int32_t *>(d_old_src.p), g->d_off,
+                                                                     g->d_perm, g->d_inv, n, g->d_src);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_graph(g);
-        return pr_cuda_fail(e, "cudaMemcpy graph");
+        return pr_cuda_fail(e, "graph relabel");
     }
+    g->h_off.swap(new_off);
     // the single-column work table is built now so that solves on this graph
     // never need to allocate it later
     const TileTable *t1 = nullptr;

@@ -130,3 +130,18 @@ def test_rmat_matches_oracle(B, orc, gg, scale):
         res = B.pr_solve(dg, 0.85, tau, norm, 500)
         assert_fp64_parity(res.ranks, res.iters, res.err, ref, tau, norm, f"rmat{scale} norm {norm}")
     dg.close()
+
+
+def test_device_side_graph_validation(B):
+    """Per-edge checks of pr_graph_create run on the device: an out-of-range
+    source and out-degrees that disagree with the sources (same total) are
+    rejected with PR_EINVAL and no handle."""
+    with pytest.raises(B.PageRankError) as ei:
+        B.Graph([0, 1, 2], [0, 5], [2, 0])
+    assert ei.value.status == B.PR_EINVAL and "out of range" in str(ei.value)
+    with pytest.raises(B.PageRankError) as ei:
+        B.Graph([0, 1, 2], [0, 0], [1, 1])
+    assert ei.value.status == B.PR_EINVAL and "does not match" in str(ei.value)
+    g = B.Graph([0, 1, 2], [1, 0], [1, 1])   # the valid 2-cycle still works afterwards
+    assert g.info() == (2, 2, 0)
+    g.close()
