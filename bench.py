@@ -86,7 +86,38 @@ def make_workload(name, gg):
         g = gg.rmat(24, 16, seed=24)
         specs = [(0, a, 1e-10, 3, 500) for a in (0.85, 0.95)]
         return [g], specs, "mixed", "rmat-s24 ef16 seed24, alpha {.85,.95}, Linf, tau 1e-10, fp32->df64"
+    if name == "learned":
+        gs = [gg.rmat(22, 16, seed=3022), gg.rmat(24, 16, seed=3024), gg.config_model(8_000_000, seed=3008)]
+        alphas = (0.5, 0.6, 0.7, 0.8, 0.85, 0.9, 0.95)
+        specs = [(i, a, 1e-10, 1, 500) for i in range(len(gs)) for a in alphas]
+        return gs, specs, "mixed", ("unseen rmat-s22 (seed 3022), rmat-s24 (seed 3024), config model N=8M "
+                                    "(seed 3008); 7 alpha x tau 1e-10 L1; learned start, fp32->df64")
     raise SystemExit(f"unknown workload {name}")
+
+
+def train_warm_start(B, gg, torch, sptr, epochs=30, lr=3e-3):
+    """The learned warm start of BASELINE's config 5: 32 seeded R-MAT graphs of
+    scale 16 + (i mod 5), alpha 0.50..0.95; targets are this library's own
+    solves at tau 1e-12. Returns (mlp, report)."""
+    alphas = [round(0.5 + 0.05 * i, 2) for i in range(10)]
+    t0 = time.perf_counter()
+    sets, keep = [], []
+    for i in range(32):
+        g = gg.rmat(16 + (i % 5), 16, seed=2000 + i)
+        dg = B.Graph.from_csr(g)
+        keep.append(dg)
+        xs = [B.Instance(dg, a, 1e-12, 1, 2000, out=torch.empty(g.n, dtype=torch.float64, device="cuda"))
+              for a in alphas]
+        B.pr_solve_batch(xs, outputs_on_device=True, stream=sptr)
+        sets += [(dg, x.alpha, x.out) for x in xs]
+    t1 = time.perf_counter()
+    mlp = B.MLP(B.init_mlp_params(seed=17))
+    loss0, _ = mlp.loss_grad(*sets[0])
+    loss = mlp.train(sets, epochs=epochs, lr=lr, stream=sptr)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return mlp, keep, {"train_sets": len(sets), "epochs": epochs, "lr": lr, "loss_first_set_initial": loss0,
+                       "loss_final_mean": loss, "target_solves_s": t1 - t0, "train_s": t2 - t1}
 
 
 # --------------------------------------------------------------------------- clocks
@@ -189,6 +220,10 @@ def run_ours(args, world, rank, local):
     outs = [torch.empty(graphs[gi].n, dtype=torch.float64, device="cuda") for gi, *_ in specs]
     stream = torch.cuda.current_stream()
     sptr = int(stream.cuda_stream)
+    mlp, learned = None, None
+    if args.workload == "learned":
+        mlp, _train_keep, learned = train_warm_start(B, gg, torch, sptr)
+    init_kw = {"init": "learned", "mlp": mlp} if mlp is not None else {}
     total_edges = sum(g.nnz for g in graphs)
     l2_bytes = sum(4 * (g.n + 1) + 4 * g.nnz + 24 * g.n for g in graphs)
     inputs_large = l2_bytes > 2 * 129e6
@@ -199,7 +234,7 @@ def run_ours(args, world, rank, local):
 
     def step():
         xs = insts()
-        B.pr_solve_batch(xs, precision=precision, outputs_on_device=True, stream=sptr, loop=args.loop)
+        B.pr_solve_batch(xs, precision=precision, outputs_on_device=True, stream=sptr, loop=args.loop, **init_kw)
         return xs
 
     for _ in range(args.warmup):
@@ -239,7 +274,7 @@ def run_ours(args, world, rank, local):
     for gi, g in enumerate(graphs):
         sel = [k for k, s in enumerate(specs) if s[0] == gi]
         xs = [B.Instance(dgs[gi], specs[k][1], specs[k][2], specs[k][3], specs[k][4], out=outs[k]) for k in sel]
-        B.pr_solve_batch(xs, precision=precision, outputs_on_device=True, stream=sptr, loop="host")
+        B.pr_solve_batch(xs, precision=precision, outputs_on_device=True, stream=sptr, loop="host", **init_kw)
         st = B.pr_last_solve_stats()
         n_src = int((g.outdeg > 0).sum())
         b = 4.0 * (g.n + 1) + 4.0 * g.nnz + 8.0 * n_src + 8.0 * g.n + 8.0 * g.n + 4.0 * g.n
@@ -252,6 +287,13 @@ def run_ours(args, world, rank, local):
     bytes_avg = bytes_per_launch / max(k_launches, 1)
     achieved = bytes_avg / (avg_launch_ms * 1e-3) / 1e9
     gteps_device = total_edges * (k_launches / max(len(graphs), 1)) / (ms_step * 1e-3) / 1e9
+    if learned is not None:
+        # iterations from the uniform start, same batched mixed-precision sweep
+        xs_u = [B.Instance(dgs[gi], a, t, nm, mi, out=outs[k]) for k, (gi, a, t, nm, mi) in enumerate(specs)]
+        B.pr_solve_batch(xs_u, precision=precision, outputs_on_device=True, stream=sptr)
+        learned["iterations_uniform"] = [x.iters for x in xs_u]
+        learned["iterations_learned"] = inst_iters
+        learned["iterations_saved_total"] = sum(x.iters for x in xs_u) - sum(inst_iters)
     # ---- plain per-instance GPU solver on the same resident graphs: every
     # instance alone through pr_solve, one launch per iteration and a host read
     # of the stop flag after each (the baseline the batched path is measured against)
@@ -327,6 +369,7 @@ def run_ours(args, world, rank, local):
                      "algorithmic_bytes_per_launch": bytes_avg, "peak_source": peak_kind},
         "e2e": e2e,
         "plain_gpu": plain,
+        "learned_start": learned,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": launches,
@@ -421,7 +464,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22",
-                    choices=["rmat22", "rmat21", "sweep330", "multi64", "rmat24mixed"])
+                    choices=["rmat22", "rmat21", "sweep330", "multi64", "rmat24mixed", "learned"])
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="device loop of the timed solves (host: one launch per iteration)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -21,10 +21,14 @@
  *     stop, converged, when err < tau
  *   otherwise stop, not converged, after max_iter updates.
  *
- * The iteration is Jacobi-style: every term uses the previous iterate. The
- * in-edge sum runs in CSR order. All sums are plain sequential FP64 sums in
- * vertex order. Optional threads split only the vertex loop, whose entries are
- * independent, so the result is bit-identical for every thread count.
+ * The iteration is Jacobi-style: every term uses the previous iterate. Every
+ * sum (a vertex's in-edge sum in CSR order, the dangling sum and the norms in
+ * vertex order) is a sequential FP64 sum with Neumaier's compensation
+ * (Neumaier 1974): the same sum as written, with its rounding error carried
+ * in a second accumulator, so that long sums over hub rows keep the total
+ * mass at 1 to rounding. Optional threads split only the vertex loop, whose
+ * entries are independent, so the result is bit-identical for every thread
+ * count.
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused and x86-64
  * and aarch64 hosts produce identical bits.
@@ -39,17 +43,28 @@
 
 enum { OR_L1 = 1, OR_L2 = 2, OR_LINF = 3 };
 
+/* Compensated running sum (Neumaier's variant of Kahan summation). */
+typedef struct { double s, c; } csum;
+static inline void csum_add(csum *a, double x) {
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+static inline double csum_get(const csum *a) { return a->s + a->c; }
+
 /* The three norms of a - b (Section 3). out[0] = L1, out[1] = L2, out[2] = Linf. */
 void oracle_norms(int32_t n, const double *a, const double *b, double *out) {
-    double l1 = 0.0, sq = 0.0, mx = 0.0;
+    csum l1 = {0.0, 0.0}, sq = {0.0, 0.0};
+    double mx = 0.0;
     for (int32_t v = 0; v < n; v++) {
         double x = fabs(a[v] - b[v]);
-        l1 += x;
-        sq += x * x;
+        csum_add(&l1, x);
+        csum_add(&sq, x * x);
         if (x > mx) mx = x;
     }
-    out[0] = l1;
-    out[1] = sqrt(sq);
+    out[0] = csum_get(&l1);
+    out[1] = sqrt(csum_get(&sq));
     out[2] = mx;
 }
 
@@ -57,19 +72,20 @@ void oracle_norms(int32_t n, const double *a, const double *b, double *out) {
  * Returns the dangling sum D that entered c0 through *dangling_out. */
 void oracle_step(int32_t n, const int32_t *offsets, const int32_t *sources, const int32_t *outdeg,
                  double alpha, const double *r, double *r_new, double *dangling_out, int nthreads) {
-    double D = 0.0;
+    csum Dc = {0.0, 0.0};
     for (int32_t u = 0; u < n; u++)
-        if (outdeg[u] == 0) D += r[u];
+        if (outdeg[u] == 0) csum_add(&Dc, r[u]);
+    double D = csum_get(&Dc);
     double N = (double)n;
     double c0 = (1.0 - alpha) / N + alpha * D / N;
 #pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
     for (int32_t v = 0; v < n; v++) {
-        double s = 0.0;
+        csum s = {0.0, 0.0};
         for (int32_t e = offsets[v]; e < offsets[v + 1]; e++) {
             int32_t u = sources[e];
-            s += r[u] / (double)outdeg[u];
+            csum_add(&s, r[u] / (double)outdeg[u]);
         }
-        r_new[v] = c0 + alpha * s;
+        r_new[v] = c0 + alpha * csum_get(&s);
     }
     if (dangling_out) *dangling_out = D;
 }
@@ -129,12 +145,14 @@ void oracle_features(int32_t n, const int32_t *offsets, const int32_t *sources, 
                      double alpha, double *feat) {
     for (int32_t v = 0; v < n; v++) {
         int32_t deg = offsets[v + 1] - offsets[v];
-        double sum = 0.0, mx = 0.0;
+        csum sc = {0.0, 0.0};
+        double mx = 0.0;
         for (int32_t e = offsets[v]; e < offsets[v + 1]; e++) {
             double x = log(1.0 + (double)outdeg[sources[e]]);
-            sum += x;
+            csum_add(&sc, x);
             if (x > mx) mx = x;
         }
+        double sum = csum_get(&sc);
         feat[5 * (size_t)v + 0] = log(1.0 + (double)deg);
         feat[5 * (size_t)v + 1] = log(1.0 + (double)outdeg[v]);
         feat[5 * (size_t)v + 2] = deg > 0 ? sum / (double)deg : 0.0;
