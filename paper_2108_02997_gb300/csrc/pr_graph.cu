@@ -80,11 +80,11 @@ bool pr_graph_valid(const pr_graph *g) { return g && registry_has(g) && g->magic
 
 // Tiles of width W (see Tile in pr_internal.cuh). Rows of one in-degree class
 // are packed into warp tiles of at most tile_rows(W) rows and tile_edges(W)
-// in-edges; the lanes of a group (g = es * W lanes, es in-edge slots of W
-// columns each) share one row when the row sums are formed, es sized so that
-// each slot adds about four values. Classes with rows longer than
-// tile_edges(W) are cut into chunks of chunk_edges(W) in-edges, each chunk a
-// warp's tile.
+// in-edges; a group of es lanes shares one row when the row sums are formed
+// (each lane adds every W columns of its in-edges, or every vec_cols of them
+// per column group), es sized so that each lane adds about four in-edges.
+// Classes with rows longer than tile_edges(W) are cut into chunks of
+// chunk_edges(W) in-edges, each chunk a warp's tile.
 pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     int wi = w_index(W);
     if (wi < 0) return pr_fail(PR_EINVAL, "unsupported column width");
@@ -94,7 +94,7 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
         return PR_OK;
     }
     const int TE = tile_edges(W), TR = tile_rows(W), CH = chunk_edges(W);
-    const int max_es = 32 / W;
+    const int max_es = 32;
     std::vector<Tile> tiles;
     std::vector<int32_t> slot_base;
     int32_t n_chunk_slots = 0;
@@ -124,7 +124,7 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
         int es = 1;
         while (es < max_es && es * 4 < cr.max_deg) es <<= 1;
         int glog = 0;
-        while ((1 << glog) < es * W) glog++;
+        while ((1 << glog) < es) glog++;
         int32_t r = cr.begin;
         while (r < cr.end) {
             int32_t r1 = r;

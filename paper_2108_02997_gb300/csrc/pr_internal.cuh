@@ -12,10 +12,11 @@
 constexpr int kBlock = 256;          // threads per CTA of every iteration kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, sum of ranks
-// Warp tiles: a rows tile holds at most kTileValues gathered values (in-edges
-// x columns) and tile_rows(W) rows; longer rows are cut into chunks of
-// chunk_edges(W) in-edges, which one warp strides through kTileValues values
-// at a time. The three sizes are compile-time tuning constants.
+// Warp tiles. One column (W = 1): a rows tile holds at most kTileValues
+// in-edges and 128 rows; longer rows are cut into chunks of kChunkValues
+// in-edges. Several columns (W > 1): a lane reads the values of one in-edge for
+// vec_cols adjacent columns with one vector load, a rows tile holds at most 256
+// in-edges and 192 / W rows, and chunks hold 8192 / W in-edges (at least 256). The sizes are compile-time tuning constants.
 #ifndef PR_TILE_VALUES
 #define PR_TILE_VALUES 256
 #endif
@@ -25,12 +26,42 @@ constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, 
 #ifndef PR_MIN_BLOCKS
 #define PR_MIN_BLOCKS 3
 #endif
+#ifndef PR_VEC_MIN_BLOCKS_4B
+#define PR_VEC_MIN_BLOCKS_4B 3
+#endif
+#ifndef PR_VEC_MIN_BLOCKS_8B
+#define PR_VEC_MIN_BLOCKS_8B 2
+#endif
+#ifndef PR_VEC_GATHER_BATCH
+#define PR_VEC_GATHER_BATCH 4
+#endif
 constexpr int kTileValues = PR_TILE_VALUES;
+// Resident CTAs per SM asked of the compiler for W > 1, by value size: with
+// 8-byte values (df64, FP64) three CTAs force register spills that cost more
+// than the third CTA gains (measured: 1.4-1.8x slower per launch).
+__host__ __device__ constexpr int vec_min_blocks(int vbytes) { return vbytes == 4 ? PR_VEC_MIN_BLOCKS_4B : PR_VEC_MIN_BLOCKS_8B; }
+constexpr int kVecGatherBatch = PR_VEC_GATHER_BATCH;  // vector gathers per lane issued together (W > 1)
 constexpr int kChunkValues = PR_CHUNK_VALUES;
 constexpr int kMinBlocks = PR_MIN_BLOCKS;
-__host__ __device__ constexpr int tile_edges(int W) { return kTileValues / W; }
-__host__ __device__ constexpr int tile_rows(int W) { return 128 / W; }
-__host__ __device__ constexpr int chunk_edges(int W) { return kChunkValues / W; }
+constexpr int kVecTileEdges = 256;
+__host__ __device__ constexpr int tile_edges(int W) { return W == 1 ? kTileValues : kVecTileEdges; }
+__host__ __device__ constexpr int tile_rows(int W) { return W == 1 ? 128 : 192 / W; }
+__host__ __device__ constexpr int chunk_edges(int W) { return W == 1 ? kChunkValues : (8192 / W > 256 ? 8192 / W : 256); }
+
+// Several columns: columns per vector load (16 bytes, or the whole row of W
+// values when that is shorter) for values of vbytes bytes.
+__host__ __device__ constexpr int vec_cols(int vbytes, int W) { return W * vbytes >= 16 ? 16 / vbytes : W; }
+__host__ __device__ constexpr int round16(int b) { return (b + 15) & ~15; }
+// Per-warp shared buffers of a multi-column tile, in bytes and in this order:
+// gathered vectors [kVecTileEdges], row sums [tile_rows * W], previous ranks
+// [tile_rows * W], in-edge sources [kVecTileEdges], row offsets
+// [tile_rows + 1], out-degrees [tile_rows].
+__host__ __device__ constexpr int vec_vals_bytes(int vbytes, int W) { return kVecTileEdges * vec_cols(vbytes, W) * vbytes; }
+__host__ __device__ constexpr int vec_rows_bytes(int vbytes, int W) { return round16(tile_rows(W) * W * vbytes); }
+__host__ __device__ constexpr int vec_warp_bytes(int vbytes, int W) {
+    return vec_vals_bytes(vbytes, W) + 2 * vec_rows_bytes(vbytes, W) + kVecTileEdges * 4 +
+           round16((tile_rows(W) + 1) * 4) + round16(tile_rows(W) * 4);
+}
 
 // ------------------------------------------------------------------ work tiles
 // A tile is one warp's work item of one pass: either a run of consecutive rows

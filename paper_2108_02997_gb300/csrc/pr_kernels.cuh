@@ -48,6 +48,25 @@ template <> __device__ __forceinline__ df64 ld_cg_v<df64>(const df64 *p) {
     return {f.x, f.y};
 }
 
+// CP adjacent column values of one vertex, read with one vector load.
+template <typename V, int CP>
+struct alignas(sizeof(V) * CP) VecV {
+    V v[CP];
+};
+template <typename V, int CP>
+__device__ __forceinline__ VecV<V, CP> load_vec(const V *p) {
+    static_assert(sizeof(VecV<V, CP>) == 16 || sizeof(VecV<V, CP>) == 8, "vector loads are 8 or 16 bytes");
+    VecV<V, CP> r;
+    if constexpr (sizeof(VecV<V, CP>) == 16) {
+        const float4 f = *reinterpret_cast<const float4 *>(p);
+        memcpy(&r, &f, 16);
+    } else {
+        const float2 f = *reinterpret_cast<const float2 *>(p);
+        memcpy(&r, &f, 8);
+    }
+    return r;
+}
+
 template <typename V>
 struct RowAcc {
     using N = Num<V>;
@@ -340,12 +359,13 @@ __global__ void __launch_bounds__(kBlock) pr_init_kernel(JobDev *jobs, GlobalDev
 
 // ---------------------------------------------------------------- the iteration kernel
 template <typename V, int W>
-__global__ void __launch_bounds__(kBlock, kMinBlocks) pr_iter_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
+__global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((int)sizeof(V))) pr_iter_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
     using N = Num<V>;
     static_assert(32 % W == 0, "W must divide the warp");
-    constexpr int VT = kTileValues;          // gathered values per warp tile
-    constexpr int TR = tile_rows(W);
-    constexpr int PER = VT / 32;             // gathers in flight per lane
+    constexpr bool kStaged = (W == 1);       // one column: values staged in shared memory
+    constexpr int VT = kStaged ? kTileValues : 32;   // gathered values per warp step
+    constexpr int TR = kStaged ? tile_rows(W) : 1;
+    constexpr int PER = VT / 32;             // gathers in flight per lane (staged path)
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int col = tid % W;                 // equals lane % W
@@ -363,10 +383,24 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) pr_iter_kernel(JobDev *job
     V *chunk_part = reinterpret_cast<V *>(job.chunk_part);
     uint32_t *chunk_cnt = job.chunk_cnt;
     const int ntiles = job.ntiles, cta_count = job.cta_count;
-    __shared__ V s_vals[kWarps][VT];
-    __shared__ V s_prev[kWarps][TR * W];
-    __shared__ int32_t s_off[kWarps][TR + 1];
-    __shared__ int32_t s_od[kWarps][TR];
+    __shared__ V s_vals[kWarps][kStaged ? VT : 1];
+    __shared__ V s_prev[kWarps][kStaged ? TR * W : 1];
+    __shared__ int32_t s_off[kWarps][kStaged ? TR + 1 : 1];
+    __shared__ int32_t s_od[kWarps][kStaged ? TR : 1];
+    // several columns: per-warp buffers in dynamic shared memory
+    constexpr int CP = vec_cols((int)sizeof(V), W);   // columns per vector load
+    constexpr int NG = W / CP;                          // column groups (passes over a tile)
+    constexpr int VTR = tile_rows(W);
+    using VV = VecV<V, CP>;
+    extern __shared__ __align__(16) unsigned char pr_dyn_smem[];
+    unsigned char *wbase = pr_dyn_smem + (size_t)warp * vec_warp_bytes((int)sizeof(V), W);
+    VV *v_vals = reinterpret_cast<VV *>(wbase);
+    V *v_rsum = reinterpret_cast<V *>(wbase + vec_vals_bytes((int)sizeof(V), W));
+    V *v_prev = reinterpret_cast<V *>(wbase + vec_vals_bytes((int)sizeof(V), W) + vec_rows_bytes((int)sizeof(V), W));
+    int32_t *v_src = reinterpret_cast<int32_t *>(wbase + vec_vals_bytes((int)sizeof(V), W) +
+                                                 2 * vec_rows_bytes((int)sizeof(V), W));
+    int32_t *v_off = v_src + kVecTileEdges;
+    int32_t *v_od = v_off + round16((VTR + 1) * 4) / 4;
 
     // Loop guard independent of the pass bookkeeping: should the job
     // finalizers ever fail to stop the graph's while-loop, the launch after the
@@ -383,12 +417,84 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) pr_iter_kernel(JobDev *job
     RowAcc<V> acc;
     acc.init();
     const bool work = job.alive && !*(volatile int32_t *)&glob->error;
+    // several columns: the active columns read the job's shared buffer parity
+    const unsigned int act_mask = __ballot_sync(0xffffffffu, cv.active);
+    const V *c_all = reinterpret_cast<const V *>(job.contrib[job.cur]);
 
     if (work) {
         const int wstride = cta_count * kWarps;
         for (int t = local * kWarps + warp; t < ntiles; t += wstride) {
             const Tile T = tiles[t];
-            if (T.glog >= 0) {
+            if constexpr (!kStaged) {
+                if (T.glog >= 0) {
+                    // ---------------- rows tile, several columns. Sources,
+                    // offsets, out-degrees and previous ranks are staged first;
+                    // then per column group: one vector gather per in-edge (eight
+                    // per lane in flight) into shared memory, and lane groups add
+                    // each row's vectors; last, lane (row, column) pairs update rows.
+                    const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
+#pragma unroll
+                    for (int k = 0; k < kVecTileEdges / 32; k++) {
+                        const int i = lane + 32 * k;
+                        if (i < ne) v_src[i] = src[T.e0 + i];
+                    }
+                    for (int i = lane; i <= nr; i += 32) v_off[i] = off[T.r0 + i] - T.e0;
+                    for (int i = lane; i < nr; i += 32) v_od[i] = outdeg[T.r0 + i];
+                    if (need_prev)
+                        for (int i = lane; i < nr * W; i += 32) v_prev[i] = cv.r_prev[(size_t)T.r0 * W + i];
+                    __syncwarp();
+                    const int g = 1 << T.glog;
+                    const int es = lane & (g - 1);
+                    const int rpp = 32 >> T.glog;
+#pragma unroll 1
+                    for (int cg = 0; cg < NG; cg++) {
+                        if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
+#pragma unroll
+                        for (int k0 = 0; k0 < kVecTileEdges / 32; k0 += kVecGatherBatch) {
+                            VV x[kVecGatherBatch];
+#pragma unroll
+                            for (int k = 0; k < kVecGatherBatch; k++) {
+                                const int i = lane + 32 * (k0 + k);
+                                if (i < ne) x[k] = load_vec<V, CP>(c_all + (size_t)v_src[i] * W + cg * CP);
+                            }
+#pragma unroll
+                            for (int k = 0; k < kVecGatherBatch; k++) {
+                                const int i = lane + 32 * (k0 + k);
+                                if (i < ne) v_vals[i] = x[k];
+                            }
+                        }
+                        __syncwarp();
+                        for (int rb = 0; rb < nr; rb += rpp) {
+                            const int r = rb + (lane >> T.glog);
+                            const bool valid = r < nr;
+                            EdgeSum<V> sum[CP];
+#pragma unroll
+                            for (int j = 0; j < CP; j++) sum[j].init();
+                            if (valid) {
+                                const int lo = v_off[r], hi = v_off[r + 1];
+                                for (int e = lo + es; e < hi; e += g) {
+                                    const VV y = v_vals[e];
+#pragma unroll
+                                    for (int j = 0; j < CP; j++) sum[j].add(y.v[j]);
+                                }
+                            }
+#pragma unroll
+                            for (int j = 0; j < CP; j++) {
+                                V sv = sum[j].get();
+                                for (int m = 1; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                                if (valid && es == 0) v_rsum[r * W + cg * CP + j] = sv;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    if (need_prev)
+                        for (int i = lane; i < nr * W; i += 32)
+                            row_update_pd<V, W>(perm, cv, acc, T.r0 + i / W, col, v_rsum[i], v_prev[i], v_od[i / W]);
+                    __syncwarp();
+                    continue;
+                }
+            }
+            if (kStaged && T.glog >= 0) {
                 // ---------------- rows tile: indices, offsets, previous ranks
                 // and out-degrees are all requested before any gather waits
                 const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
@@ -437,7 +543,43 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) pr_iter_kernel(JobDev *job
                 const int nv = (T.e1 - T.e0) * W;
                 EdgeSum<V> sum;
                 sum.init();
-                if (cv.active) {
+                if constexpr (!kStaged) {
+                    // several columns: per column group, lanes stride over the
+                    // chunk's in-edges with vector loads, four in flight
+                    const int ne = T.e1 - T.e0;
+#pragma unroll 1
+                    for (int cg = 0; cg < NG; cg++) {
+                        if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
+                        EdgeSum<V> vs[CP];
+#pragma unroll
+                        for (int j = 0; j < CP; j++) vs[j].init();
+                        const V *cb = c_all + cg * CP;
+                        int i = lane;
+                        for (; i + 96 < ne; i += 128) {
+                            const int32_t u0 = src[T.e0 + i], u1 = src[T.e0 + i + 32];
+                            const int32_t u2 = src[T.e0 + i + 64], u3 = src[T.e0 + i + 96];
+                            const VV x0 = load_vec<V, CP>(cb + (size_t)u0 * W), x1 = load_vec<V, CP>(cb + (size_t)u1 * W);
+                            const VV x2 = load_vec<V, CP>(cb + (size_t)u2 * W), x3 = load_vec<V, CP>(cb + (size_t)u3 * W);
+#pragma unroll
+                            for (int j = 0; j < CP; j++) {
+                                vs[j].add(x0.v[j]); vs[j].add(x1.v[j]); vs[j].add(x2.v[j]); vs[j].add(x3.v[j]);
+                            }
+                        }
+                        for (; i < ne; i += 32) {
+                            const VV x0 = load_vec<V, CP>(cb + (size_t)src[T.e0 + i] * W);
+#pragma unroll
+                            for (int j = 0; j < CP; j++) vs[j].add(x0.v[j]);
+                        }
+#pragma unroll
+                        for (int j = 0; j < CP; j++) {
+                            V sv = vs[j].get();
+                            for (int m = 1; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                            if (lane == 0) v_rsum[cg * CP + j] = sv;
+                        }
+                    }
+                    __syncwarp();
+                }
+                if (kStaged && cv.active) {
                     for (int base = lane; base < nv; base += VT) {
                         int32_t u[PER];
 #pragma unroll
@@ -454,7 +596,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) pr_iter_kernel(JobDev *job
                     }
                 }
                 V sv = sum.get();
-                for (int m = W; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                if constexpr (kStaged) {
+                    for (int m = W; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                } else {
+                    if (lane < W) sv = v_rsum[lane];
+                    __syncwarp();
+                }
                 if (T.slot < 0) {
                     if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, sv);
                 } else {

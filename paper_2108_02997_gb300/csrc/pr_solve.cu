@@ -118,7 +118,13 @@ void *pr_init_kernel_for(int prec, int W) {
         default: return init_ptr<df64>(W);
     }
 }
-size_t pr_tile_smem_bytes(int, int) { return 0; }   // the kernels use static shared memory only
+// One column: static shared memory only. Several columns: the per-warp tile
+// buffers (vec_warp_bytes) in dynamic shared memory.
+size_t pr_tile_smem_bytes(int prec, int W) {
+    if (W == 1) return 0;
+    const int vbytes = prec == PR_PREC_FP32 ? 4 : 8;
+    return (size_t)kWarps * vec_warp_bytes(vbytes, W);
+}
 
 // Opt the iteration kernel into its dynamic shared memory (once per process
 // and instantiation) and report its resident CTAs per SM.
