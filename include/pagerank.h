@@ -90,6 +90,30 @@ typedef enum pr_loop {
                              baseline; also used to time single launches) */
 } pr_loop;
 
+/* How pr_solve_batch packs its columns (iterate sequences) into jobs. A job
+ * holds up to W columns of one graph as an N x W vertex-major matrix, so that
+ * one read of a row's in-edge indices serves all W columns; every job of a
+ * solve advances in the same kernel launches, and a job stops costing time
+ * once its last column has stopped. Packing columns whose iteration counts
+ * differ makes the short ones wait on the long one, and a wide job gathers
+ * more bytes per in-edge, so the best packing depends on the graph.
+ * Grouping changes only the order of floating-point additions: every
+ * grouping meets the same accuracy bounds. */
+typedef enum pr_group {
+    PR_GROUP_AUTO = 0,    /* default: per graph, columns sorted by the estimated
+                             iteration count log(tau)/log(alpha) (Section 1) are
+                             cut into the contiguous jobs that minimise the sum
+                             over jobs of (iterations x launch time at the job's
+                             width); launch times come from pr_graph_tune, run
+                             automatically the first time a graph with two or
+                             more columns meets this mode (cached per process by
+                             graph signature: vertices, edges and in-degree
+                             class layout). The grouping can differ between
+                             processes, hence so can the last bits. */
+    PR_GROUP_PACK = 1,    /* the columns of each graph packed 32 at a time */
+    PR_GROUP_SINGLE = 2   /* one column per job (W = 1) */
+} pr_group;
+
 typedef struct pr_mlp pr_mlp;   /* learned warm start, see pr_mlp_* below */
 
 typedef struct pr_options {
@@ -111,7 +135,8 @@ typedef struct pr_options {
     double *err_history;        /* pr_solve only, optional host buffer of
                                    3*max_iter doubles: row i-1 = (L1, L2, Linf)
                                    of r^i - r^{i-1} */
-    int32_t reserved[8];        /* zero */
+    int32_t group;              /* pr_group; default PR_GROUP_AUTO */
+    int32_t reserved[7];        /* zero */
 } pr_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -262,6 +287,38 @@ pr_status pr_mlp_loss_grad(const pr_mlp *m, const pr_graph *g, double alpha, con
 pr_status pr_mlp_train(pr_mlp *m, const pr_graph *const *graphs, const double *alphas,
                        const double *const *targets, int32_t nsets, int32_t epochs, float lr,
                        float *loss_out, void *stream);
+
+/*
+ * Autotuning of the column width (no counterpart in the paper, which solves
+ * one instance at a time): times the iteration kernel on graph g for the
+ * widths W = 1, 2, 4, ..., max_width (a power of two, 1..32) in `precision`
+ * (PR_PREC_DF64, PR_PREC_FP64 or PR_PREC_FP32; PR_PREC_MIXED tunes FP32 and
+ * DF64 and reports DF64), by solving W synthetic columns (alpha 0.85, uniform
+ * start) for a few iterations with one launch per iteration on `stream`.
+ *   us_out : NULL or 6 doubles: microseconds per launch for W = 1 .. 32;
+ *            0 for widths not measured (above max_width, or skipped because
+ *            the W-column workspace would exceed a quarter of the free device
+ *            memory)
+ * Results are cached per process and device by graph signature; widths
+ * already measured are not timed again. Errors: PR_ESTATE for a bad handle,
+ * PR_EINVAL for a bad precision or width, PR_ENOMEM / PR_ECUDA from the
+ * timing solves.
+ */
+pr_status pr_graph_tune(pr_graph *g, int32_t precision, int32_t max_width, void *stream, double *us_out);
+
+/*
+ * The planner behind PR_GROUP_AUTO, on host data only (no device work):
+ * given `count` columns of one graph with estimated iteration counts
+ * iters[c] > 0 and launch times us_per_launch[k] for width 2^k (k = 0..5;
+ * <= 0 marks a width as unavailable, and width 1 must be available), cuts
+ * the columns, sorted by decreasing iters (ties by index), into contiguous
+ * jobs of at most 32 minimising sum over jobs of max(iters) x us_per_launch at
+ * the smallest available width holding the job. Writes job_of[c] (jobs
+ * numbered 0.. in sorted order) and width_of[c] (the job's width); *cost_out
+ * (may be NULL) receives the minimum. PR_EINVAL on a bad argument.
+ */
+pr_status pr_plan_columns(int32_t count, const double *iters, const double *us_per_launch, int32_t *job_of,
+                          int32_t *width_of, double *cost_out);
 
 /*
  * Counters of the last solve on any thread (host pointers, each may be NULL):

@@ -27,7 +27,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
 
-CU_SOURCES = ["pr_api.cu", "pr_graph.cu", "pr_solve.cu", "pr_learn.cu", "pr_noalloc.cu"]
+CU_SOURCES = ["pr_api.cu", "pr_graph.cu", "pr_solve.cu", "pr_learn.cu", "pr_noalloc.cu", "pr_plan.cu"]
 CU_HEADERS = ["pr_internal.cuh", "pr_kernels.cuh", "df64.cuh"]
 
 

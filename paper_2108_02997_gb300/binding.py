@@ -26,6 +26,8 @@ PR_NORM_L1, PR_NORM_L2, PR_NORM_LINF = 1, 2, 3
 PR_PREC_DF64, PR_PREC_FP64, PR_PREC_MIXED, PR_PREC_FP32 = 0, 1, 2, 3
 PR_INIT_UNIFORM, PR_INIT_USER, PR_INIT_LEARNED = 0, 1, 2
 PR_LOOP_GRAPH, PR_LOOP_HOST = 0, 1
+PR_GROUP_AUTO, PR_GROUP_PACK, PR_GROUP_SINGLE = 0, 1, 2
+GROUPS = {"auto": PR_GROUP_AUTO, "pack": PR_GROUP_PACK, "single": PR_GROUP_SINGLE}
 PRECISIONS = {"df64": PR_PREC_DF64, "fp64": PR_PREC_FP64, "mixed": PR_PREC_MIXED, "fp32": PR_PREC_FP32}
 NORMS = {"L1": 1, "L2": 2, "Linf": 3, 1: 1, 2: 2, 3: 3}
 MLP_PARAMS = 64 * 5 + 64 + 64 * 64 + 64 + 64 + 1
@@ -36,7 +38,7 @@ class pr_options(C.Structure):
                 ("init_on_device", C.c_int32), ("outputs_on_device", C.c_int32),
                 ("switch_tol", C.c_double), ("stream", C.c_void_p),
                 ("share_trajectories", C.c_int32), ("loop", C.c_int32), ("mlp", C.c_void_p),
-                ("err_history", C.c_void_p), ("reserved", C.c_int32 * 8)]
+                ("err_history", C.c_void_p), ("group", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class pr_instance(C.Structure):
@@ -72,6 +74,8 @@ SIGNATURES = {
     "pr_mlp_train": ([_vp, _vp, _vp, _vp, _i32, _i32, _f, _vp, _vp], _i32),
     "pr_mlp_loss_grad": ([_vp, _vp, _d, _vp, _vp, _vp, _vp], _i32),
     "pr_last_solve_stats": ([_vp, _vp, _vp, _vp], _i32),
+    "pr_graph_tune": ([_vp, _i32, _i32, _vp, _vp], _i32),
+    "pr_plan_columns": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "pr_solve_noalloc": ([_vp, _d, _d, _i32, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "pr_last_error": ([], C.c_char_p),
     "pr_status_string": ([_i32], C.c_char_p),
@@ -181,8 +185,9 @@ class SolveResult:
 
 
 def _make_options(precision="df64", init=None, loop="graph", stream=None, share=True, switch_tol=1e-6,
-                  outputs_on_device=False, mlp=None):
+                  outputs_on_device=False, mlp=None, group="auto"):
     o = default_options()
+    o.group = GROUPS[group] if isinstance(group, str) else int(group)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.loop = PR_LOOP_HOST if loop == "host" else PR_LOOP_GRAPH
     o.share_trajectories = 1 if share else 0
@@ -242,7 +247,7 @@ class Instance:
 
 
 def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=None, share=True,
-                   switch_tol=1e-6, outputs_on_device=False, mlp=None, check=True):
+                   switch_tol=1e-6, outputs_on_device=False, mlp=None, check=True, group="auto"):
     """Solve many instances together. Fills ``out`` (allocated as numpy, or as
     torch CUDA tensors when ``outputs_on_device``), ``iters``, ``err``,
     ``converged`` and ``status`` of every :class:`Instance`; returns the
@@ -273,7 +278,7 @@ def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=N
             keep.append(x.init)
     if stream is None and any_dev:
         stream = current_stream_ptr()
-    o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, outputs_on_device, mlp)
+    o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, outputs_on_device, mlp, group)
     if any(x.init is not None for x in insts) and o.init == PR_INIT_UNIFORM:
         o.init = PR_INIT_USER
     st = lib().pr_solve_batch(arr, len(insts), C.byref(o))
@@ -286,6 +291,29 @@ def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=N
     if check:
         _check(st, "pr_solve_batch")
     return st
+
+
+def pr_graph_tune(g: "Graph", precision="df64", max_width: int = 32, stream=None):
+    """Launch times (microseconds) of the iteration kernel on ``g`` for widths
+    1, 2, 4, 8, 16, 32 (0 = not measured); measured once per graph signature."""
+    us = (C.c_double * 6)()
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().pr_graph_tune(g.handle, p, int(max_width), stream, us), "pr_graph_tune")
+    return list(us)
+
+
+def plan_columns(iters, us_per_launch):
+    """The PR_GROUP_AUTO planner on host data: (job_of, width_of, cost)."""
+    it = np.ascontiguousarray(iters, np.float64)
+    us = np.ascontiguousarray(us_per_launch, np.float64)
+    if us.size != 6:
+        raise ValueError("need 6 launch times (W = 1 .. 32)")
+    job = np.empty(it.size, np.int32)
+    wid = np.empty(it.size, np.int32)
+    cost = C.c_double()
+    _check(lib().pr_plan_columns(it.size, it.ctypes.data, us.ctypes.data, job.ctypes.data, wid.ctypes.data,
+                                 C.byref(cost)), "pr_plan_columns")
+    return job, wid, cost.value
 
 
 def pr_last_solve_stats():

@@ -69,6 +69,7 @@ extern "C" void pr_options_default(pr_options *opt) {
     opt->switch_tol = 1e-6;
     opt->share_trajectories = 1;
     opt->loop = PR_LOOP_GRAPH;
+    opt->group = PR_GROUP_AUTO;
 }
 
 // Implemented in pr_learn.cu.
@@ -81,6 +82,7 @@ pr_status check_options(const pr_options &o) {
     if (o.precision < PR_PREC_DF64 || o.precision > PR_PREC_FP32) return pr_fail(PR_EINVAL, "unknown precision");
     if (o.init < PR_INIT_UNIFORM || o.init > PR_INIT_LEARNED) return pr_fail(PR_EINVAL, "unknown init mode");
     if (o.loop != PR_LOOP_GRAPH && o.loop != PR_LOOP_HOST) return pr_fail(PR_EINVAL, "unknown loop mode");
+    if (o.group < PR_GROUP_AUTO || o.group > PR_GROUP_SINGLE) return pr_fail(PR_EINVAL, "unknown group mode");
     if (o.precision == PR_PREC_MIXED && !(o.switch_tol > 0.0 && std::isfinite(o.switch_tol)))
         return pr_fail(PR_EINVAL, "switch_tol must be positive and finite");
     if (o.init == PR_INIT_LEARNED && !pr_mlp_valid(o.mlp)) return pr_fail(PR_EINVAL, "PR_INIT_LEARNED needs a live pr_mlp");
@@ -211,13 +213,40 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
         req.cols[0].hist_host = hist_host;
         req.cols[0].hist_cap = hist_cap;
     }
-    std::vector<std::vector<Tap>> taps;
-    s = pr_run_solve(req, taps);
-    if (s != PR_OK) {
-        std::string msg = pr_last_error();
-        for (auto &c : req.cols)
-            for (int i : c.inst) inst[i].status = s;
-        return pr_fail(s, msg);
+    // ---- jobs: the grouping plan, one sub-solve per job width
+    std::vector<std::vector<Tap>> taps(req.cols.size());
+    {
+        auto fail_all = [&](pr_status fs) {
+            std::string msg = pr_last_error();
+            for (auto &c : req.cols)
+                for (int i : c.inst) inst[i].status = fs;
+            return pr_fail(fs, msg);
+        };
+        std::vector<SubSolve> plan;
+        if (!req.cols.empty() && (s = pr_plan_request(req, opt.group, plan)) != PR_OK) return fail_all(s);
+        SolveStats total;
+        for (const SubSolve &sp : plan) {
+            SolveRequest sub;
+            sub.precision = req.precision;
+            sub.loop = req.loop;
+            sub.switch_tol = req.switch_tol;
+            sub.stream = req.stream;
+            std::vector<int> cmap;   // sub-request column -> request column
+            for (const auto &jc : sp.jobs) {
+                std::vector<int> local;
+                for (int c : jc) {
+                    local.push_back((int)sub.cols.size());
+                    cmap.push_back(c);
+                    sub.cols.push_back(req.cols[c]);
+                }
+                sub.jobs.push_back(local);
+            }
+            std::vector<std::vector<Tap>> sub_taps;
+            if ((s = pr_run_solve(sub, sub_taps)) != PR_OK) return fail_all(s);
+            for (size_t k = 0; k < cmap.size(); k++) taps[cmap[k]] = sub_taps[k];
+            total.add(sub.stats);
+        }
+        pr_record_last_stats(total);
     }
     for (size_t c = 0; c < req.cols.size(); c++)
         for (size_t q = 0; q < req.cols[c].inst.size(); q++) {

@@ -351,6 +351,26 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
         free_graph(g);
         return pr_cuda_fail(e, "graph relabel");
     }
+    // signature for caches keyed by graph shape: FNV-1a over n, nnz and each
+    // in-degree class's (first row, end row, largest in-degree, edges)
+    {
+        uint64_t h = 1469598103934665603ull;
+        auto mix = [&h](uint64_t x) {
+            for (int b = 0; b < 8; b++) {
+                h ^= (x >> (8 * b)) & 0xffu;
+                h *= 1099511628211ull;
+            }
+        };
+        mix((uint64_t)n);
+        mix((uint64_t)nnz);
+        for (const ClassRange &cr : g->classes) {
+            mix((uint64_t)cr.begin);
+            mix((uint64_t)cr.end);
+            mix((uint64_t)cr.max_deg);
+            mix((uint64_t)(new_off[cr.end] - new_off[cr.begin]));
+        }
+        g->signature = h;
+    }
     g->h_off.swap(new_off);
     // the single-column work table is built now so that solves on this graph
     // never need to allocate it later

@@ -186,6 +186,7 @@ struct pr_graph {
     std::vector<ClassRange> classes; // in-degree classes in relabelled order
     std::vector<int32_t> h_off;      // relabelled offsets (host copy, for tile tables)
     TileTable tables[6];             // W = 1, 2, 4, 8, 16, 32
+    uint64_t signature = 0;          // hash of n, nnz and the in-degree class layout
 };
 constexpr uint32_t kGraphMagic = 0x50524731u;   // "PRG1"
 constexpr uint32_t kMlpMagic = 0x50524d31u;     // "PRM1"
@@ -223,15 +224,39 @@ struct SolveColumn {
     int32_t hist_cap = 0;
 };
 
+// Launch accounting of one solve (or the sum over a request's sub-solves).
+struct SolveStats {
+    int launches = 0;       // kernel launches, init passes included
+    int passes = 0;         // iteration passes the device performed
+    double kernel_ms = 0.0; // PR_LOOP_HOST: sum of the iteration launches' event times
+    double total_ms = 0.0;  // device time of the whole solve
+    void add(const SolveStats &o) {
+        launches += o.launches; passes += o.passes; kernel_ms += o.kernel_ms; total_ms += o.total_ms;
+    }
+};
+
 struct SolveRequest {
     int precision = PR_PREC_DF64;
     int loop = PR_LOOP_GRAPH;
     double switch_tol = 1e-6;
     cudaStream_t stream = nullptr;
     std::vector<SolveColumn> cols;
+    // Optional explicit jobs: lists of column indices, all on one graph, at most
+    // 32 each; empty = the columns of each graph packed 32 at a time.
+    std::vector<std::vector<int>> jobs;
+    SolveStats stats;       // out
 };
 
 pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out);
+void pr_record_last_stats(const SolveStats &s);
+
+// Column grouping (pr_plan.cu). A sub-solve is one pr_run_solve: jobs of one
+// width W, given as lists of request column indices.
+struct SubSolve {
+    int W = 1;
+    std::vector<std::vector<int>> jobs;
+};
+pr_status pr_plan_request(const SolveRequest &req, int group, std::vector<SubSolve> &plan);
 
 // Kernel selection and launch geometry (pr_solve.cu)
 void *pr_iter_kernel_for(int precision, int W);

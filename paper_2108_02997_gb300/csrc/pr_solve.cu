@@ -92,15 +92,10 @@ struct HostJob {
     int hist_total = 0;
 };
 
-struct LoopStats {
-    int launches = 0;
-    int passes = 0;
-    double kernel_ms = 0.0;
-    double total_ms = 0.0;
-};
+using LoopStats = SolveStats;
 
 std::mutex g_stats_mu;
-LoopStats g_last_stats;
+SolveStats g_last_stats;
 
 }  // namespace
 
@@ -145,6 +140,11 @@ pr_status pr_kernel_setup(int prec, int W, int *blocks_per_sm) {
     PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBlock, smem));
     *blocks_per_sm = std::max(occ, 1);
     return PR_OK;
+}
+
+void pr_record_last_stats(const SolveStats &st) {
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    g_last_stats = st;
 }
 
 extern "C" pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms) {
@@ -265,7 +265,17 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     const int prec1 = mixed ? PR_PREC_FP32 : req.precision;
     // ---- group columns into jobs (same graph, <= 32 columns)
     std::vector<HostJob> jobs;
-    {
+    if (!req.jobs.empty()) {
+        for (const auto &jc : req.jobs) {
+            if (jc.empty() || jc.size() > 32) return pr_fail(PR_EINVAL, "internal: job of bad size");
+            HostJob j;
+            j.g = req.cols[jc[0]].g;
+            for (int c : jc)
+                if (c < 0 || c >= ncols || req.cols[c].g != j.g) return pr_fail(PR_EINVAL, "internal: bad job column");
+            j.cols = jc;
+            jobs.push_back(j);
+        }
+    } else {
         std::map<const pr_graph *, std::vector<int>> by_graph;
         std::vector<const pr_graph *> order;
         for (int c = 0; c < ncols; c++) {
@@ -515,9 +525,6 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         }
     }
     PR_CUDA(cudaStreamSynchronize(st));
-    {
-        std::lock_guard<std::mutex> lk(g_stats_mu);
-        g_last_stats = stats;
-    }
+    req.stats = stats;
     return PR_OK;
 }

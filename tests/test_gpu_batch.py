@@ -122,3 +122,48 @@ def test_invalid_instance_reports_its_status(B, er):
         st = B.pr_solve_batch([good, bad], check=False)
         assert st == B.PR_EINVAL and bad.status == B.PR_EINVAL
         assert good.status == 0 and good.converged
+
+
+@pytest.mark.parametrize("group", ["auto", "pack", "single"])
+def test_grouping_modes_match_oracle(B, orc, gg, group):
+    """Every grouping of a 12-column alpha x tau batch on two graphs (jobs of
+    several widths, run as separate sub-solves under "auto") meets parity."""
+    g1 = gg.rmat(15, 16, seed=41)
+    g2 = gg.erdos_renyi(20000, 160000, 900, 42)
+    specs = [(gi, a, t, nm) for gi in (0, 1) for a, t, nm in
+             ((0.5, 1e-9, 1), (0.7, 1e-10, 2), (0.85, 1e-10, 1), (0.9, 1e-8, 3), (0.95, 1e-10, 1), (0.99, 1e-7, 2))]
+    graphs = [g1, g2]
+    dgs = [B.Graph.from_csr(g) for g in graphs]
+    insts = [B.Instance(dgs[gi], a, t, nm, 500) for gi, a, t, nm in specs]
+    B.pr_solve_batch(insts, group=group)
+    for (gi, a, t, nm), x in zip(specs, insts):
+        ref = orc.pagerank(graphs[gi], a, t, nm, 500, history=True, threads=orc.default_threads())
+        assert_fp64_parity(x.out, x.iters, x.err, ref, t, nm, f"{group} graph {gi} alpha {a}")
+    for d in dgs:
+        d.close()
+
+
+@pytest.mark.parametrize("group", ["auto", "pack", "single"])
+def test_grouping_modes_mixed_precision(B, orc, gg, group):
+    g = gg.rmat(14, 16, seed=43)
+    alphas = (0.6, 0.8, 0.85, 0.9, 0.95)
+    refs = {a: orc.pagerank(g, a, 1e-13, 1, 10000) for a in alphas}
+    with B.Graph.from_csr(g) as dg:
+        insts = [B.Instance(dg, a, 1e-10, 1, 500) for a in alphas]
+        B.pr_solve_batch(insts, precision="mixed", group=group)
+        for a, x in zip(alphas, insts):
+            assert x.converged
+            assert np.abs(x.out - refs[a].ranks).sum() <= bound_l1(a, 1e-10, 1, x.err_l1)
+
+
+def test_graph_tune_measures_and_caches(B, gg):
+    g = gg.rmat(14, 16, seed=44)
+    with B.Graph.from_csr(g) as dg:
+        t1 = B.pr_graph_tune(dg, "df64", 8)
+        assert all(t > 0 for t in t1[:4]) and t1[4] == 0 and t1[5] == 0
+        t2 = B.pr_graph_tune(dg, "df64", 8)
+        assert t2 == t1                                   # cached, not timed again
+        with B.Graph.from_csr(g) as dg2:                  # same signature: same entry
+            assert B.pr_graph_tune(dg2, "df64", 4)[:3] == t1[:3]
+        with pytest.raises(B.PageRankError):
+            B.pr_graph_tune(dg, "df64", 3)
