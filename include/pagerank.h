@@ -321,6 +321,15 @@ pr_status pr_plan_columns(int32_t count, const double *iters, const double *us_p
                           int32_t *width_of, double *cost_out);
 
 /*
+ * Resident CTAs per SM of the iteration kernel for `precision` (PR_PREC_DF64,
+ * PR_PREC_FP64 or PR_PREC_FP32) and column width `width` (1, 2, 4, .., 32) on
+ * the current device, as the CUDA occupancy calculator reports it for the
+ * kernel's 256 threads and shared memory; solves size their grids as this
+ * times the SM count. PR_EINVAL for a bad argument, PR_ECUDA on failure.
+ */
+pr_status pr_kernel_occupancy(int32_t precision, int32_t width, int32_t *ctas_per_sm);
+
+/*
  * Counters of the last solve on any thread (host pointers, each may be NULL):
  *   launches  : iteration-kernel launches (init passes included)
  *   passes    : iteration passes executed on the device

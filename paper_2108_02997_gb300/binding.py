@@ -75,6 +75,7 @@ SIGNATURES = {
     "pr_mlp_loss_grad": ([_vp, _vp, _d, _vp, _vp, _vp, _vp], _i32),
     "pr_last_solve_stats": ([_vp, _vp, _vp, _vp], _i32),
     "pr_graph_tune": ([_vp, _i32, _i32, _vp, _vp], _i32),
+    "pr_kernel_occupancy": ([_i32, _i32, _vp], _i32),
     "pr_plan_columns": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "pr_solve_noalloc": ([_vp, _d, _d, _i32, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "pr_last_error": ([], C.c_char_p),
@@ -300,6 +301,14 @@ def pr_graph_tune(g: "Graph", precision="df64", max_width: int = 32, stream=None
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     _check(lib().pr_graph_tune(g.handle, p, int(max_width), stream, us), "pr_graph_tune")
     return list(us)
+
+
+def kernel_occupancy(precision="df64", width: int = 1) -> int:
+    """Resident CTAs per SM of the iteration kernel (needs a GPU)."""
+    c = C.c_int32()
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().pr_kernel_occupancy(p, int(width), C.byref(c)), "pr_kernel_occupancy")
+    return c.value
 
 
 def plan_columns(iters, us_per_launch):

@@ -26,6 +26,12 @@ constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, 
 #ifndef PR_MIN_BLOCKS
 #define PR_MIN_BLOCKS 3
 #endif
+#ifndef PR_PREFETCH_TILE
+#define PR_PREFETCH_TILE 1
+#endif
+#ifndef PR_SMEM_CARVEOUT
+#define PR_SMEM_CARVEOUT -1
+#endif
 #ifndef PR_VEC_MIN_BLOCKS_4B
 #define PR_VEC_MIN_BLOCKS_4B 3
 #endif
@@ -35,6 +41,10 @@ constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, 
 #ifndef PR_VEC_GATHER_BATCH
 #define PR_VEC_GATHER_BATCH 4
 #endif
+constexpr bool kPrefetchTile = PR_PREFETCH_TILE != 0;  // load the next tile's descriptor a tile ahead
+// Shared-memory carveout requested for kernels with dynamic shared memory
+// (percent; -1 leaves the driver's choice).
+constexpr int kSmemCarveout = PR_SMEM_CARVEOUT;
 constexpr int kTileValues = PR_TILE_VALUES;
 // Resident CTAs per SM asked of the compiler for W > 1, by value size: with
 // 8-byte values (df64, FP64) three CTAs force register spills that cost more

@@ -48,6 +48,13 @@ template <> __device__ __forceinline__ df64 ld_cg_v<df64>(const df64 *p) {
     return {f.x, f.y};
 }
 
+// A work tile's descriptor: two 16-byte loads.
+__device__ __forceinline__ Tile load_tile(const Tile *p) {
+    const int4 a = __ldg(reinterpret_cast<const int4 *>(p));
+    const int4 b = __ldg(reinterpret_cast<const int4 *>(p) + 1);
+    return Tile{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+}
+
 // CP adjacent column values of one vertex, read with one vector load.
 template <typename V, int CP>
 struct alignas(sizeof(V) * CP) VecV {
@@ -423,80 +430,77 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
 
     if (work) {
         const int wstride = cta_count * kWarps;
-        for (int t = local * kWarps + warp; t < ntiles; t += wstride) {
-            const Tile T = tiles[t];
+        // ---------------- rows tile, several columns. Sources, offsets,
+        // out-degrees and previous ranks are staged first; then per column
+        // group: one vector gather per in-edge into shared memory, and lane
+        // groups add each row's vectors; last, lane (row, column) pairs update rows.
+        auto rows_tile_vec = [&](const Tile &T) {
             if constexpr (!kStaged) {
-                if (T.glog >= 0) {
-                    // ---------------- rows tile, several columns. Sources,
-                    // offsets, out-degrees and previous ranks are staged first;
-                    // then per column group: one vector gather per in-edge (eight
-                    // per lane in flight) into shared memory, and lane groups add
-                    // each row's vectors; last, lane (row, column) pairs update rows.
-                    const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
+                const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
 #pragma unroll
-                    for (int k = 0; k < kVecTileEdges / 32; k++) {
-                        const int i = lane + 32 * k;
-                        if (i < ne) v_src[i] = src[T.e0 + i];
-                    }
-                    for (int i = lane; i <= nr; i += 32) v_off[i] = off[T.r0 + i] - T.e0;
-                    for (int i = lane; i < nr; i += 32) v_od[i] = outdeg[T.r0 + i];
-                    if (need_prev)
-                        for (int i = lane; i < nr * W; i += 32) v_prev[i] = cv.r_prev[(size_t)T.r0 * W + i];
-                    __syncwarp();
-                    const int g = 1 << T.glog;
-                    const int es = lane & (g - 1);
-                    const int rpp = 32 >> T.glog;
-#pragma unroll 1
-                    for (int cg = 0; cg < NG; cg++) {
-                        if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
-#pragma unroll
-                        for (int k0 = 0; k0 < kVecTileEdges / 32; k0 += kVecGatherBatch) {
-                            VV x[kVecGatherBatch];
-#pragma unroll
-                            for (int k = 0; k < kVecGatherBatch; k++) {
-                                const int i = lane + 32 * (k0 + k);
-                                if (i < ne) x[k] = load_vec<V, CP>(c_all + (size_t)v_src[i] * W + cg * CP);
-                            }
-#pragma unroll
-                            for (int k = 0; k < kVecGatherBatch; k++) {
-                                const int i = lane + 32 * (k0 + k);
-                                if (i < ne) v_vals[i] = x[k];
-                            }
-                        }
-                        __syncwarp();
-                        for (int rb = 0; rb < nr; rb += rpp) {
-                            const int r = rb + (lane >> T.glog);
-                            const bool valid = r < nr;
-                            EdgeSum<V> sum[CP];
-#pragma unroll
-                            for (int j = 0; j < CP; j++) sum[j].init();
-                            if (valid) {
-                                const int lo = v_off[r], hi = v_off[r + 1];
-                                for (int e = lo + es; e < hi; e += g) {
-                                    const VV y = v_vals[e];
-#pragma unroll
-                                    for (int j = 0; j < CP; j++) sum[j].add(y.v[j]);
-                                }
-                            }
-#pragma unroll
-                            for (int j = 0; j < CP; j++) {
-                                V sv = sum[j].get();
-                                for (int m = 1; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-                                if (valid && es == 0) v_rsum[r * W + cg * CP + j] = sv;
-                            }
-                        }
-                        __syncwarp();
-                    }
-                    if (need_prev)
-                        for (int i = lane; i < nr * W; i += 32)
-                            row_update_pd<V, W>(perm, cv, acc, T.r0 + i / W, col, v_rsum[i], v_prev[i], v_od[i / W]);
-                    __syncwarp();
-                    continue;
+                for (int k = 0; k < kVecTileEdges / 32; k++) {
+                    const int i = lane + 32 * k;
+                    if (i < ne) v_src[i] = src[T.e0 + i];
                 }
+                for (int i = lane; i <= nr; i += 32) v_off[i] = off[T.r0 + i] - T.e0;
+                for (int i = lane; i < nr; i += 32) v_od[i] = outdeg[T.r0 + i];
+                if (need_prev)
+                    for (int i = lane; i < nr * W; i += 32) v_prev[i] = cv.r_prev[(size_t)T.r0 * W + i];
+                __syncwarp();
+                const int g = 1 << T.glog;
+                const int es = lane & (g - 1);
+                const int rpp = 32 >> T.glog;
+#pragma unroll 1
+                for (int cg = 0; cg < NG; cg++) {
+                    if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
+#pragma unroll
+                    for (int k0 = 0; k0 < kVecTileEdges / 32; k0 += kVecGatherBatch) {
+                        VV x[kVecGatherBatch];
+#pragma unroll
+                        for (int k = 0; k < kVecGatherBatch; k++) {
+                            const int i = lane + 32 * (k0 + k);
+                            if (i < ne) x[k] = load_vec<V, CP>(c_all + (size_t)v_src[i] * W + cg * CP);
+                        }
+#pragma unroll
+                        for (int k = 0; k < kVecGatherBatch; k++) {
+                            const int i = lane + 32 * (k0 + k);
+                            if (i < ne) v_vals[i] = x[k];
+                        }
+                    }
+                    __syncwarp();
+                    for (int rb = 0; rb < nr; rb += rpp) {
+                        const int r = rb + (lane >> T.glog);
+                        const bool valid = r < nr;
+                        EdgeSum<V> sum[CP];
+#pragma unroll
+                        for (int j = 0; j < CP; j++) sum[j].init();
+                        if (valid) {
+                            const int lo = v_off[r], hi = v_off[r + 1];
+                            for (int e = lo + es; e < hi; e += g) {
+                                const VV y = v_vals[e];
+#pragma unroll
+                                for (int j = 0; j < CP; j++) sum[j].add(y.v[j]);
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < CP; j++) {
+                            V sv = sum[j].get();
+                            for (int m = 1; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                            if (valid && es == 0) v_rsum[r * W + cg * CP + j] = sv;
+                        }
+                    }
+                    __syncwarp();
+                }
+                if (need_prev)
+                    for (int i = lane; i < nr * W; i += 32)
+                        row_update_pd<V, W>(perm, cv, acc, T.r0 + i / W, col, v_rsum[i], v_prev[i], v_od[i / W]);
+                __syncwarp();
             }
-            if (kStaged && T.glog >= 0) {
-                // ---------------- rows tile: indices, offsets, previous ranks
-                // and out-degrees are all requested before any gather waits
+        };
+        // ---------------- rows tile, one column: indices, offsets, previous
+        // ranks and out-degrees are all requested before any gather waits
+        auto rows_tile_w1 = [&](const Tile &T) {
+            if constexpr (kStaged) {
                 const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
                 int32_t u[PER];
 #pragma unroll
@@ -537,95 +541,116 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
                         row_update_pd<V, W>(perm, cv, acc, T.r0 + r, col, sv, s_prev[warp][r * W + col], s_od[warp][r]);
                 }
                 __syncwarp();
-            } else {
-                // ---------------- one chunk of a long row, VT values per step
-                const int32_t v = T.r0;
-                const int nv = (T.e1 - T.e0) * W;
-                EdgeSum<V> sum;
-                sum.init();
-                if constexpr (!kStaged) {
-                    // several columns: per column group, lanes stride over the
-                    // chunk's in-edges with vector loads, four in flight
-                    const int ne = T.e1 - T.e0;
+            }
+        };
+        // ---------------- one chunk of a long row
+        auto chunk_tile = [&](const Tile &T) {
+            // ---------------- one chunk of a long row, VT values per step
+            const int32_t v = T.r0;
+            const int nv = (T.e1 - T.e0) * W;
+            EdgeSum<V> sum;
+            sum.init();
+            if constexpr (!kStaged) {
+                // several columns: per column group, lanes stride over the
+                // chunk's in-edges with vector loads, four in flight
+                const int ne = T.e1 - T.e0;
 #pragma unroll 1
-                    for (int cg = 0; cg < NG; cg++) {
-                        if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
-                        EdgeSum<V> vs[CP];
+                for (int cg = 0; cg < NG; cg++) {
+                    if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
+                    EdgeSum<V> vs[CP];
 #pragma unroll
-                        for (int j = 0; j < CP; j++) vs[j].init();
-                        const V *cb = c_all + cg * CP;
-                        int i = lane;
-                        for (; i + 96 < ne; i += 128) {
-                            const int32_t u0 = src[T.e0 + i], u1 = src[T.e0 + i + 32];
-                            const int32_t u2 = src[T.e0 + i + 64], u3 = src[T.e0 + i + 96];
-                            const VV x0 = load_vec<V, CP>(cb + (size_t)u0 * W), x1 = load_vec<V, CP>(cb + (size_t)u1 * W);
-                            const VV x2 = load_vec<V, CP>(cb + (size_t)u2 * W), x3 = load_vec<V, CP>(cb + (size_t)u3 * W);
-#pragma unroll
-                            for (int j = 0; j < CP; j++) {
-                                vs[j].add(x0.v[j]); vs[j].add(x1.v[j]); vs[j].add(x2.v[j]); vs[j].add(x3.v[j]);
-                            }
-                        }
-                        for (; i < ne; i += 32) {
-                            const VV x0 = load_vec<V, CP>(cb + (size_t)src[T.e0 + i] * W);
-#pragma unroll
-                            for (int j = 0; j < CP; j++) vs[j].add(x0.v[j]);
-                        }
+                    for (int j = 0; j < CP; j++) vs[j].init();
+                    const V *cb = c_all + cg * CP;
+                    int i = lane;
+                    for (; i + 96 < ne; i += 128) {
+                        const int32_t u0 = src[T.e0 + i], u1 = src[T.e0 + i + 32];
+                        const int32_t u2 = src[T.e0 + i + 64], u3 = src[T.e0 + i + 96];
+                        const VV x0 = load_vec<V, CP>(cb + (size_t)u0 * W), x1 = load_vec<V, CP>(cb + (size_t)u1 * W);
+                        const VV x2 = load_vec<V, CP>(cb + (size_t)u2 * W), x3 = load_vec<V, CP>(cb + (size_t)u3 * W);
 #pragma unroll
                         for (int j = 0; j < CP; j++) {
-                            V sv = vs[j].get();
-                            for (int m = 1; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-                            if (lane == 0) v_rsum[cg * CP + j] = sv;
+                            vs[j].add(x0.v[j]); vs[j].add(x1.v[j]); vs[j].add(x2.v[j]); vs[j].add(x3.v[j]);
                         }
                     }
-                    __syncwarp();
-                }
-                if (kStaged && cv.active) {
-                    for (int base = lane; base < nv; base += VT) {
-                        int32_t u[PER];
+                    for (; i < ne; i += 32) {
+                        const VV x0 = load_vec<V, CP>(cb + (size_t)src[T.e0 + i] * W);
 #pragma unroll
-                        for (int k = 0; k < PER; k++) {
-                            const int idx = base + 32 * k;
-                            u[k] = idx < nv ? src[T.e0 + idx / W] : -1;
-                        }
-                        V x[PER];
+                        for (int j = 0; j < CP; j++) vs[j].add(x0.v[j]);
+                    }
 #pragma unroll
-                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? cv.c_prev[(size_t)u[k] * W + col] : N::zero();
-#pragma unroll
-                        for (int k = 0; k < PER; k++)
-                            if (u[k] >= 0) sum.add(x[k]);
+                    for (int j = 0; j < CP; j++) {
+                        V sv = vs[j].get();
+                        for (int m = 1; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                        if (lane == 0) v_rsum[cg * CP + j] = sv;
                     }
                 }
-                V sv = sum.get();
-                if constexpr (kStaged) {
-                    for (int m = W; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-                } else {
-                    if (lane < W) sv = v_rsum[lane];
-                    __syncwarp();
+                __syncwarp();
+            }
+            if (kStaged && cv.active) {
+                for (int base = lane; base < nv; base += VT) {
+                    int32_t u[PER];
+#pragma unroll
+                    for (int k = 0; k < PER; k++) {
+                        const int idx = base + 32 * k;
+                        u[k] = idx < nv ? src[T.e0 + idx / W] : -1;
+                    }
+                    V x[PER];
+#pragma unroll
+                    for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? cv.c_prev[(size_t)u[k] * W + col] : N::zero();
+#pragma unroll
+                    for (int k = 0; k < PER; k++)
+                        if (u[k] >= 0) sum.add(x[k]);
                 }
-                if (T.slot < 0) {
-                    if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, sv);
-                } else {
-                    const int32_t base = slot_base[T.slot];
-                    if (lane < W) chunk_part[(size_t)(base + T.k) * W + lane] = sv;
+            }
+            V sv = sum.get();
+            if constexpr (kStaged) {
+                for (int m = W; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+            } else {
+                if (lane < W) sv = v_rsum[lane];
+                __syncwarp();
+            }
+            if (T.slot < 0) {
+                if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, sv);
+            } else {
+                const int32_t base = slot_base[T.slot];
+                if (lane < W) chunk_part[(size_t)(base + T.k) * W + lane] = sv;
+                __threadfence();
+                __syncwarp();
+                int last = 0;
+                if (lane == 0) last = atomicAdd(&chunk_cnt[T.slot], 1u) == (unsigned int)(T.nch - 1);
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (last) {
+                    // the row's chunk sums, lane-parallel in a fixed order:
+                    // lane slot q0 adds chunks q0, q0 + 32/W, ... then a fixed tree
                     __threadfence();
-                    __syncwarp();
-                    int last = 0;
-                    if (lane == 0) last = atomicAdd(&chunk_cnt[T.slot], 1u) == (unsigned int)(T.nch - 1);
-                    last = __shfl_sync(0xffffffffu, last, 0);
-                    if (last) {
-                        // the row's chunk sums, lane-parallel in a fixed order:
-                        // lane slot q0 adds chunks q0, q0 + 32/W, ... then a fixed tree
-                        __threadfence();
-                        constexpr int QS = 32 / W;
-                        V t = N::zero();
-                        for (int32_t q = lane / W; q < T.nch; q += QS)
-                            t = N::add_pos(t, ld_cg_v<V>(chunk_part + (size_t)(base + q) * W + col));
-                        for (int m = W; m < 32; m <<= 1) t = N::add_pos(t, N::shfl_xor(t, m));
-                        if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, t);
-                        if (lane == 0) chunk_cnt[T.slot] = 0;
-                    }
-                    __syncwarp();
+                    constexpr int QS = 32 / W;
+                    V t = N::zero();
+                    for (int32_t q = lane / W; q < T.nch; q += QS)
+                        t = N::add_pos(t, ld_cg_v<V>(chunk_part + (size_t)(base + q) * W + col));
+                    for (int m = W; m < 32; m <<= 1) t = N::add_pos(t, N::shfl_xor(t, m));
+                    if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, t);
+                    if (lane == 0) chunk_cnt[T.slot] = 0;
                 }
+                __syncwarp();
+            }
+        };
+
+        // the next tile's descriptor is requested while this tile is worked on
+        Tile T_next{};
+        if (kPrefetchTile && local * kWarps + warp < ntiles) T_next = load_tile(tiles + local * kWarps + warp);
+        for (int t = local * kWarps + warp; t < ntiles; t += wstride) {
+            Tile T;
+            if constexpr (kPrefetchTile) {
+                T = T_next;
+                if (t + wstride < ntiles) T_next = load_tile(tiles + t + wstride);
+            } else {
+                T = tiles[t];
+            }
+            if (T.glog >= 0) {
+                if constexpr (kStaged) rows_tile_w1(T);
+                else rows_tile_vec(T);
+            } else {
+                chunk_tile(T);
             }
         }
     }

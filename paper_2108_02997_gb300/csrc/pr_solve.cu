@@ -113,11 +113,11 @@ void *pr_init_kernel_for(int prec, int W) {
         default: return init_ptr<df64>(W);
     }
 }
-// One column: static shared memory only. Several columns: the per-warp tile
-// buffers (vec_warp_bytes) in dynamic shared memory.
+// Dynamic shared memory of the iteration kernel: none for one column (static
+// buffers only); for several columns, the per-warp tile buffers (vec_warp_bytes).
 size_t pr_tile_smem_bytes(int prec, int W) {
-    if (W == 1) return 0;
     const int vbytes = prec == PR_PREC_FP32 ? 4 : 8;
+    if (W == 1) return 0;
     return (size_t)kWarps * vec_warp_bytes(vbytes, W);
 }
 
@@ -133,6 +133,8 @@ pr_status pr_kernel_setup(int prec, int W, int *blocks_per_sm) {
         int pi = prec & 3, wi = w_index(W);
         if (!done[pi][wi]) {
             PR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (smem > 0 && kSmemCarveout >= 0)
+                PR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, kSmemCarveout));
             done[pi][wi] = true;
         }
     }
@@ -145,6 +147,18 @@ pr_status pr_kernel_setup(int prec, int W, int *blocks_per_sm) {
 void pr_record_last_stats(const SolveStats &st) {
     std::lock_guard<std::mutex> lk(g_stats_mu);
     g_last_stats = st;
+}
+
+extern "C" pr_status pr_kernel_occupancy(int32_t precision, int32_t width, int32_t *ctas_per_sm) {
+    pr_clear_error();
+    if (precision < PR_PREC_DF64 || precision > PR_PREC_FP32 || precision == PR_PREC_MIXED)
+        return pr_fail(PR_EINVAL, "precision must be PR_PREC_DF64, PR_PREC_FP64 or PR_PREC_FP32");
+    if (w_index(width) < 0) return pr_fail(PR_EINVAL, "width must be 1, 2, 4, 8, 16 or 32");
+    int occ = 0;
+    pr_status s = pr_kernel_setup(precision, width, &occ);
+    if (s != PR_OK) return s;
+    if (ctas_per_sm) *ctas_per_sm = occ;
+    return PR_OK;
 }
 
 extern "C" pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms) {
