@@ -66,28 +66,32 @@ def peaks():
 
 # --------------------------------------------------------------------------- workloads
 
-def make_workload(name, gg):
-    """(graphs, instance specs [(graph index, alpha, tau, norm, max_iter)], precision, description)."""
+def make_workload(name, gg, rank=0):
+    """(graphs, instance specs [(graph index, alpha, tau, norm, max_iter)], precision, description).
+    Rank r > 0 of a multi-GPU run gets graphs of the same shape from its own
+    seeds (weak scaling: every rank solves a full batch of its own)."""
+    from paper_2108_02997_gb300.dist import rank_seed
+    s = lambda seed: rank_seed(seed, rank)
     if name in ("rmat22", "rmat21"):
         scale = int(name[4:])
-        g = gg.rmat(scale, 16, seed=scale)
+        g = gg.rmat(scale, 16, seed=s(scale))
         specs = [(0, 0.85, t, nm, 500) for t in (1e-6, 1e-10) for nm in (1, 2, 3)]
         return [g], specs, "df64", f"rmat-s{scale} ef16 seed{scale}, alpha .85, tau {{1e-6,1e-10}} x {{L1,L2,Linf}}"
     if name == "sweep330":
-        g = gg.erdos_renyi_10k(seed=1)
+        g = gg.erdos_renyi_10k(seed=s(1))
         alphas = [round(0.5 + 0.05 * i, 2) for i in range(11)]
         specs = [(0, a, 10.0 ** -k, nm, 500) for a in alphas for k in range(1, 11) for nm in (1, 2, 3)]
         return [g], specs, "df64", "er-10k (100k edges, 5% dangling), 11 alpha x 10 tau x 3 norms"
     if name == "multi64":
-        gs = [gg.rmat(12 + (i % 9), 16, seed=1000 + i) for i in range(64)]
+        gs = [gg.rmat(12 + (i % 9), 16, seed=s(1000 + i)) for i in range(64)]
         specs = [(i, 0.85, 1e-10, 1, 500) for i in range(64)]
         return gs, specs, "df64", "64 rmat graphs scale 12..20 ef16, alpha .85, tau 1e-10, L1"
     if name == "rmat24mixed":
-        g = gg.rmat(24, 16, seed=24)
+        g = gg.rmat(24, 16, seed=s(24))
         specs = [(0, a, 1e-10, 3, 500) for a in (0.85, 0.95)]
         return [g], specs, "mixed", "rmat-s24 ef16 seed24, alpha {.85,.95}, Linf, tau 1e-10, fp32->df64"
     if name == "learned":
-        gs = [gg.rmat(22, 16, seed=3022), gg.rmat(24, 16, seed=3024), gg.config_model(8_000_000, seed=3008)]
+        gs = [gg.rmat(22, 16, seed=s(3022)), gg.rmat(24, 16, seed=s(3024)), gg.config_model(8_000_000, seed=s(3008))]
         alphas = (0.5, 0.6, 0.7, 0.8, 0.85, 0.9, 0.95)
         specs = [(i, a, 1e-10, 1, 500) for i in range(len(gs)) for a in alphas]
         return gs, specs, "mixed", ("unseen rmat-s22 (seed 3022), rmat-s24 (seed 3024), config model N=8M "
@@ -177,31 +181,18 @@ class ClockSampler:
 # --------------------------------------------------------------------------- distributed
 
 def dist_init(n_gpus):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    return world, rank, local
+    from paper_2108_02997_gb300 import dist
+    return dist.init("cuda")
 
 
 def barrier(world):
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        dist.barrier()
-        torch.cuda.synchronize()
+    from paper_2108_02997_gb300 import dist
+    dist.barrier(world, "cuda")
 
 
 def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2108_02997_gb300 import dist
+    return dist.max_over_ranks(x, world, "cuda")
 
 
 # --------------------------------------------------------------------------- our arm
@@ -215,7 +206,7 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     B.lib()
-    graphs, specs, precision, desc = make_workload(args.workload, gg)
+    graphs, specs, precision, desc = make_workload(args.workload, gg, rank)
     dgs = [B.Graph.from_csr(g) for g in graphs]
     outs = [torch.empty(graphs[gi].n, dtype=torch.float64, device="cuda") for gi, *_ in specs]
     stream = torch.cuda.current_stream()
@@ -357,7 +348,7 @@ def run_ours(args, world, rank, local):
         "dtype": {"df64": "df64 (f32x2)", "mixed": "f32 -> df64", "fp64": "f64", "fp32": "f32"}[precision],
         "data": "synthetic (seeded generators; paper's SuiteSparse graphs unavailable)",
         "config": {"workload": desc, "instances": solves, "graphs": len(graphs),
-                   "edges": total_edges, "parallelism": f"replicas x{world}",
+                   "edges": total_edges, "parallelism": f"instance batches x{world} (one per rank, no collective)",
                    "l2": "inputs larger than L2" if inputs_large else "L2 flushed (256 MB write) between steps"},
         "iterations": inst_iters,
         "gteps_instances": edges_inst / (ms_step * 1e-3) / 1e9,
@@ -479,9 +470,8 @@ def main():
         return
     world, rank, local = dist_init(args.gpus)
     run_ours(args, world, rank, local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    from paper_2108_02997_gb300 import dist
+    dist.finish(world)
 
 
 if __name__ == "__main__":
