@@ -100,7 +100,7 @@ def make_workload(name, gg, rank=0):
 
 
 def train_warm_start(B, gg, torch, sptr, epochs=30, lr=3e-3):
-    """The learned warm start of BASELINE's config 5: 32 seeded R-MAT graphs of
+    """Training of the learned warm start: 32 seeded R-MAT graphs of
     scale 16 + (i mod 5), alpha 0.50..0.95; targets are this library's own
     solves at tau 1e-12. Returns (mlp, report)."""
     alphas = [round(0.5 + 0.05 * i, 2) for i in range(10)]
