@@ -90,6 +90,11 @@ def make_workload(name, gg, rank=0):
         g = gg.rmat(24, 16, seed=s(24))
         specs = [(0, a, 1e-10, 3, 500) for a in (0.85, 0.95)]
         return [g], specs, "mixed", "rmat-s24 ef16 seed24, alpha {.85,.95}, Linf, tau 1e-10, fp32->df64"
+    if name == "road24":
+        g = gg.road_grid(4096, 4096, seed=s(7))
+        specs = [(0, 0.85, t, nm, 500) for t in (1e-6, 1e-10) for nm in (1, 2, 3)]
+        return [g], specs, "df64", ("road-like lattice 4096 x 4096 (links kept .8, one-way .2), alpha .85, "
+                                    "tau {1e-6,1e-10} x {L1,L2,Linf}")
     if name == "learned":
         gs = [gg.rmat(22, 16, seed=s(3022)), gg.rmat(24, 16, seed=s(3024)), gg.config_model(8_000_000, seed=s(3008))]
         alphas = (0.5, 0.6, 0.7, 0.8, 0.85, 0.9, 0.95)
@@ -179,6 +184,30 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- distributed
+
+def sweep_report(B, torch, dgs, specs, last, outs, sptr):
+    """Outputs of the alpha x tau x norm sweep beyond its timing (untimed):
+    per alpha, the L1 distance of its ranks (tau 1e-10, L1) to the alpha = 0.85
+    ranks and its iteration count relative to alpha = 0.85 (the comparisons of
+    Section 2); and the same 330 instances solved in FP32 throughout, giving per
+    norm the largest tau at which an alpha < 1 instance ran into the 500 cap
+    (the stalls Section 4 describes)."""
+    ref_k = [k for k, (gi, a, t, nm, mi) in enumerate(specs) if a == 0.85 and t == 1e-10 and nm == 1][0]
+    alphas, l1, ratio = [], [], []
+    for k, (gi, a, t, nm, mi) in enumerate(specs):
+        if t == 1e-10 and nm == 1:
+            alphas.append(a)
+            l1.append(float((outs[k] - outs[ref_k]).abs().sum()))
+            ratio.append(last[k].iters / last[ref_k].iters)
+    xs = [B.Instance(dgs[gi], a, t, nm, mi) for gi, a, t, nm, mi in specs]
+    B.pr_solve_batch(xs, precision="fp32", stream=sptr)
+    stall = {}
+    for nm, name in ((1, "L1"), (2, "L2"), (3, "Linf")):
+        hit = [t for (gi, a, t, n2, mi), x in zip(specs, xs) if n2 == nm and a < 1.0 and not x.converged]
+        stall[name] = max(hit) if hit else None
+    return {"alpha": alphas, "l1_vs_alpha_085": l1, "iterations_vs_alpha_085": ratio,
+            "fp32_largest_tau_hitting_cap": stall}
+
 
 def dist_init(n_gpus):
     from paper_2108_02997_gb300 import dist
@@ -285,6 +314,7 @@ def run_ours(args, world, rank, local):
         learned["iterations_uniform"] = [x.iters for x in xs_u]
         learned["iterations_learned"] = inst_iters
         learned["iterations_saved_total"] = sum(x.iters for x in xs_u) - sum(inst_iters)
+    sweep = sweep_report(B, torch, dgs, specs, last, outs, sptr) if args.workload == "sweep330" else None
     # ---- plain per-instance GPU solver on the same resident graphs: every
     # instance alone through pr_solve, one launch per iteration and a host read
     # of the stop flag after each (the baseline the batched path is measured against)
@@ -361,6 +391,7 @@ def run_ours(args, world, rank, local):
         "e2e": e2e,
         "plain_gpu": plain,
         "learned_start": learned,
+        "sweep_report": sweep,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": launches,
@@ -455,7 +486,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22",
-                    choices=["rmat22", "rmat21", "sweep330", "multi64", "rmat24mixed", "learned"])
+                    choices=["rmat22", "rmat21", "sweep330", "multi64", "rmat24mixed", "learned", "road24"])
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="device loop of the timed solves (host: one launch per iteration)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -136,7 +136,12 @@ typedef struct pr_options {
                                    3*max_iter doubles: row i-1 = (L1, L2, Linf)
                                    of r^i - r^{i-1} */
     int32_t group;              /* pr_group; default PR_GROUP_AUTO */
-    int32_t reserved[7];        /* zero */
+    int32_t max_passes;         /* watchdog: iteration passes the device may run
+                                   in one phase before the solve is abandoned
+                                   with PR_ETIMEOUT (the device stops itself;
+                                   the context stays usable); 0 (default) =
+                                   the largest max_iter + 3 */
+    int32_t reserved[6];        /* zero */
 } pr_options;
 
 /* Fill *opt with the defaults listed above. */

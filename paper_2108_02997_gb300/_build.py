@@ -28,7 +28,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
 
 CU_SOURCES = ["pr_api.cu", "pr_graph.cu", "pr_solve.cu", "pr_learn.cu", "pr_noalloc.cu", "pr_plan.cu"]
-CU_HEADERS = ["pr_internal.cuh", "pr_kernels.cuh", "df64.cuh"]
+CU_HEADERS = ["pr_internal.cuh", "pr_host.h", "pr_kernels.cuh", "df64.cuh"]
 
 
 def _nvcc() -> str:

@@ -38,7 +38,8 @@ class pr_options(C.Structure):
                 ("init_on_device", C.c_int32), ("outputs_on_device", C.c_int32),
                 ("switch_tol", C.c_double), ("stream", C.c_void_p),
                 ("share_trajectories", C.c_int32), ("loop", C.c_int32), ("mlp", C.c_void_p),
-                ("err_history", C.c_void_p), ("group", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("err_history", C.c_void_p), ("group", C.c_int32), ("max_passes", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class pr_instance(C.Structure):
@@ -186,9 +187,10 @@ class SolveResult:
 
 
 def _make_options(precision="df64", init=None, loop="graph", stream=None, share=True, switch_tol=1e-6,
-                  outputs_on_device=False, mlp=None, group="auto"):
+                  outputs_on_device=False, mlp=None, group="auto", max_passes=0):
     o = default_options()
     o.group = GROUPS[group] if isinstance(group, str) else int(group)
+    o.max_passes = int(max_passes)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.loop = PR_LOOP_HOST if loop == "host" else PR_LOOP_GRAPH
     o.share_trajectories = 1 if share else 0
@@ -248,7 +250,7 @@ class Instance:
 
 
 def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=None, share=True,
-                   switch_tol=1e-6, outputs_on_device=False, mlp=None, check=True, group="auto"):
+                   switch_tol=1e-6, outputs_on_device=False, mlp=None, check=True, group="auto", max_passes=0):
     """Solve many instances together. Fills ``out`` (allocated as numpy, or as
     torch CUDA tensors when ``outputs_on_device``), ``iters``, ``err``,
     ``converged`` and ``status`` of every :class:`Instance`; returns the
@@ -279,7 +281,8 @@ def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=N
             keep.append(x.init)
     if stream is None and any_dev:
         stream = current_stream_ptr()
-    o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, outputs_on_device, mlp, group)
+    o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, outputs_on_device, mlp, group,
+                             max_passes)
     if any(x.init is not None for x in insts) and o.init == PR_INIT_UNIFORM:
         o.init = PR_INIT_USER
     st = lib().pr_solve_batch(arr, len(insts), C.byref(o))

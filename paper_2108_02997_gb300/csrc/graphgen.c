@@ -235,6 +235,58 @@ int gg_rmat(int32_t scale, int32_t edge_factor, double a, double b, double c,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Road-like grid: rows x cols vertices on a lattice, vertex (i, j) = i*cols + j.
+ * Each lattice link to the right and downward neighbour exists with
+ * probability p_keep (first draw of stream 4 for the link); an existing link
+ * is one-way with probability p_oneway (second draw's high half), in the
+ * direction given by the second draw's lowest bit, else two-way. Ids are then
+ * relabelled by a random permutation (stream 5) when `permute` is set. Mean
+ * out-degree 2 p_keep (2 - p_oneway), at most 4; vertices with no outgoing
+ * link are dangling. */
+int gg_road_grid(int32_t rows, int32_t cols, double p_keep, double p_oneway, uint64_t seed, int32_t permute,
+                 gg_graph **out) {
+    if (rows < 1 || cols < 1 || !out) return 1;
+    if ((int64_t)rows * cols > 2147483647LL) return 1;
+    if (!(p_keep >= 0.0 && p_keep <= 1.0 && p_oneway >= 0.0 && p_oneway <= 1.0)) return 1;
+    const int32_t n = rows * cols;
+    const double two32 = 4294967296.0;
+    const uint64_t t_keep = (uint64_t)(p_keep * two32), t_one = (uint64_t)(p_oneway * two32);
+    uint64_t key = gg_key(seed, 4);
+    int32_t *perm = NULL;
+    if (permute) {
+        perm = random_permutation(n, seed, 5);
+        if (!perm) return 2;
+    }
+    uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n * 4 + 8);
+    if (!keys) { free(perm); return 2; }
+    int64_t m = 0;
+    for (int32_t i = 0; i < rows; i++) {
+        for (int32_t j = 0; j < cols; j++) {
+            const int32_t v = i * cols + j;
+            for (int dir = 0; dir < 2; dir++) {
+                int32_t w;
+                if (dir == 0) { if (j + 1 >= cols) continue; w = v + 1; }
+                else { if (i + 1 >= rows) continue; w = v + cols; }
+                const uint64_t x = gg_at(key, 4 * (uint64_t)v + 2 * (uint64_t)dir);
+                if ((x >> 32) >= t_keep) continue;
+                const uint64_t y = gg_at(key, 4 * (uint64_t)v + 2 * (uint64_t)dir + 1);
+                uint32_t a = (uint32_t)v, b = (uint32_t)w;
+                if (perm) { a = (uint32_t)perm[a]; b = (uint32_t)perm[b]; }
+                if ((y >> 32) < t_one) {
+                    if (y & 1u) keys[m++] = ((uint64_t)a << 32) | b;   /* b -> a */
+                    else keys[m++] = ((uint64_t)b << 32) | a;          /* a -> b */
+                } else {
+                    keys[m++] = ((uint64_t)b << 32) | a;
+                    keys[m++] = ((uint64_t)a << 32) | b;
+                }
+            }
+        }
+    }
+    free(perm);
+    return csr_from_keys(n, keys, m, out);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Directed Erdos-Renyi: draw (src, dst) uniformly (stream 1, two draws per
  * candidate) and keep the first m_unique distinct non-self-loop edges in draw
  * order; then pick n_dangling distinct vertices (partial Fisher-Yates,

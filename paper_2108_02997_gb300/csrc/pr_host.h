@@ -1,0 +1,111 @@
+// pr_host.h — host-side objects of the library: the graph handle, solve
+// requests and their accounting, the grouping planner's interface, kernel
+// selection and the live-handle registry. Included by pr_internal.cuh after
+// the device-visible structures it builds on.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pagerank.h"
+
+// ------------------------------------------------------------------ graph object
+struct pr_graph {
+    uint32_t magic;
+    int32_t n;
+    int64_t nnz;
+    int32_t n_dangling;
+    int32_t device;
+    int32_t *d_off = nullptr;        // n+1 (padded for 16-byte bulk copies)
+    int32_t *d_src = nullptr;        // nnz (padded)
+    int32_t *d_outdeg = nullptr;     // n (padded)
+    int32_t *d_perm = nullptr;       // relabelled -> caller
+    int32_t *d_inv = nullptr;        // caller -> relabelled
+    std::vector<ClassRange> classes; // in-degree classes in relabelled order
+    std::vector<int32_t> h_off;      // relabelled offsets (host copy, for tile tables)
+    TileTable tables[6];             // W = 1, 2, 4, 8, 16, 32
+    uint64_t signature = 0;          // hash of n, nnz and the in-degree class layout
+};
+constexpr uint32_t kGraphMagic = 0x50524731u;   // "PRG1"
+constexpr uint32_t kMlpMagic = 0x50524d31u;     // "PRM1"
+
+// Elements of padding after each graph array and value buffer, so that
+// 16-byte-rounded bulk copies of any tile stay inside the allocation.
+constexpr int kPad = 8;
+
+// ------------------------------------------------------------------ errors
+void pr_set_error(const std::string &msg);
+void pr_clear_error();
+pr_status pr_fail(pr_status s, const std::string &msg);
+pr_status pr_cuda_fail(cudaError_t e, const char *what);
+
+#define PR_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return pr_cuda_fail(_e, #call);          \
+    } while (0)
+
+// ------------------------------------------------------------------ internals
+int w_index(int W);   // 1,2,4,..,32 -> 0..5
+pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out);
+bool pr_graph_valid(const pr_graph *g);
+
+// Solve driver (pr_solve.cu)
+struct SolveColumn {
+    const pr_graph *g;
+    double alpha;
+    std::vector<Tap> taps;          // filled with out pointers (device, caller order)
+    std::vector<int32_t> inst;      // instance index of each tap
+    std::vector<double *> host_dst; // per tap: host buffer to receive the answer, or null
+    const double *init_dev = nullptr;   // device start vector in caller order, or null
+    double *hist_host = nullptr;
+    int32_t hist_cap = 0;
+};
+
+// Launch accounting of one solve (or the sum over a request's sub-solves).
+struct SolveStats {
+    int launches = 0;       // kernel launches, init passes included
+    int passes = 0;         // iteration passes the device performed
+    double kernel_ms = 0.0; // PR_LOOP_HOST: sum of the iteration launches' event times
+    double total_ms = 0.0;  // device time of the whole solve
+    void add(const SolveStats &o) {
+        launches += o.launches; passes += o.passes; kernel_ms += o.kernel_ms; total_ms += o.total_ms;
+    }
+};
+
+struct SolveRequest {
+    int precision = PR_PREC_DF64;
+    int loop = PR_LOOP_GRAPH;
+    double switch_tol = 1e-6;
+    cudaStream_t stream = nullptr;
+    std::vector<SolveColumn> cols;
+    // Optional explicit jobs: lists of column indices, all on one graph, at most
+    // 32 each; empty = the columns of each graph packed 32 at a time.
+    std::vector<std::vector<int>> jobs;
+    int max_passes = 0;     // 0: the largest max_iter + 3
+    SolveStats stats;       // out
+};
+
+pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out);
+void pr_record_last_stats(const SolveStats &s);
+
+// Column grouping (pr_plan.cu). A sub-solve is one pr_run_solve: jobs of one
+// width W, given as lists of request column indices.
+struct SubSolve {
+    int W = 1;
+    std::vector<std::vector<int>> jobs;
+};
+pr_status pr_plan_request(const SolveRequest &req, int group, std::vector<SubSolve> &plan);
+
+// Kernel selection and launch geometry (pr_solve.cu)
+void *pr_iter_kernel_for(int precision, int W);
+void *pr_init_kernel_for(int precision, int W);
+size_t pr_tile_smem_bytes(int precision, int W);
+pr_status pr_kernel_setup(int precision, int W, int *blocks_per_sm);
+
+// Live-handle registry: guards every entry point against stale handles.
+void registry_add(const void *p);
+void registry_remove(const void *p);
+bool registry_has(const void *p);

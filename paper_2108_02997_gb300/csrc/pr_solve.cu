@@ -461,7 +461,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     }
     PR_CUDA(cudaMemcpyAsync(ar.at<JobDev>(off_jobs), hjobs.data(), hjobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice, st));
     PR_CUDA(cudaMemcpyAsync(ar.at<int32_t>(off_ctajob), ctajob.data(), ctajob.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    const int pass_cap = max_iter_all + 3;
+    const int pass_cap = req.max_passes > 0 ? req.max_passes : max_iter_all + 3;
     // ---- phase 1 (or the only phase)
     s = run_phase(prec1, W, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, pass_cap, req.loop, st, stats);
     if (s != PR_OK) return s;

@@ -11,6 +11,8 @@ Workload recipes (stand-ins for the paper's SuiteSparse graphs, Section 2):
   500 vertices made dangling by deleting their out-edges (seed 1).
 * ``rmat(scale)`` — R-MAT a/b/c/d = .57/.19/.19/.05, edge factor 16, ids
   randomly permuted, self-loops and duplicates removed.
+* ``road_grid(rows, cols)`` — road-like lattice digraph (mean out-degree about
+  2.9, at most 4), ids randomly permuted.
 * ``config_model(n)`` — directed configuration model, power-law in/out degree
   with exponent 2.1 and mean close to 12.
 """
@@ -43,6 +45,9 @@ def _load():
                                 C.c_uint64, C.c_int32, C.POINTER(vp)]
         lib.gg_rmat.restype = C.c_int
         lib.gg_erdos_renyi.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_uint64, C.POINTER(vp)]
+        lib.gg_road_grid.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_uint64, C.c_int32,
+                                     C.POINTER(vp)]
+        lib.gg_road_grid.restype = C.c_int
         lib.gg_erdos_renyi.restype = C.c_int
         lib.gg_config_model.argtypes = [C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_uint64,
                                         C.POINTER(vp)]
@@ -126,6 +131,18 @@ def erdos_renyi(n: int, m_unique: int, n_dangling: int, seed: int) -> Graph:
     h = C.c_void_p()
     _check(lib.gg_erdos_renyi(n, m_unique, n_dangling, seed, C.byref(h)), "erdos_renyi")
     return _take(h, f"er-n{n}-m{m_unique}-d{n_dangling}-seed{seed}")
+
+
+def road_grid(rows: int, cols: int, p_keep: float = 0.8, p_oneway: float = 0.2, seed: int = 7,
+              permute: bool = True) -> Graph:
+    """Road-like lattice digraph: each right/down lattice link kept with
+    probability p_keep, one-way with probability p_oneway (random direction),
+    else two-way; mean out-degree 2 p_keep (2 - p_oneway) (2.88 by default)."""
+    lib = _load()
+    h = C.c_void_p()
+    _check(lib.gg_road_grid(int(rows), int(cols), float(p_keep), float(p_oneway), int(seed), 1 if permute else 0,
+                            C.byref(h)), "road_grid")
+    return _take(h, f"road-{rows}x{cols}-seed{seed}")
 
 
 def erdos_renyi_10k(seed: int = 1) -> Graph:

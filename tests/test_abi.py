@@ -89,6 +89,12 @@ def test_solve_rejects_bad_handles_and_arguments(L):
     o = binding.default_options()
     o.precision = 17
     assert L.pr_solve_batch(None, 0, C.byref(o)) == 1
+    o = binding.default_options()
+    o.max_passes = -1
+    assert L.pr_solve_batch(None, 0, C.byref(o)) == 1 and b"max_passes" in L.pr_last_error()
+    o = binding.default_options()
+    o.group = 7
+    assert L.pr_solve_batch(None, 0, C.byref(o)) == 1 and b"group" in L.pr_last_error()
     assert L.pr_solve_batch(None, -1, None) == 1
 
 
@@ -97,3 +103,4 @@ def test_options_defaults(L):
     o = binding.default_options()
     assert o.precision == binding.PR_PREC_DF64 and o.switch_tol == 1e-6 and o.share_trajectories == 1
     assert o.loop == binding.PR_LOOP_GRAPH and o.init == binding.PR_INIT_UNIFORM
+    assert o.group == binding.PR_GROUP_AUTO and o.max_passes == 0

@@ -145,3 +145,27 @@ def test_device_side_graph_validation(B):
     g = B.Graph([0, 1, 2], [1, 0], [1, 1])   # the valid 2-cycle still works afterwards
     assert g.info() == (2, 2, 0)
     g.close()
+
+
+@pytest.mark.parametrize("loop", ["graph", "host"])
+def test_watchdog_ends_the_device_loop(B, orc, er10k, er10k_dev, loop):
+    """A device loop that outlives its pass budget stops itself and reports
+    PR_ETIMEOUT; the context stays usable (no GPU fault is involved)."""
+    x = B.Instance(er10k_dev, 0.99, 1e-14, 1, 500)
+    st = B.pr_solve_batch([x], loop=loop, max_passes=5, check=False)
+    assert st == B.PR_ETIMEOUT and x.status == B.PR_ETIMEOUT
+    assert b"pass cap" in B.lib().pr_last_error()
+    ref = orc.pagerank(er10k, 0.85, 1e-10, 1, 500, history=True)
+    res = B.pr_solve(er10k_dev, 0.85, 1e-10, 1, 500, loop=loop)
+    assert_fp64_parity(res.ranks, res.iters, res.err, ref, 1e-10, 1, f"after watchdog ({loop})")
+
+
+def test_road_grid_matches_oracle(B, orc, gg):
+    """A road-like lattice (in-degrees 0..4, many dangling-free short rows):
+    every row is in a small-degree class."""
+    g = gg.road_grid(300, 400, seed=11)
+    with B.Graph.from_csr(g) as dg:
+        for norm, tau in ((1, 1e-10), (2, 1e-9), (3, 1e-7)):
+            ref = orc.pagerank(g, 0.85, tau, norm, 500, history=True, threads=orc.default_threads())
+            res = B.pr_solve(dg, 0.85, tau, norm, 500)
+            assert_fp64_parity(res.ranks, res.iters, res.err, ref, tau, norm, f"road norm {norm}")

@@ -66,3 +66,21 @@ def test_config_model_small(gg):
     _check_csr(g)
     mean = g.nnz / g.n
     assert 6 < mean < 14
+
+
+def test_road_grid_shape(gg):
+    g = gg.road_grid(200, 300, seed=5)
+    assert g.n == 60000
+    src, dst = g.edges()
+    assert np.all(src != dst)
+    assert np.unique(dst.astype(np.int64) * g.n + src).size == g.nnz        # no duplicates
+    assert g.outdeg.max() <= 4 and g.indeg.max() <= 4
+    # links kept with p = 0.8, two-way with p = 0.8: about 2 * 0.8 * 1.8 = 2.88 per vertex
+    assert abs(g.nnz / g.n - 2.88) < 0.05
+    # unpermuted: every edge joins lattice neighbours
+    h = gg.road_grid(40, 50, seed=5, permute=False)
+    s, d = h.edges()
+    di, dj = np.abs(s // 50 - d // 50), np.abs(s % 50 - d % 50)
+    assert np.all(di + dj == 1)
+    # deterministic in the seed
+    assert np.array_equal(gg.road_grid(40, 50, seed=5, permute=False).sources, h.sources)
