@@ -19,13 +19,6 @@
 
 namespace {
 
-int deg_class(int32_t d) {   // 0 for d = 0, else 1 + floor(log2 d)
-    if (d <= 0) return 0;
-    int c = 0;
-    while (d) { c++; d >>= 1; }
-    return c;
-}
-
 template <typename T>
 pr_status dalloc(T **p, size_t count) {
     *p = nullptr;
@@ -193,6 +186,176 @@ __global__ void remap_rows_kernel(const int32_t *__restrict__ old_off, const int
     }
 }
 
+// ---------------------------------------------------------------- device relabelling
+// Sort key of a vertex: in-degree class descending, then out-degree class
+// descending (classes 0..32: 0 for degree 0, else 1 + floor(log2 d)). The
+// relabelled order is the stable sort by key (ties by caller id).
+constexpr int kClasses = 33;
+constexpr int kKeys = kClasses * kClasses;
+constexpr int kSortChunk = 2048;     // vertices per CTA of the counting sort
+constexpr int kSortThreads = 256;
+
+__device__ __forceinline__ int dev_class(int32_t d) { return d > 0 ? 32 - __clz(d) : 0; }
+
+// Keys, and the largest in-degree of every in-degree class.
+__global__ void class_keys_kernel(const int32_t *__restrict__ off, const int32_t *__restrict__ outdeg, int32_t n,
+                                  int32_t *__restrict__ key, int32_t *__restrict__ class_max) {
+    __shared__ int32_t s_max[kClasses];
+    for (int i = threadIdx.x; i < kClasses; i += blockDim.x) s_max[i] = 0;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t din = off[v + 1] - off[v];
+        const int cin = dev_class(din), cout = dev_class(outdeg[v]);
+        key[v] = (32 - cin) * kClasses + (32 - cout);
+        atomicMax(&s_max[cin], din);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kClasses; i += blockDim.x)
+        if (s_max[i] > 0) atomicMax(&class_max[i], s_max[i]);
+}
+
+// Per chunk of kSortChunk vertices, the count of every key: M[key * nchunks + chunk].
+__global__ void __launch_bounds__(kSortThreads) chunk_hist_kernel(const int32_t *__restrict__ key, int32_t n,
+                                                                  int32_t nchunks, int32_t *__restrict__ M) {
+    __shared__ int32_t h[kKeys];
+    const int chunk = blockIdx.x;
+    for (int i = threadIdx.x; i < kKeys; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t v0 = (int64_t)chunk * kSortChunk;
+    for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
+        const int64_t v = v0 + i;
+        if (v < n) atomicAdd(&h[key[v]], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kKeys; i += blockDim.x) M[(int64_t)i * nchunks + chunk] = h[i];
+}
+
+// Stable scatter: a vertex goes to (first slot of its key in its chunk) + (the
+// vertices of the same key before it in the chunk). The chunk is walked in
+// rounds of 256 consecutive vertices; within a round, lanes of equal key find
+// their order by warp match, warps in order through per-warp key counts.
+__global__ void __launch_bounds__(kSortThreads) chunk_scatter_kernel(const int32_t *__restrict__ key, int32_t n,
+                                                                     int32_t nchunks, const int32_t *__restrict__ Mscan,
+                                                                     int32_t *__restrict__ perm, int32_t *__restrict__ inv) {
+    constexpr int kW = kSortThreads / 32;
+    __shared__ int32_t running[kKeys];
+    __shared__ int32_t wcnt[kW][kKeys];
+    const int chunk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kKeys; i += blockDim.x) {
+        running[i] = 0;
+        for (int w = 0; w < kW; w++) wcnt[w][i] = 0;
+    }
+    __syncthreads();
+    const int64_t v0 = (int64_t)chunk * kSortChunk;
+    for (int r = 0; r < kSortChunk; r += kSortThreads) {
+        const int64_t v = v0 + r + tid;
+        const bool valid = v < n;
+        const int k = valid ? key[v] : kKeys;   // kKeys: no vertex
+        const unsigned int mask = __match_any_sync(0xffffffffu, k);
+        const int rank_in_warp = __popc(mask & ((1u << lane) - 1u));
+        const bool leader = rank_in_warp == 0;
+        if (valid && leader) wcnt[warp][k] = __popc(mask);
+        __syncthreads();
+        if (valid) {
+            int before = running[k] + rank_in_warp;
+            for (int w = 0; w < warp; w++) before += wcnt[w][k];
+            const int32_t dest = Mscan[(int64_t)k * nchunks + chunk] + before;
+            perm[dest] = (int32_t)v;
+            inv[v] = dest;
+        }
+        __syncthreads();
+        if (valid && leader) {
+            atomicAdd(&running[k], __popc(mask));
+            wcnt[warp][k] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// Relabelled in-degrees and out-degrees: row i is caller row perm[i].
+__global__ void relabel_degrees_kernel(const int32_t *__restrict__ perm, const int32_t *__restrict__ old_off,
+                                       const int32_t *__restrict__ old_od, int32_t n, int32_t *__restrict__ new_deg,
+                                       int32_t *__restrict__ new_od) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = perm[i];
+        new_deg[i] = old_off[v + 1] - old_off[v];
+        new_od[i] = old_od[v];
+    }
+}
+
+// First relabelled row of every in-degree class (in-key ik = 32 - class),
+// read from the scanned key counts: bucket (ik, out-key 0) of chunk 0.
+__global__ void class_starts_kernel(const int32_t *__restrict__ Mscan, int32_t nchunks, int32_t *__restrict__ starts) {
+    const int ik = threadIdx.x;
+    if (ik < kClasses) starts[ik] = Mscan[(int64_t)ik * kClasses * nchunks];
+}
+
+// ---------------------------------------------------------------- exclusive scan (int32)
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Exclusive scan of one tile per CTA; the tile's total goes to sums[block].
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const int32_t *__restrict__ in, int64_t len,
+                                                                  int32_t *__restrict__ out, int32_t *__restrict__ sums) {
+    __shared__ int32_t warp_tot[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)tid * kScanItems;
+    int32_t x[kScanItems];
+    int32_t t = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        x[i] = base + i < len ? in[base + i] : 0;
+        t += x[i];
+    }
+    int32_t incl = t;
+    for (int m = 1; m < 32; m <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, m);
+        if (lane >= m) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int32_t woff = 0;
+    for (int w = 0; w < warp; w++) woff += warp_tot[w];
+    int32_t run = woff + incl - t;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        if (base + i < len) out[base + i] = run;
+        run += x[i];
+    }
+    if (tid == kScanThreads - 1) sums[blockIdx.x] = woff + incl;
+}
+// Exclusive scan of the tile totals, one CTA, in order.
+__global__ void scan_sums_kernel(int32_t *sums, int32_t nsums) {
+    __shared__ int32_t carry;
+    __shared__ int32_t warp_tot[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int32_t b = 0; b < nsums; b += blockDim.x) {
+        const int32_t i = b + tid;
+        const int32_t x = i < nsums ? sums[i] : 0;
+        int32_t incl = x;
+        for (int m = 1; m < 32; m <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, incl, m);
+            if (lane >= m) incl += y;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        int32_t woff = 0;
+        for (int w = 0; w < warp; w++) woff += warp_tot[w];
+        const int32_t c = carry;
+        if (i < nsums) sums[i] = c + woff + incl - x;
+        __syncthreads();
+        if (tid == blockDim.x - 1) carry = c + woff + incl;
+        __syncthreads();
+    }
+}
+__global__ void add_tile_offsets_kernel(int32_t *__restrict__ out, int64_t len, const int32_t *__restrict__ sums) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] += sums[i / kScanTile];
+}
+
 int blocks_for(int64_t work, int threads) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -206,11 +369,24 @@ struct DevTmp {
     ~DevTmp() { if (p) cudaFree(p); }
 };
 
+// out[i] = in[0] + .. + in[i-1] for i < len (int32; the caller guarantees the
+// total fits); sums: scratch of at least ceil(len / kScanTile) int32.
+cudaError_t exclusive_scan(const int32_t *in, int64_t len, int32_t *out, int32_t *sums) {
+    if (len <= 0) return cudaSuccess;
+    const int64_t tiles = (len + kScanTile - 1) / kScanTile;
+    scan_tiles_kernel<<<(unsigned int)tiles, kScanThreads>>>(in, len, out, sums);
+    scan_sums_kernel<<<1, 1024>>>(sums, (int32_t)tiles);
+    add_tile_offsets_kernel<<<(unsigned int)((len + 255) / 256), 256>>>(out, len, sums);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-// Graph creation. The host does the O(n) work (offset checks, the
-// relabelling sort, new offsets, class ranges and tile tables); the device does
-// the O(nnz) work (validation of every source and the remapped copy of the rows).
+// Graph creation. The host checks the offsets and out-degrees (O(n) reads of
+// the caller's arrays) and builds the tile tables from the relabelled offsets;
+// the device validates every source, sorts the vertices into the relabelled
+// order (stable counting sort by degree classes), forms the new offsets by a
+// scan and writes the remapped rows.
 extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_offsets,
                                      const int32_t *in_sources, const int32_t *out_degree, pr_graph **out) {
     pr_clear_error();
@@ -233,7 +409,7 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     }
     if (deg_sum != nnz) return pr_fail(PR_EINVAL, "out_degree does not sum to nnz (it must match the edges in in_sources)");
     // ---- caller arrays on the device, sources validated there
-    DevTmp d_old_off, d_old_src, d_cnt, d_bad;
+    DevTmp d_old_off, d_old_src, d_old_od, d_cnt, d_bad;
     cudaError_t e = cudaSuccess;
     const size_t n_off = (size_t)n + 1 + kPad, n_src = (size_t)nnz + kPad, n_od = (size_t)n + kPad;
     pr_graph *g = new (std::nothrow) pr_graph();
@@ -252,14 +428,14 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     }
     e = cudaMalloc(&d_old_off.p, sizeof(int32_t) * ((size_t)n + 1));
     if (e == cudaSuccess) e = cudaMalloc(&d_old_src.p, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_old_od.p, sizeof(int32_t) * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&d_cnt.p, sizeof(int32_t) * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&d_bad.p, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(d_old_off.p, in_offsets, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_old_src.p, in_sources, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(d_cnt.p, 0, sizeof(int32_t) * (size_t)n);
     if (e == cudaSuccess) e = cudaMemset(d_bad.p, 0xFF, 2 * sizeof(unsigned long long));
-    // the caller's out-degrees go straight into the final array's scratch use: copy to d_outdeg first
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_outdeg, out_degree, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_old_od.p, out_degree, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_graph(g);
         return pr_cuda_fail(e, "graph upload");
@@ -268,7 +444,8 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     if (nnz > 0)
         count_sources_kernel<<<blocks_for(nnz, 256), 256>>>(static_cast<const int32_t *>(d_old_src.p), nnz, n,
                                                             static_cast<int32_t *>(d_cnt.p), bad);
-    check_outdeg_kernel<<<blocks_for(n, 256), 256>>>(static_cast<const int32_t *>(d_cnt.p), g->d_outdeg, n, bad + 1);
+    check_outdeg_kernel<<<blocks_for(n, 256), 256>>>(static_cast<const int32_t *>(d_cnt.p),
+                                                     static_cast<const int32_t *>(d_old_od.p), n, bad + 1);
     unsigned long long hbad[2] = {~0ull, ~0ull};
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpy(hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost);
@@ -284,72 +461,68 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
         free_graph(g);
         return pr_fail(PR_EINVAL, "out_degree[" + std::to_string(hbad[1]) + "] does not match the edges in in_sources");
     }
-    // ---- relabel on the host: stable counting sort by (in-class desc, out-class desc), O(n)
-    std::vector<int32_t> perm, inv, new_off, new_od, tmp;
+    // ---- relabel on the device: stable counting sort by (in-class desc,
+    // out-class desc, caller id); new offsets by a scan of the relabelled degrees
+    const int32_t *old_off = static_cast<const int32_t *>(d_old_off.p);
+    const int32_t *old_od = static_cast<const int32_t *>(d_old_od.p);
+    const int32_t nchunks = (int32_t)(((int64_t)n + kSortChunk - 1) / kSortChunk);
+    const int64_t mlen = (int64_t)kKeys * nchunks;
+    const int64_t nsums = std::max<int64_t>((mlen + kScanTile - 1) / kScanTile, ((int64_t)n + kScanTile - 1) / kScanTile);
+    DevTmp d_key, d_M, d_Ms, d_sums, d_cmax, d_starts, d_newdeg;
+    e = cudaMalloc(&d_key.p, sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_M.p, sizeof(int32_t) * (size_t)mlen);
+    if (e == cudaSuccess) e = cudaMalloc(&d_Ms.p, sizeof(int32_t) * (size_t)mlen);
+    if (e == cudaSuccess) e = cudaMalloc(&d_sums.p, sizeof(int32_t) * (size_t)nsums);
+    if (e == cudaSuccess) e = cudaMalloc(&d_cmax.p, sizeof(int32_t) * kClasses);
+    if (e == cudaSuccess) e = cudaMalloc(&d_starts.p, sizeof(int32_t) * kClasses);
+    if (e == cudaSuccess) e = cudaMalloc(&d_newdeg.p, sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemset(d_cmax.p, 0, sizeof(int32_t) * kClasses);
+    if (e == cudaSuccess) e = cudaMemset(g->d_off, 0, sizeof(int32_t) * n_off);
+    if (e == cudaSuccess) e = cudaMemset(g->d_src, 0, sizeof(int32_t) * n_src);
+    if (e == cudaSuccess) e = cudaMemset(g->d_outdeg, 0, sizeof(int32_t) * n_od);
+    int32_t *key = static_cast<int32_t *>(d_key.p), *M = static_cast<int32_t *>(d_M.p), *Ms = static_cast<int32_t *>(d_Ms.p);
+    int32_t *sums = static_cast<int32_t *>(d_sums.p), *cmax = static_cast<int32_t *>(d_cmax.p);
+    if (e == cudaSuccess) {
+        class_keys_kernel<<<blocks_for(n, 256), 256>>>(old_off, old_od, n, key, cmax);
+        chunk_hist_kernel<<<nchunks, kSortThreads>>>(key, n, nchunks, M);
+        e = exclusive_scan(M, mlen, Ms, sums);
+    }
+    if (e == cudaSuccess) {
+        chunk_scatter_kernel<<<nchunks, kSortThreads>>>(key, n, nchunks, Ms, g->d_perm, g->d_inv);
+        relabel_degrees_kernel<<<blocks_for(n, 256), 256>>>(g->d_perm, old_off, old_od, n,
+                                                           static_cast<int32_t *>(d_newdeg.p), g->d_outdeg);
+        e = exclusive_scan(static_cast<const int32_t *>(d_newdeg.p), n, g->d_off, sums);
+    }
+    if (e == cudaSuccess) {
+        const int32_t total = (int32_t)nnz;
+        class_starts_kernel<<<1, 64>>>(Ms, nchunks, static_cast<int32_t *>(d_starts.p));
+        e = cudaMemcpy(g->d_off + n, &total, sizeof(int32_t), cudaMemcpyHostToDevice);
+    }
+    std::vector<int32_t> new_off;
+    int32_t h_starts[kClasses], h_cmax[kClasses];
     try {
-        perm.resize((size_t)n);
-        inv.resize((size_t)n);
-        tmp.resize((size_t)n);
         new_off.resize((size_t)n + 1);
-        new_od.resize((size_t)n);
     } catch (const std::bad_alloc &) {
         free_graph(g);
         return pr_fail(PR_ENOMEM, "host allocation failed");
     }
-    {
-        size_t cnt[33];
-        std::memset(cnt, 0, sizeof(cnt));
-        for (int32_t v = 0; v < n; v++) cnt[32 - deg_class(out_degree[v])]++;
-        size_t acc = 0;
-        for (int b = 0; b < 33; b++) { size_t c = cnt[b]; cnt[b] = acc; acc += c; }
-        for (int32_t v = 0; v < n; v++) tmp[cnt[32 - deg_class(out_degree[v])]++] = v;
-        std::memset(cnt, 0, sizeof(cnt));
-        for (int32_t v = 0; v < n; v++) cnt[32 - deg_class(in_offsets[v + 1] - in_offsets[v])]++;
-        acc = 0;
-        for (int b = 0; b < 33; b++) { size_t c = cnt[b]; cnt[b] = acc; acc += c; }
-        for (int32_t i = 0; i < n; i++) {
-            const int32_t v = tmp[i];
-            perm[cnt[32 - deg_class(in_offsets[v + 1] - in_offsets[v])]++] = v;
-        }
-    }
-    new_off[0] = 0;
-    for (int32_t i = 0; i < n; i++) {
-        const int32_t v = perm[i];
-        inv[v] = i;
-        new_off[i + 1] = new_off[i] + (in_offsets[v + 1] - in_offsets[v]);
-        new_od[i] = out_degree[v];
-    }
-    {
-        int32_t i = 0;
-        while (i < n) {
-            const int c = deg_class(new_off[i + 1] - new_off[i]);
-            ClassRange cr{i, i, 0};
-            while (i < n && deg_class(new_off[i + 1] - new_off[i]) == c) {
-                cr.max_deg = std::max(cr.max_deg, new_off[i + 1] - new_off[i]);
-                i++;
-            }
-            cr.end = i;
-            g->classes.push_back(cr);
-        }
-    }
-    // ---- relabelled arrays on the device (padding zeroed), rows remapped there
-    e = cudaMemset(g->d_off, 0, sizeof(int32_t) * n_off);
-    if (e == cudaSuccess) e = cudaMemset(g->d_src, 0, sizeof(int32_t) * n_src);
-    if (e == cudaSuccess) e = cudaMemset(g->d_outdeg, 0, sizeof(int32_t) * n_od);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_off, new_off.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_outdeg, new_od.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_inv, inv.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(new_off.data(), g->d_off, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(h_starts, d_starts.p, sizeof(h_starts), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(h_cmax, d_cmax.p, sizeof(h_cmax), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && nnz > 0) {
-        remap_rows_kernel<<<blocks_for((int64_t)n * 32, 256), 256>>>(static_cast<const int32_t *>(d_old_off.p),
-                                                                     static_cast<const int32_t *>(d_old_src.p), g->d_off,
-                                                                     g->d_perm, g->d_inv, n, g->d_src);
+        remap_rows_kernel<<<blocks_for((int64_t)n * 32, 256), 256>>>(old_off, static_cast<const int32_t *>(d_old_src.p),
+                                                                     g->d_off, g->d_perm, g->d_inv, n, g->d_src);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_graph(g);
         return pr_cuda_fail(e, "graph relabel");
+    }
+    // in-degree classes in relabelled order: in-key ik = 32 - class, ascending
+    for (int ik = 0; ik < kClasses; ik++) {
+        const int32_t begin = h_starts[ik], end = ik + 1 < kClasses ? h_starts[ik + 1] : n;
+        if (end > begin) g->classes.push_back(ClassRange{begin, end, h_cmax[32 - ik]});
     }
     // signature for caches keyed by graph shape: FNV-1a over n, nnz and each
     // in-degree class's (first row, end row, largest in-degree, edges)

@@ -29,6 +29,9 @@ constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, 
 #ifndef PR_PREFETCH_TILE
 #define PR_PREFETCH_TILE 1
 #endif
+#ifndef PR_CHUNK_PIPE
+#define PR_CHUNK_PIPE 1
+#endif
 #ifndef PR_SMEM_CARVEOUT
 #define PR_SMEM_CARVEOUT -1
 #endif
@@ -42,6 +45,9 @@ constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, 
 #define PR_VEC_GATHER_BATCH 4
 #endif
 constexpr bool kPrefetchTile = PR_PREFETCH_TILE != 0;  // load the next tile's descriptor a tile ahead
+// One column, chunks of long rows: the next step's in-edge indices are loaded
+// while the current step's gathers are in flight.
+constexpr bool kChunkPipe = PR_CHUNK_PIPE != 0;
 // Shared-memory carveout requested for kernels with dynamic shared memory
 // (percent; -1 leaves the driver's choice).
 constexpr int kSmemCarveout = PR_SMEM_CARVEOUT;

@@ -587,19 +587,46 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
                 __syncwarp();
             }
             if (kStaged && cv.active) {
-                for (int base = lane; base < nv; base += VT) {
+                if constexpr (kChunkPipe) {
+                    // the next step's indices are requested while this step's
+                    // gathers are in flight
                     int32_t u[PER];
 #pragma unroll
                     for (int k = 0; k < PER; k++) {
-                        const int idx = base + 32 * k;
-                        u[k] = idx < nv ? src[T.e0 + idx / W] : -1;
+                        const int idx = lane + 32 * k;
+                        u[k] = idx < nv ? src[T.e0 + idx] : -1;
                     }
-                    V x[PER];
+                    for (int base = lane; base < nv; base += VT) {
+                        V x[PER];
 #pragma unroll
-                    for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? cv.c_prev[(size_t)u[k] * W + col] : N::zero();
+                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? cv.c_prev[u[k]] : N::zero();
+                        int32_t un[PER];
 #pragma unroll
-                    for (int k = 0; k < PER; k++)
-                        if (u[k] >= 0) sum.add(x[k]);
+                        for (int k = 0; k < PER; k++) {
+                            const int idx = base + VT + 32 * k;
+                            un[k] = idx < nv ? src[T.e0 + idx] : -1;
+                        }
+#pragma unroll
+                        for (int k = 0; k < PER; k++)
+                            if (u[k] >= 0) sum.add(x[k]);
+#pragma unroll
+                        for (int k = 0; k < PER; k++) u[k] = un[k];
+                    }
+                } else {
+                    for (int base = lane; base < nv; base += VT) {
+                        int32_t u[PER];
+#pragma unroll
+                        for (int k = 0; k < PER; k++) {
+                            const int idx = base + 32 * k;
+                            u[k] = idx < nv ? src[T.e0 + idx / W] : -1;
+                        }
+                        V x[PER];
+#pragma unroll
+                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? cv.c_prev[(size_t)u[k] * W + col] : N::zero();
+#pragma unroll
+                        for (int k = 0; k < PER; k++)
+                            if (u[k] >= 0) sum.add(x[k]);
+                    }
                 }
             }
             V sv = sum.get();
