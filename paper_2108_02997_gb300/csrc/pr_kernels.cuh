@@ -373,6 +373,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
     constexpr int VT = kStaged ? kTileValues : 32;   // gathered values per warp step
     constexpr int TR = kStaged ? tile_rows(W) : 1;
     constexpr int PER = VT / 32;             // gathers in flight per lane (staged path)
+    constexpr bool kTU = kTileUpdate && sizeof(V) == 8;   // all-lane row updates (8-byte values)
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int col = tid % W;                 // equals lane % W
@@ -394,6 +395,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
     __shared__ V s_prev[kWarps][kStaged ? TR * W : 1];
     __shared__ int32_t s_off[kWarps][kStaged ? TR + 1 : 1];
     __shared__ int32_t s_od[kWarps][kStaged ? TR : 1];
+    __shared__ V s_sum[kWarps][kStaged && kTU ? TR : 1];
     // several columns: per-warp buffers in dynamic shared memory
     constexpr int CP = vec_cols((int)sizeof(V), W);   // columns per vector load
     constexpr int NG = W / CP;                          // column groups (passes over a tile)
@@ -537,10 +539,23 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
                     }
                     V sv = sum.get();
                     for (int m = W; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-                    if (valid && es == 0 && need_prev)
-                        row_update_pd<V, W>(perm, cv, acc, T.r0 + r, col, sv, s_prev[warp][r * W + col], s_od[warp][r]);
+                    if constexpr (kTU) {
+                        if (valid && es == 0) s_sum[warp][r] = sv;
+                    } else {
+                        if (valid && es == 0 && need_prev)
+                            row_update_pd<V, W>(perm, cv, acc, T.r0 + r, col, sv, s_prev[warp][r * W + col],
+                                                s_od[warp][r]);
+                    }
                 }
                 __syncwarp();
+                if constexpr (kTU) {
+                    // every lane updates rows: consecutive rows on consecutive lanes
+                    if (need_prev)
+                        for (int r = lane; r < nr; r += 32)
+                            row_update_pd<V, W>(perm, cv, acc, T.r0 + r, col, s_sum[warp][r], s_prev[warp][r],
+                                                s_od[warp][r]);
+                    __syncwarp();
+                }
             }
         };
         // ---------------- one chunk of a long row
