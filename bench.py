@@ -298,7 +298,7 @@ def run_ours(args, world, rank, local):
         st = B.pr_last_solve_stats()
         n_src = int((g.outdeg > 0).sum())
         b = 4.0 * (g.n + 1) + 4.0 * g.nnz + 8.0 * n_src + 8.0 * g.n + 8.0 * g.n + 4.0 * g.n
-        iters_launched = st["launches"] - 1 - (1 if precision == "mixed" else 0)
+        iters_launched = st["passes"]
         k_ms += st["kernel_ms"]
         k_launches += iters_launched
         bytes_per_launch += b * iters_launched

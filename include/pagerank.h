@@ -329,18 +329,21 @@ pr_status pr_plan_columns(int32_t count, const double *iters, const double *us_p
  * Resident CTAs per SM of the iteration kernel for `precision` (PR_PREC_DF64,
  * PR_PREC_FP64 or PR_PREC_FP32) and column width `width` (1, 2, 4, .., 32) on
  * the current device, as the CUDA occupancy calculator reports it for the
- * kernel's 256 threads and shared memory; solves size their grids as this
- * times the SM count. PR_EINVAL for a bad argument, PR_ECUDA on failure.
+ * kernel's 256 threads and shared memory (for width 1, whose passes run as a
+ * gather kernel and an update kernel, the gather kernel's); solves size the
+ * gather grids as this times the SM count. PR_EINVAL for a bad argument,
+ * PR_ECUDA on failure.
  */
 pr_status pr_kernel_occupancy(int32_t precision, int32_t width, int32_t *ctas_per_sm);
 
 /*
  * Counters of the last solve on any thread (host pointers, each may be NULL):
- *   launches  : iteration-kernel launches (init passes included)
+ *   launches  : kernel launches of the solve loop (init passes included; a
+ *               one-column pass is two kernels, a gather and an update)
  *   passes    : iteration passes executed on the device
- *   kernel_ms : PR_LOOP_HOST only: sum over iteration launches of the CUDA-event
+ *   kernel_ms : PR_LOOP_HOST only: sum over iteration passes of the CUDA-event
  *               time between the events recorded just before and just after
- *               each launch on the solve's stream; 0 for PR_LOOP_GRAPH
+ *               each pass's launches on the solve's stream; 0 for PR_LOOP_GRAPH
  *   total_ms  : CUDA-event time of the whole device loop (all phases)
  */
 pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms);

@@ -32,6 +32,15 @@ constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, 
 #ifndef PR_CHUNK_PIPE
 #define PR_CHUNK_PIPE 1
 #endif
+#ifndef PR_SPLIT_PASSES
+#define PR_SPLIT_PASSES 1
+#endif
+#ifndef PR_GATHER_MIN_BLOCKS
+#define PR_GATHER_MIN_BLOCKS 4
+#endif
+#ifndef PR_UPDATE_MIN_BLOCKS
+#define PR_UPDATE_MIN_BLOCKS 3
+#endif
 #ifndef PR_TILE_UPDATE
 #define PR_TILE_UPDATE 1
 #endif
@@ -56,6 +65,12 @@ constexpr bool kChunkPipe = PR_CHUNK_PIPE != 0;
 // instead of the one lane per lane group that formed each sum (measured: 2-3 %
 // faster for df64, 1-3 % slower for float, whose update is cheap).
 constexpr bool kTileUpdate = PR_TILE_UPDATE != 0;
+// One column: each pass runs as two kernels, a gather kernel that only forms
+// the row sums (few registers, more resident warps) and a streaming update
+// kernel (new ranks, contributions, norms, stopping rules).
+constexpr bool kSplitPasses = PR_SPLIT_PASSES != 0;
+constexpr int kGatherMinBlocks = PR_GATHER_MIN_BLOCKS;
+constexpr int kUpdateMinBlocks = PR_UPDATE_MIN_BLOCKS;
 // Shared-memory carveout requested for kernels with dynamic shared memory
 // (percent; -1 leaves the driver's choice).
 constexpr int kSmemCarveout = PR_SMEM_CARVEOUT;
@@ -178,6 +193,8 @@ struct JobDev {
     Tap *taps;
     uint32_t arrive;          // CTAs of this job that finished the pass
     int32_t cur;              // buffer parity shared by the job's active columns
+    void *rowsum;             // one column, split passes: the n row sums of the pass
+    int32_t gcta_begin, gcta_count;   // CTAs of the gather pass (split passes)
 };
 
 struct GlobalDev {

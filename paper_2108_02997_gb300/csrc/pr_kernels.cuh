@@ -27,6 +27,9 @@
 #include "pr_internal.cuh"
 
 enum PassMode { kPassInit = 0, kPassIterate = 1 };
+// Iteration kernel flavours: the whole pass in one kernel, or (one column,
+// split passes) the gather half that only writes row sums.
+enum KernelMode { kModeFused = 0, kModeGather = 1 };
 
 // ---------------------------------------------------------------- small helpers
 template <typename V>
@@ -365,9 +368,13 @@ __global__ void __launch_bounds__(kBlock) pr_init_kernel(JobDev *jobs, GlobalDev
 }
 
 // ---------------------------------------------------------------- the iteration kernel
-template <typename V, int W>
-__global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((int)sizeof(V))) pr_iter_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
+template <typename V, int W, int Mode = kModeFused>
+__global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGatherMinBlocks : kMinBlocks)
+                                                 : vec_min_blocks((int)sizeof(V)))
+    pr_iter_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
     using N = Num<V>;
+    constexpr bool kGather = Mode == kModeGather;
+    static_assert(!kGather || W == 1, "the gather-only kernel serves one column");
     static_assert(32 % W == 0, "W must divide the warp");
     constexpr bool kStaged = (W == 1);       // one column: values staged in shared memory
     constexpr int VT = kStaged ? kTileValues : 32;   // gathered values per warp step
@@ -381,7 +388,8 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
     // The job's fields are read once into registers: reads through `job` would
     // be repeated after every global store, which the compiler must assume
     // could alias the descriptor.
-    const int local = blockIdx.x - job.cta_begin;
+    const int local = blockIdx.x - (kGather ? job.gcta_begin : job.cta_begin);
+    V *rowsum = reinterpret_cast<V *>(job.rowsum);
     const int32_t *__restrict__ src = job.src;
     const int32_t *__restrict__ off = job.off;
     const int32_t *__restrict__ outdeg = job.outdeg;
@@ -390,12 +398,12 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
     const int32_t *__restrict__ slot_base = job.slot_base;
     V *chunk_part = reinterpret_cast<V *>(job.chunk_part);
     uint32_t *chunk_cnt = job.chunk_cnt;
-    const int ntiles = job.ntiles, cta_count = job.cta_count;
+    const int ntiles = job.ntiles, cta_count = kGather ? job.gcta_count : job.cta_count;
     __shared__ V s_vals[kWarps][kStaged ? VT : 1];
-    __shared__ V s_prev[kWarps][kStaged ? TR * W : 1];
+    __shared__ V s_prev[kWarps][kStaged && !kGather ? TR * W : 1];
     __shared__ int32_t s_off[kWarps][kStaged ? TR + 1 : 1];
-    __shared__ int32_t s_od[kWarps][kStaged ? TR : 1];
-    __shared__ V s_sum[kWarps][kStaged && kTU ? TR : 1];
+    __shared__ int32_t s_od[kWarps][kStaged && !kGather ? TR : 1];
+    __shared__ V s_sum[kWarps][kStaged && kTU && !kGather ? TR : 1];
     // several columns: per-warp buffers in dynamic shared memory
     constexpr int CP = vec_cols((int)sizeof(V), W);   // columns per vector load
     constexpr int NG = W / CP;                          // column groups (passes over a tile)
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
     // Loop guard independent of the pass bookkeeping: should the job
     // finalizers ever fail to stop the graph's while-loop, the launch after the
     // cap ends it (no other thread sets the condition in that case).
-    if (blockIdx.x == 0 && tid == 0) {
+    if (!kGather && blockIdx.x == 0 && tid == 0) {
         unsigned int nb = atomicAdd(&glob->body_count, 1u) + 1u;
         if (nb > (unsigned int)glob->pass_cap + 8u) {
             glob->error = kErrLoopGuard;
@@ -512,9 +520,11 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
                 }
                 for (int i = lane; i <= nr; i += 32) s_off[warp][i] = off[T.r0 + i] - T.e0;
                 // element i of the rows belongs to column i % W == lane % W
-                if (need_prev)
-                    for (int i = lane; i < nr * W; i += 32) s_prev[warp][i] = cv.r_prev[(size_t)T.r0 * W + i];
-                for (int i = lane; i < nr; i += 32) s_od[warp][i] = outdeg[T.r0 + i];
+                if constexpr (!kGather) {
+                    if (need_prev)
+                        for (int i = lane; i < nr * W; i += 32) s_prev[warp][i] = cv.r_prev[(size_t)T.r0 * W + i];
+                    for (int i = lane; i < nr; i += 32) s_od[warp][i] = outdeg[T.r0 + i];
+                }
                 {
                     V x[PER];
 #pragma unroll
@@ -539,7 +549,9 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
                     }
                     V sv = sum.get();
                     for (int m = W; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-                    if constexpr (kTU) {
+                    if constexpr (kGather) {
+                        if (valid && es == 0 && cv.active) rowsum[T.r0 + r] = sv;
+                    } else if constexpr (kTU) {
                         if (valid && es == 0) s_sum[warp][r] = sv;
                     } else {
                         if (valid && es == 0 && need_prev)
@@ -548,7 +560,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
                     }
                 }
                 __syncwarp();
-                if constexpr (kTU) {
+                if constexpr (kTU && !kGather) {
                     // every lane updates rows: consecutive rows on consecutive lanes
                     if (need_prev)
                         for (int r = lane; r < nr; r += 32)
@@ -652,7 +664,11 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
                 __syncwarp();
             }
             if (T.slot < 0) {
-                if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, sv);
+                if constexpr (kGather) {
+                    if (lane == 0 && cv.active) rowsum[v] = sv;
+                } else {
+                    if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, sv);
+                }
             } else {
                 const int32_t base = slot_base[T.slot];
                 if (lane < W) chunk_part[(size_t)(base + T.k) * W + lane] = sv;
@@ -670,7 +686,11 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
                     for (int32_t q = lane / W; q < T.nch; q += QS)
                         t = N::add_pos(t, ld_cg_v<V>(chunk_part + (size_t)(base + q) * W + col));
                     for (int m = W; m < 32; m <<= 1) t = N::add_pos(t, N::shfl_xor(t, m));
-                    if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, t);
+                    if constexpr (kGather) {
+                        if (lane == 0 && cv.active) rowsum[v] = t;
+                    } else {
+                        if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, t);
+                    }
                     if (lane == 0) chunk_cnt[T.slot] = 0;
                 }
                 __syncwarp();
@@ -694,6 +714,60 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? kMinBlocks : vec_min_blocks((
             } else {
                 chunk_tile(T);
             }
+        }
+    }
+    if constexpr (!kGather) finish_pass<V, W>(jobs, job, glob, acc, local, kPassIterate);
+}
+
+// ---------------------------------------------------------------- the update kernel (split passes)
+// Second half of a split pass: streams the rows, turns each row sum into the
+// new rank (r' = c0 + alpha * s), its contribution or dangling share and the
+// norm terms, copies iterates into stopping-rule outputs, and ends the pass
+// like the fused kernel (CTA partials, last-CTA decisions, c0 for the next pass).
+template <typename V, int W>
+__global__ void __launch_bounds__(kBlock, kUpdateMinBlocks) pr_update_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
+    using N = Num<V>;
+    const int tid = threadIdx.x;
+    const int col = tid % W;
+    JobDev &job = jobs[cta_job[blockIdx.x]];
+    const int local = blockIdx.x - job.cta_begin;
+    if (blockIdx.x == 0 && tid == 0) {
+        unsigned int nb = atomicAdd(&glob->body_count, 1u) + 1u;
+        if (nb > (unsigned int)glob->pass_cap + 8u) {
+            glob->error = kErrLoopGuard;
+            if (glob->cond) cudaGraphSetConditional((cudaGraphConditionalHandle)glob->cond, 0u);
+        }
+    }
+    const ColView<V> cv = col_view<V>(job, col);
+    RowAcc<V> acc;
+    acc.init();
+    const bool work = job.alive && !*(volatile int32_t *)&glob->error;
+    if (work && cv.has && (cv.active || cv.copy_dst)) {
+        const V *__restrict__ rowsum = reinterpret_cast<const V *>(job.rowsum);
+        const int32_t *__restrict__ outdeg = job.outdeg;
+        const int32_t *__restrict__ perm = job.perm;
+        const V *__restrict__ r_prev = cv.r_prev;
+        const long long total = (long long)job.n * W;
+        const long long stride = (long long)job.cta_count * kBlock;
+        long long i = (long long)local * kBlock + tid;
+        // four rows per step, their loads issued before any update
+        for (; i + 3 * stride < total; i += 4 * stride) {
+            V sv[4], pv[4];
+            int32_t dv[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const long long j = i + k * stride;
+                sv[k] = cv.active ? rowsum[j] : N::zero();
+                pv[k] = r_prev[j];
+                dv[k] = outdeg[j / W];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                row_update_pd<V, W>(perm, cv, acc, (int32_t)((i + k * stride) / W), col, sv[k], pv[k], dv[k]);
+        }
+        for (; i < total; i += stride) {
+            const V sv = cv.active ? rowsum[i] : N::zero();
+            row_update<V, W>(outdeg, perm, cv, acc, (int32_t)(i / W), col, sv);
         }
     }
     finish_pass<V, W>(jobs, job, glob, acc, local, kPassIterate);

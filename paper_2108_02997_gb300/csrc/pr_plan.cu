@@ -196,8 +196,7 @@ pr_status time_width(const pr_graph *g, int precision, int W, cudaStream_t st, d
     std::vector<std::vector<Tap>> taps;
     pr_status s = pr_run_solve(r, taps);
     if (s != PR_OK) return s;
-    const int iter_launches = std::max(r.stats.launches - 1, 1);
-    *us = r.stats.kernel_ms * 1000.0 / iter_launches;
+    *us = r.stats.kernel_ms * 1000.0 / std::max(r.stats.passes, 1);
     if (decay) {
         // e_k = e1 rho^(k-1): rho from the last four differences, where the
         // start's fastest components have died out

@@ -51,6 +51,34 @@ void *iter_ptr(int W) {
         default: return (void *)pr_iter_kernel<V, 32>;
     }
 }
+// One column, split passes: the gather-only and update kernels.
+template <typename V>
+void *gather_ptr() { return (void *)pr_iter_kernel<V, 1, kModeGather>; }
+template <typename V>
+void *update_ptr() { return (void *)pr_update_kernel<V, 1>; }
+void *gather_kernel_for(int prec) {
+    switch (prec) {
+        case PR_PREC_FP64: return gather_ptr<double>();
+        case PR_PREC_FP32: return gather_ptr<float>();
+        default: return gather_ptr<df64>();
+    }
+}
+void *update_kernel_for(int prec) {
+    switch (prec) {
+        case PR_PREC_FP64: return update_ptr<double>();
+        case PR_PREC_FP32: return update_ptr<float>();
+        default: return update_ptr<df64>();
+    }
+}
+int resident_ctas(void *k, size_t smem) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBlock, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::max(occ, 1);
+}
+
 template <typename V>
 void *init_ptr(int W) {
     switch (W) {
@@ -87,7 +115,8 @@ struct HostJob {
     std::vector<int> cols;           // request column indices
     const TileTable *tt = nullptr;
     int cta_count = 0;
-    size_t off_r[2], off_c[2], off_cp, off_cnt, off_part, off_cols, off_taps, off_hist;
+    int gcta_count = 0;              // split passes: CTAs of the gather kernel
+    size_t off_r[2], off_c[2], off_cp, off_cnt, off_part, off_cols, off_taps, off_hist, off_rowsum = 0;
     int ntaps = 0;
     int hist_total = 0;
 };
@@ -157,6 +186,7 @@ extern "C" pr_status pr_kernel_occupancy(int32_t precision, int32_t width, int32
     int occ = 0;
     pr_status s = pr_kernel_setup(precision, width, &occ);
     if (s != PR_OK) return s;
+    if (width == 1 && kSplitPasses) occ = resident_ctas(gather_kernel_for(precision), 0);
     if (ctas_per_sm) *ctas_per_sm = occ;
     return PR_OK;
 }
@@ -174,8 +204,12 @@ namespace {
 
 // One phase of a solve in one value type: init pass + loop of iteration passes.
 pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size_t off_jobs, size_t off_glob,
-                    size_t off_ctajob, int total_ctas, int pass_cap, int loop, cudaStream_t st, LoopStats &stats) {
-    void *kiter = pr_iter_kernel_for(prec, W);
+                    size_t off_ctajob, int total_ctas, size_t off_gctajob, int total_gctas, int pass_cap, int loop,
+                    cudaStream_t st, LoopStats &stats) {
+    const bool split = W == 1 && kSplitPasses;
+    // split passes: the pass is the gather kernel then the update kernel
+    void *kiter = split ? update_kernel_for(prec) : pr_iter_kernel_for(prec, W);
+    void *kgather = split ? gather_kernel_for(prec) : nullptr;
     void *kinit = pr_init_kernel_for(prec, W);
     const size_t smem = pr_tile_smem_bytes(prec, W);
     int occ = 0;
@@ -184,6 +218,7 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
     JobDev *d_jobs = ar.at<JobDev>(off_jobs);
     GlobalDev *d_glob = ar.at<GlobalDev>(off_glob);
     const int32_t *d_ctajob = ar.at<int32_t>(off_ctajob);
+    const int32_t *d_gctajob = split ? ar.at<int32_t>(off_gctajob) : nullptr;
     GlobalDev hg;
     std::memset(&hg, 0, sizeof(hg));
     hg.njobs = (int32_t)jobs.size();
@@ -193,7 +228,9 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
     PR_CUDA(cudaEventCreate(&ev1));
     struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{ev0, ev1};
     void *args[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_ctajob};
-    dim3 grid(total_ctas), block(kBlock);
+    void *gargs[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_gctajob};
+    dim3 grid(total_ctas), ggrid(split ? total_gctas : 1), block(kBlock);
+    const size_t iter_smem = split ? 0 : smem;
     PR_CUDA(cudaEventRecord(ev0, st));
     if (loop == PR_LOOP_HOST) {
         hg.cond = 0;
@@ -208,7 +245,11 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
         std::memset(&back, 0, sizeof(back));
         for (int p = 0; p < pass_cap + 1; p++) {
             PR_CUDA(cudaEventRecord(k0, st));
-            PR_CUDA(cudaLaunchKernel(kiter, grid, block, args, smem, st));
+            if (split) {
+                PR_CUDA(cudaLaunchKernel(kgather, ggrid, block, gargs, 0, st));
+                stats.launches++;
+            }
+            PR_CUDA(cudaLaunchKernel(kiter, grid, block, args, iter_smem, st));
             PR_CUDA(cudaEventRecord(k1, st));
             stats.launches++;
             PR_CUDA(cudaMemcpyAsync(&back, d_glob, sizeof(back), cudaMemcpyDeviceToHost, st));
@@ -247,16 +288,25 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
         cp.conditional.size = 1;
         PR_CUDA(cudaGraphAddNode(&n_cond, graph, &n_init, nullptr, 1, &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t n_gather = nullptr;
+        if (split) {
+            cudaKernelNodeParams gp = kp;
+            gp.func = kgather;
+            gp.gridDim = ggrid;
+            gp.sharedMemBytes = 0;
+            gp.kernelParams = gargs;
+            PR_CUDA(cudaGraphAddKernelNode(&n_gather, body, nullptr, 0, &gp));
+        }
         kp.func = kiter;
-        kp.sharedMemBytes = (unsigned int)smem;
-        PR_CUDA(cudaGraphAddKernelNode(&n_body, body, nullptr, 0, &kp));
+        kp.sharedMemBytes = (unsigned int)iter_smem;
+        PR_CUDA(cudaGraphAddKernelNode(&n_body, body, split ? &n_gather : nullptr, split ? 1 : 0, &kp));
         PR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
         PR_CUDA(cudaGraphLaunch(exec, st));
         GlobalDev back;
         std::memset(&back, 0, sizeof(back));
         PR_CUDA(cudaMemcpyAsync(&back, d_glob, sizeof(back), cudaMemcpyDeviceToHost, st));
         PR_CUDA(cudaStreamSynchronize(st));
-        stats.launches += 1 + (int)back.body_count;
+        stats.launches += 1 + (split ? 2 : 1) * (int)back.body_count;
         stats.passes += back.pass;
         if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
     }
@@ -321,17 +371,38 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         if ((s = pr_kernel_setup(PR_PREC_DF64, W, &occ2)) != PR_OK) return s;
         occ = std::min(occ, occ2);
     }
-    const int budget = sms * occ;
+    const bool split = W == 1 && kSplitPasses;
+    int occ_gather = 1;
+    if (split) {
+        // split passes: the update kernel's grid carries the pass bookkeeping,
+        // the gather kernel gets its own (more resident CTAs)
+        occ = resident_ctas(update_kernel_for(prec1), 0);
+        occ_gather = resident_ctas(gather_kernel_for(prec1), 0);
+        if (mixed) {
+            occ = std::min(occ, resident_ctas(update_kernel_for(PR_PREC_DF64), 0));
+            occ_gather = std::min(occ_gather, resident_ctas(gather_kernel_for(PR_PREC_DF64), 0));
+        }
+    }
+    const int budget = sms * occ, gbudget = sms * occ_gather;
     double total_work = 0.0;
     for (auto &j : jobs) {
         s = pr_graph_tiles(const_cast<pr_graph *>(j.g), W, &j.tt);
         if (s != PR_OK) return s;
         total_work += std::max(j.tt->work, 1.0);
     }
-    int total_ctas = 0;
+    int total_ctas = 0, total_gctas = 0;
     for (auto &j : jobs) {
-        int want = (int)std::lround(budget * std::max(j.tt->work, 1.0) / total_work);
-        j.cta_count = std::max(1, std::min(want, std::max(j.tt->ntiles, 1)));
+        const double share = std::max(j.tt->work, 1.0) / total_work;
+        int want = (int)std::lround(budget * share);
+        if (split) {
+            // update kernel: rows grid-stride
+            j.cta_count = std::max(1, std::min<int>(want, (int)(((int64_t)j.g->n + kBlock - 1) / kBlock)));
+            int gwant = (int)std::lround(gbudget * share);
+            j.gcta_count = std::max(1, std::min(gwant, std::max(j.tt->ntiles, 1)));
+            total_gctas += j.gcta_count;
+        } else {
+            j.cta_count = std::max(1, std::min(want, std::max(j.tt->ntiles, 1)));
+        }
         total_ctas += j.cta_count;
     }
     // ---- workspace layout (value buffers padded for 16-byte tile copies)
@@ -349,6 +420,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         j.off_cp = ar.reserve((size_t)std::max(j.tt->n_chunk_slots, 1) * W * vs_max);
         j.off_cnt = ar.reserve((size_t)std::max(j.tt->n_long, 1) * sizeof(uint32_t));
         j.off_part = ar.reserve((size_t)j.cta_count * W * kPartials * sizeof(double));
+        if (split) j.off_rowsum = ar.reserve((n + kPad) * vs_max);
         j.off_cols = ar.reserve((size_t)W * sizeof(ColState));
         for (int c : j.cols) j.ntaps += (int)req.cols[c].taps.size();
         j.off_taps = ar.reserve((size_t)std::max(j.ntaps, 1) * sizeof(Tap));
@@ -373,11 +445,13 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     const size_t off_jobs = ar.reserve(jobs.size() * sizeof(JobDev));
     const size_t off_glob = ar.reserve(sizeof(GlobalDev));
     const size_t off_ctajob = ar.reserve((size_t)total_ctas * sizeof(int32_t));
+    const size_t off_gctajob = ar.reserve((size_t)std::max(total_gctas, 1) * sizeof(int32_t));
     s = ar.alloc();
     if (s != PR_OK) return s;
     // ---- fill job and column state on the host
     std::vector<JobDev> hjobs(jobs.size());
-    std::vector<int32_t> ctajob(total_ctas);
+    std::vector<int32_t> ctajob(total_ctas), gctajob(std::max(total_gctas, 1), 0);
+    int gcta_at = 0;
     std::vector<std::vector<ColState>> hcols(jobs.size());
     std::vector<std::vector<Tap>> htaps(jobs.size());
     size_t stage_i = 0;
@@ -398,6 +472,13 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         d.cta_count = j.cta_count;
         for (int q = 0; q < j.cta_count; q++) ctajob[cta_at + q] = (int32_t)ji;
         cta_at += j.cta_count;
+        if (split) {
+            d.gcta_begin = gcta_at;
+            d.gcta_count = j.gcta_count;
+            for (int q = 0; q < j.gcta_count; q++) gctajob[gcta_at + q] = (int32_t)ji;
+            gcta_at += j.gcta_count;
+            d.rowsum = ar.at<void>(j.off_rowsum);
+        }
         d.ncols = (int32_t)j.cols.size();
         d.alive = 1;
         d.cur = 0;
@@ -461,9 +542,11 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     }
     PR_CUDA(cudaMemcpyAsync(ar.at<JobDev>(off_jobs), hjobs.data(), hjobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice, st));
     PR_CUDA(cudaMemcpyAsync(ar.at<int32_t>(off_ctajob), ctajob.data(), ctajob.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    PR_CUDA(cudaMemcpyAsync(ar.at<int32_t>(off_gctajob), gctajob.data(), gctajob.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     const int pass_cap = req.max_passes > 0 ? req.max_passes : max_iter_all + 3;
     // ---- phase 1 (or the only phase)
-    s = run_phase(prec1, W, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, pass_cap, req.loop, st, stats);
+    s = run_phase(prec1, W, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, off_gctajob, total_gctas, pass_cap,
+                  req.loop, st, stats);
     if (s != PR_OK) return s;
     // ---- mixed precision: refinement phase in DF64 from the FP32 iterates
     if (mixed) {
@@ -502,7 +585,8 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         if (any) {
             PR_CUDA(cudaMemcpyAsync(ar.at<JobDev>(off_jobs), hjobs.data(), hjobs.size() * sizeof(JobDev),
                                     cudaMemcpyHostToDevice, st));
-            s = run_phase(PR_PREC_DF64, W, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, pass_cap, req.loop, st, stats);
+            s = run_phase(PR_PREC_DF64, W, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, off_gctajob, total_gctas,
+                          pass_cap, req.loop, st, stats);
             if (s != PR_OK) return s;
         }
     }

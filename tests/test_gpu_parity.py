@@ -100,7 +100,10 @@ def test_host_loop_equals_graph_loop(B, er10k_dev):
     b = B.pr_solve(er10k_dev, 0.85, 1e-10, 2, 500, loop="host")
     assert a.iters == b.iters and np.array_equal(a.ranks, b.ranks) and a.err == b.err
     st = B.pr_last_solve_stats()
-    assert st["launches"] == b.iters + 2 and st["kernel_ms"] > 0
+    # init + one pass per update + the pass that copies the answer out; a pass
+    # is one kernel, or two (gather + update) for one column
+    assert st["passes"] == b.iters + 1 and st["kernel_ms"] > 0
+    assert st["launches"] in (1 + st["passes"], 1 + 2 * st["passes"])
 
 
 def test_user_start_vector(B, orc, er10k, er10k_dev):
