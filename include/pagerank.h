@@ -348,6 +348,16 @@ pr_status pr_kernel_occupancy(int32_t precision, int32_t width, int32_t *ctas_pe
  */
 pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms);
 
+/*
+ * The last solve's kernel_ms (PR_LOOP_HOST) split by kernel for one-column
+ * passes, which run as a gather kernel (row sums) and an update kernel (new
+ * ranks, norms, stopping rules): the CUDA-event time from the start of each
+ * pass to the end of its gather kernel, and from there to the end of the
+ * pass, summed over passes. Both 0 when the passes were single kernels or the
+ * loop was PR_LOOP_GRAPH. Host pointers, each may be NULL.
+ */
+pr_status pr_last_solve_kernel_ms(double *gather_ms, double *update_ms);
+
 /* Message for the last error on this thread ("" if none). */
 const char *pr_last_error(void);
 

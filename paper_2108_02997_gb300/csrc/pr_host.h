@@ -70,8 +70,11 @@ struct SolveStats {
     int passes = 0;         // iteration passes the device performed
     double kernel_ms = 0.0; // PR_LOOP_HOST: sum of the iteration launches' event times
     double total_ms = 0.0;  // device time of the whole solve
+    double gather_ms = 0.0; // PR_LOOP_HOST, split passes: the gather kernels' share of kernel_ms
+    double update_ms = 0.0; //   and the update kernels' share
     void add(const SolveStats &o) {
         launches += o.launches; passes += o.passes; kernel_ms += o.kernel_ms; total_ms += o.total_ms;
+        gather_ms += o.gather_ms; update_ms += o.update_ms;
     }
 };
 

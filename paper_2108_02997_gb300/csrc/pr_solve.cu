@@ -191,6 +191,13 @@ extern "C" pr_status pr_kernel_occupancy(int32_t precision, int32_t width, int32
     return PR_OK;
 }
 
+extern "C" pr_status pr_last_solve_kernel_ms(double *gather_ms, double *update_ms) {
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    if (gather_ms) *gather_ms = g_last_stats.gather_ms;
+    if (update_ms) *update_ms = g_last_stats.update_ms;
+    return PR_OK;
+}
+
 extern "C" pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms) {
     std::lock_guard<std::mutex> lk(g_stats_mu);
     if (launches) *launches = g_last_stats.launches;
@@ -237,16 +244,21 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
         PR_CUDA(cudaMemcpyAsync(d_glob, &hg, sizeof(hg), cudaMemcpyHostToDevice, st));
         PR_CUDA(cudaLaunchKernel(kinit, grid, block, args, 0, st));
         stats.launches++;
-        cudaEvent_t k0 = nullptr, k1 = nullptr;
+        cudaEvent_t k0 = nullptr, km = nullptr, k1 = nullptr;
         PR_CUDA(cudaEventCreate(&k0));
+        PR_CUDA(cudaEventCreate(&km));
         PR_CUDA(cudaEventCreate(&k1));
-        struct KGuard { cudaEvent_t a, b; ~KGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } kg{k0, k1};
+        struct KGuard {
+            cudaEvent_t a, b, c;
+            ~KGuard() { cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c); }
+        } kg{k0, km, k1};
         GlobalDev back;
         std::memset(&back, 0, sizeof(back));
         for (int p = 0; p < pass_cap + 1; p++) {
             PR_CUDA(cudaEventRecord(k0, st));
             if (split) {
                 PR_CUDA(cudaLaunchKernel(kgather, ggrid, block, gargs, 0, st));
+                PR_CUDA(cudaEventRecord(km, st));
                 stats.launches++;
             }
             PR_CUDA(cudaLaunchKernel(kiter, grid, block, args, iter_smem, st));
@@ -257,6 +269,12 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
             float ms = 0.f;
             PR_CUDA(cudaEventElapsedTime(&ms, k0, k1));
             stats.kernel_ms += ms;
+            if (split) {
+                float mg = 0.f;
+                PR_CUDA(cudaEventElapsedTime(&mg, k0, km));
+                stats.gather_ms += mg;
+                stats.update_ms += ms - mg;
+            }
             if (!back.alive || back.error) break;
         }
         stats.passes += back.pass;
