@@ -65,12 +65,16 @@ constexpr bool kChunkPipe = PR_CHUNK_PIPE != 0;
 // instead of the one lane per lane group that formed each sum (measured: 2-3 %
 // faster for df64, 1-3 % slower for float, whose update is cheap).
 constexpr bool kTileUpdate = PR_TILE_UPDATE != 0;
-// One column: each pass runs as two kernels, a gather kernel that only forms
-// the row sums (few registers, more resident warps) and a streaming update
-// kernel (new ranks, contributions, norms, stopping rules).
+// Each pass runs as two kernels: a gather kernel that only forms the row sums
+// (fewer registers, more resident warps) and a streaming update kernel (new
+// ranks, contributions, norms, stopping rules).
 constexpr bool kSplitPasses = PR_SPLIT_PASSES != 0;
 constexpr int kGatherMinBlocks = PR_GATHER_MIN_BLOCKS;
 constexpr int kUpdateMinBlocks = PR_UPDATE_MIN_BLOCKS;
+#ifndef PR_VEC_GATHER_MIN_BLOCKS
+#define PR_VEC_GATHER_MIN_BLOCKS 3
+#endif
+constexpr int kVecGatherMinBlocks = PR_VEC_GATHER_MIN_BLOCKS;   // several columns, gather kernel
 // Shared-memory carveout requested for kernels with dynamic shared memory
 // (percent; -1 leaves the driver's choice).
 constexpr int kSmemCarveout = PR_SMEM_CARVEOUT;
@@ -92,14 +96,15 @@ __host__ __device__ constexpr int chunk_edges(int W) { return W == 1 ? kChunkVal
 __host__ __device__ constexpr int vec_cols(int vbytes, int W) { return W * vbytes >= 16 ? 16 / vbytes : W; }
 __host__ __device__ constexpr int round16(int b) { return (b + 15) & ~15; }
 // Per-warp shared buffers of a multi-column tile, in bytes and in this order:
-// gathered vectors [kVecTileEdges], row sums [tile_rows * W], previous ranks
-// [tile_rows * W], in-edge sources [kVecTileEdges], row offsets
-// [tile_rows + 1], out-degrees [tile_rows].
+// gathered vectors [kVecTileEdges], row sums [tile_rows * W], in-edge sources
+// [kVecTileEdges], row offsets [tile_rows + 1], and, when the kernel also
+// updates the rows (not the gather-only kernel), previous ranks
+// [tile_rows * W] and out-degrees [tile_rows].
 __host__ __device__ constexpr int vec_vals_bytes(int vbytes, int W) { return kVecTileEdges * vec_cols(vbytes, W) * vbytes; }
 __host__ __device__ constexpr int vec_rows_bytes(int vbytes, int W) { return round16(tile_rows(W) * W * vbytes); }
-__host__ __device__ constexpr int vec_warp_bytes(int vbytes, int W) {
-    return vec_vals_bytes(vbytes, W) + 2 * vec_rows_bytes(vbytes, W) + kVecTileEdges * 4 +
-           round16((tile_rows(W) + 1) * 4) + round16(tile_rows(W) * 4);
+__host__ __device__ constexpr int vec_warp_bytes(int vbytes, int W, bool gather_only) {
+    return vec_vals_bytes(vbytes, W) + vec_rows_bytes(vbytes, W) + kVecTileEdges * 4 + round16((tile_rows(W) + 1) * 4) +
+           (gather_only ? 0 : vec_rows_bytes(vbytes, W) + round16(tile_rows(W) * 4));
 }
 
 // ------------------------------------------------------------------ work tiles

@@ -370,11 +370,10 @@ __global__ void __launch_bounds__(kBlock) pr_init_kernel(JobDev *jobs, GlobalDev
 // ---------------------------------------------------------------- the iteration kernel
 template <typename V, int W, int Mode = kModeFused>
 __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGatherMinBlocks : kMinBlocks)
-                                                 : vec_min_blocks((int)sizeof(V)))
+                                                 : (Mode == kModeGather ? kVecGatherMinBlocks : vec_min_blocks((int)sizeof(V))))
     pr_iter_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
     using N = Num<V>;
     constexpr bool kGather = Mode == kModeGather;
-    static_assert(!kGather || W == 1, "the gather-only kernel serves one column");
     static_assert(32 % W == 0, "W must divide the warp");
     constexpr bool kStaged = (W == 1);       // one column: values staged in shared memory
     constexpr int VT = kStaged ? kTileValues : 32;   // gathered values per warp step
@@ -410,14 +409,15 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
     constexpr int VTR = tile_rows(W);
     using VV = VecV<V, CP>;
     extern __shared__ __align__(16) unsigned char pr_dyn_smem[];
-    unsigned char *wbase = pr_dyn_smem + (size_t)warp * vec_warp_bytes((int)sizeof(V), W);
+    unsigned char *wbase = pr_dyn_smem + (size_t)warp * vec_warp_bytes((int)sizeof(V), W, kGather);
     VV *v_vals = reinterpret_cast<VV *>(wbase);
     V *v_rsum = reinterpret_cast<V *>(wbase + vec_vals_bytes((int)sizeof(V), W));
-    V *v_prev = reinterpret_cast<V *>(wbase + vec_vals_bytes((int)sizeof(V), W) + vec_rows_bytes((int)sizeof(V), W));
     int32_t *v_src = reinterpret_cast<int32_t *>(wbase + vec_vals_bytes((int)sizeof(V), W) +
-                                                 2 * vec_rows_bytes((int)sizeof(V), W));
+                                                 vec_rows_bytes((int)sizeof(V), W));
     int32_t *v_off = v_src + kVecTileEdges;
-    int32_t *v_od = v_off + round16((VTR + 1) * 4) / 4;
+    V *v_prev = reinterpret_cast<V *>(v_off + round16((VTR + 1) * 4) / 4);   // not in the gather-only kernel
+    int32_t *v_od = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(v_prev) +
+                                                vec_rows_bytes((int)sizeof(V), W));
 
     // Loop guard independent of the pass bookkeeping: should the job
     // finalizers ever fail to stop the graph's while-loop, the launch after the
@@ -453,9 +453,11 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                     if (i < ne) v_src[i] = src[T.e0 + i];
                 }
                 for (int i = lane; i <= nr; i += 32) v_off[i] = off[T.r0 + i] - T.e0;
-                for (int i = lane; i < nr; i += 32) v_od[i] = outdeg[T.r0 + i];
-                if (need_prev)
-                    for (int i = lane; i < nr * W; i += 32) v_prev[i] = cv.r_prev[(size_t)T.r0 * W + i];
+                if constexpr (!kGather) {
+                    for (int i = lane; i < nr; i += 32) v_od[i] = outdeg[T.r0 + i];
+                    if (need_prev)
+                        for (int i = lane; i < nr * W; i += 32) v_prev[i] = cv.r_prev[(size_t)T.r0 * W + i];
+                }
                 __syncwarp();
                 const int g = 1 << T.glog;
                 const int es = lane & (g - 1);
@@ -501,9 +503,15 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                     }
                     __syncwarp();
                 }
-                if (need_prev)
-                    for (int i = lane; i < nr * W; i += 32)
-                        row_update_pd<V, W>(perm, cv, acc, T.r0 + i / W, col, v_rsum[i], v_prev[i], v_od[i / W]);
+                if constexpr (kGather) {
+                    // element i of the rows belongs to column i % W == lane % W
+                    if (cv.active)
+                        for (int i = lane; i < nr * W; i += 32) rowsum[(size_t)T.r0 * W + i] = v_rsum[i];
+                } else {
+                    if (need_prev)
+                        for (int i = lane; i < nr * W; i += 32)
+                            row_update_pd<V, W>(perm, cv, acc, T.r0 + i / W, col, v_rsum[i], v_prev[i], v_od[i / W]);
+                }
                 __syncwarp();
             }
         };
@@ -665,7 +673,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
             }
             if (T.slot < 0) {
                 if constexpr (kGather) {
-                    if (lane == 0 && cv.active) rowsum[v] = sv;
+                    if (lane < W && cv.active) rowsum[(size_t)v * W + lane] = sv;
                 } else {
                     if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, sv);
                 }
@@ -687,7 +695,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                         t = N::add_pos(t, ld_cg_v<V>(chunk_part + (size_t)(base + q) * W + col));
                     for (int m = W; m < 32; m <<= 1) t = N::add_pos(t, N::shfl_xor(t, m));
                     if constexpr (kGather) {
-                        if (lane == 0 && cv.active) rowsum[v] = t;
+                        if (lane < W && cv.active) rowsum[(size_t)v * W + lane] = t;
                     } else {
                         if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, t);
                     }

@@ -15,6 +15,8 @@
 
 #include "pr_kernels.cuh"
 
+size_t gather_smem_bytes(int prec, int W);   // below, beside pr_tile_smem_bytes
+
 namespace {
 
 struct Arena {
@@ -51,23 +53,41 @@ void *iter_ptr(int W) {
         default: return (void *)pr_iter_kernel<V, 32>;
     }
 }
-// One column, split passes: the gather-only and update kernels.
+// Split passes: the gather-only and update kernels.
 template <typename V>
-void *gather_ptr() { return (void *)pr_iter_kernel<V, 1, kModeGather>; }
-template <typename V>
-void *update_ptr() { return (void *)pr_update_kernel<V, 1>; }
-void *gather_kernel_for(int prec) {
-    switch (prec) {
-        case PR_PREC_FP64: return gather_ptr<double>();
-        case PR_PREC_FP32: return gather_ptr<float>();
-        default: return gather_ptr<df64>();
+void *gather_ptr(int W) {
+    switch (W) {
+        case 1: return (void *)pr_iter_kernel<V, 1, kModeGather>;
+        case 2: return (void *)pr_iter_kernel<V, 2, kModeGather>;
+        case 4: return (void *)pr_iter_kernel<V, 4, kModeGather>;
+        case 8: return (void *)pr_iter_kernel<V, 8, kModeGather>;
+        case 16: return (void *)pr_iter_kernel<V, 16, kModeGather>;
+        default: return (void *)pr_iter_kernel<V, 32, kModeGather>;
     }
 }
-void *update_kernel_for(int prec) {
+template <typename V>
+void *update_ptr(int W) {
+    switch (W) {
+        case 1: return (void *)pr_update_kernel<V, 1>;
+        case 2: return (void *)pr_update_kernel<V, 2>;
+        case 4: return (void *)pr_update_kernel<V, 4>;
+        case 8: return (void *)pr_update_kernel<V, 8>;
+        case 16: return (void *)pr_update_kernel<V, 16>;
+        default: return (void *)pr_update_kernel<V, 32>;
+    }
+}
+void *gather_kernel_for(int prec, int W) {
     switch (prec) {
-        case PR_PREC_FP64: return update_ptr<double>();
-        case PR_PREC_FP32: return update_ptr<float>();
-        default: return update_ptr<df64>();
+        case PR_PREC_FP64: return gather_ptr<double>(W);
+        case PR_PREC_FP32: return gather_ptr<float>(W);
+        default: return gather_ptr<df64>(W);
+    }
+}
+void *update_kernel_for(int prec, int W) {
+    switch (prec) {
+        case PR_PREC_FP64: return update_ptr<double>(W);
+        case PR_PREC_FP32: return update_ptr<float>(W);
+        default: return update_ptr<df64>(W);
     }
 }
 int resident_ctas(void *k, size_t smem) {
@@ -77,6 +97,28 @@ int resident_ctas(void *k, size_t smem) {
         return 1;
     }
     return std::max(occ, 1);
+}
+
+// Split passes: opt the gather kernel into its dynamic shared memory (once per
+// process, precision and width) and report both kernels' residency.
+pr_status setup_split(int prec, int W, int *occ_gather, int *occ_update) {
+    static std::mutex mu;
+    static bool done[4][6] = {};
+    void *kg = gather_kernel_for(prec, W);
+    const size_t smem = gather_smem_bytes(prec, W);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        const int pi = prec & 3, wi = w_index(W);
+        if (!done[pi][wi]) {
+            PR_CUDA(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (smem > 0 && kSmemCarveout >= 0)
+                PR_CUDA(cudaFuncSetAttribute(kg, cudaFuncAttributePreferredSharedMemoryCarveout, kSmemCarveout));
+            done[pi][wi] = true;
+        }
+    }
+    *occ_gather = resident_ctas(kg, smem);
+    *occ_update = resident_ctas(update_kernel_for(prec, W), 0);
+    return PR_OK;
 }
 
 template <typename V>
@@ -147,7 +189,13 @@ void *pr_init_kernel_for(int prec, int W) {
 size_t pr_tile_smem_bytes(int prec, int W) {
     const int vbytes = prec == PR_PREC_FP32 ? 4 : 8;
     if (W == 1) return 0;
-    return (size_t)kWarps * vec_warp_bytes(vbytes, W);
+    return (size_t)kWarps * vec_warp_bytes(vbytes, W, false);
+}
+// The gather-only kernel's: no previous ranks or out-degrees staged.
+size_t gather_smem_bytes(int prec, int W) {
+    const int vbytes = prec == PR_PREC_FP32 ? 4 : 8;
+    if (W == 1) return 0;
+    return (size_t)kWarps * vec_warp_bytes(vbytes, W, true);
 }
 
 // Opt the iteration kernel into its dynamic shared memory (once per process
@@ -186,7 +234,10 @@ extern "C" pr_status pr_kernel_occupancy(int32_t precision, int32_t width, int32
     int occ = 0;
     pr_status s = pr_kernel_setup(precision, width, &occ);
     if (s != PR_OK) return s;
-    if (width == 1 && kSplitPasses) occ = resident_ctas(gather_kernel_for(precision), 0);
+    if (kSplitPasses) {
+        int ou = 1;
+        if ((s = setup_split(precision, width, &occ, &ou)) != PR_OK) return s;
+    }
     if (ctas_per_sm) *ctas_per_sm = occ;
     return PR_OK;
 }
@@ -213,10 +264,10 @@ namespace {
 pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size_t off_jobs, size_t off_glob,
                     size_t off_ctajob, int total_ctas, size_t off_gctajob, int total_gctas, int pass_cap, int loop,
                     cudaStream_t st, LoopStats &stats) {
-    const bool split = W == 1 && kSplitPasses;
+    const bool split = kSplitPasses;
     // split passes: the pass is the gather kernel then the update kernel
-    void *kiter = split ? update_kernel_for(prec) : pr_iter_kernel_for(prec, W);
-    void *kgather = split ? gather_kernel_for(prec) : nullptr;
+    void *kiter = split ? update_kernel_for(prec, W) : pr_iter_kernel_for(prec, W);
+    void *kgather = split ? gather_kernel_for(prec, W) : nullptr;
     void *kinit = pr_init_kernel_for(prec, W);
     const size_t smem = pr_tile_smem_bytes(prec, W);
     int occ = 0;
@@ -237,7 +288,7 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
     void *args[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_ctajob};
     void *gargs[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_gctajob};
     dim3 grid(total_ctas), ggrid(split ? total_gctas : 1), block(kBlock);
-    const size_t iter_smem = split ? 0 : smem;
+    const size_t iter_smem = split ? 0 : smem, gather_smem = split ? gather_smem_bytes(prec, W) : 0;
     PR_CUDA(cudaEventRecord(ev0, st));
     if (loop == PR_LOOP_HOST) {
         hg.cond = 0;
@@ -257,7 +308,7 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
         for (int p = 0; p < pass_cap + 1; p++) {
             PR_CUDA(cudaEventRecord(k0, st));
             if (split) {
-                PR_CUDA(cudaLaunchKernel(kgather, ggrid, block, gargs, 0, st));
+                PR_CUDA(cudaLaunchKernel(kgather, ggrid, block, gargs, gather_smem, st));
                 PR_CUDA(cudaEventRecord(km, st));
                 stats.launches++;
             }
@@ -311,7 +362,7 @@ pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size
             cudaKernelNodeParams gp = kp;
             gp.func = kgather;
             gp.gridDim = ggrid;
-            gp.sharedMemBytes = 0;
+            gp.sharedMemBytes = (unsigned int)gather_smem;
             gp.kernelParams = gargs;
             PR_CUDA(cudaGraphAddKernelNode(&n_gather, body, nullptr, 0, &gp));
         }
@@ -389,16 +440,17 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         if ((s = pr_kernel_setup(PR_PREC_DF64, W, &occ2)) != PR_OK) return s;
         occ = std::min(occ, occ2);
     }
-    const bool split = W == 1 && kSplitPasses;
+    const bool split = kSplitPasses;
     int occ_gather = 1;
     if (split) {
         // split passes: the update kernel's grid carries the pass bookkeeping,
         // the gather kernel gets its own (more resident CTAs)
-        occ = resident_ctas(update_kernel_for(prec1), 0);
-        occ_gather = resident_ctas(gather_kernel_for(prec1), 0);
+        if ((s = setup_split(prec1, W, &occ_gather, &occ)) != PR_OK) return s;
         if (mixed) {
-            occ = std::min(occ, resident_ctas(update_kernel_for(PR_PREC_DF64), 0));
-            occ_gather = std::min(occ_gather, resident_ctas(gather_kernel_for(PR_PREC_DF64), 0));
+            int og = 1, ou = 1;
+            if ((s = setup_split(PR_PREC_DF64, W, &og, &ou)) != PR_OK) return s;
+            occ = std::min(occ, ou);
+            occ_gather = std::min(occ_gather, og);
         }
     }
     const int budget = sms * occ, gbudget = sms * occ_gather;
@@ -414,7 +466,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         int want = (int)std::lround(budget * share);
         if (split) {
             // update kernel: rows grid-stride
-            j.cta_count = std::max(1, std::min<int>(want, (int)(((int64_t)j.g->n + kBlock - 1) / kBlock)));
+            j.cta_count = std::max(1, std::min<int>(want, (int)(((int64_t)j.g->n * W + kBlock - 1) / kBlock)));
             int gwant = (int)std::lround(gbudget * share);
             j.gcta_count = std::max(1, std::min(gwant, std::max(j.tt->ntiles, 1)));
             total_gctas += j.gcta_count;
@@ -438,7 +490,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         j.off_cp = ar.reserve((size_t)std::max(j.tt->n_chunk_slots, 1) * W * vs_max);
         j.off_cnt = ar.reserve((size_t)std::max(j.tt->n_long, 1) * sizeof(uint32_t));
         j.off_part = ar.reserve((size_t)j.cta_count * W * kPartials * sizeof(double));
-        if (split) j.off_rowsum = ar.reserve((n + kPad) * vs_max);
+        if (split) j.off_rowsum = ar.reserve((n * W + kPad) * vs_max);
         j.off_cols = ar.reserve((size_t)W * sizeof(ColState));
         for (int c : j.cols) j.ntaps += (int)req.cols[c].taps.size();
         j.off_taps = ar.reserve((size_t)std::max(j.ntaps, 1) * sizeof(Tap));
