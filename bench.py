@@ -90,6 +90,12 @@ def make_workload(name, gg, rank=0):
         g = gg.rmat(24, 16, seed=s(24))
         specs = [(0, a, 1e-10, 3, 500) for a in (0.85, 0.95)]
         return [g], specs, "mixed", "rmat-s24 ef16 seed24, alpha {.85,.95}, Linf, tau 1e-10, fp32->df64"
+    if name == "sweep330warm":
+        g = gg.erdos_renyi_10k(seed=s(1))
+        alphas = [round(0.5 + 0.05 * i, 2) for i in range(11)]
+        specs = [(0, a, 10.0 ** -k, nm, 500) for a in alphas for k in range(1, 11) for nm in (1, 2, 3)]
+        return [g], specs, "mixed", ("er-10k, 11 alpha x 10 tau x 3 norms; learned start, fp32->df64 "
+                                     "(the batched mixed-precision warm-started sweep)")
     if name == "road24":
         g = gg.road_grid(4096, 4096, seed=s(7))
         specs = [(0, 0.85, t, nm, 500) for t in (1e-6, 1e-10) for nm in (1, 2, 3)]
@@ -241,7 +247,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
     sptr = int(stream.cuda_stream)
     mlp, learned = None, None
-    if args.workload == "learned":
+    if args.workload in ("learned", "sweep330warm"):
         mlp, _train_keep, learned = train_warm_start(B, gg, torch, sptr)
     init_kw = {"init": "learned", "mlp": mlp} if mlp is not None else {}
     total_edges = sum(g.nnz for g in graphs)
@@ -332,7 +338,7 @@ def run_ours(args, world, rank, local):
         learned["iterations_uniform"] = [x.iters for x in xs_u]
         learned["iterations_learned"] = inst_iters
         learned["iterations_saved_total"] = sum(x.iters for x in xs_u) - sum(inst_iters)
-    sweep = sweep_report(B, torch, dgs, specs, last, outs, sptr) if args.workload == "sweep330" else None
+    sweep = sweep_report(B, torch, dgs, specs, last, outs, sptr) if args.workload.startswith("sweep330") else None
     # ---- plain per-instance GPU solver on the same resident graphs: every
     # instance alone through pr_solve, one launch per iteration and a host read
     # of the stop flag after each (the baseline the batched path is measured against)
@@ -506,7 +512,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22",
-                    choices=["rmat22", "rmat21", "sweep330", "multi64", "rmat24mixed", "learned", "road24"])
+                    choices=["rmat22", "rmat21", "sweep330", "sweep330warm", "multi64", "rmat24mixed", "learned",
+                             "road24"])
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="device loop of the timed solves (host: one launch per iteration)")
     ap.add_argument("--no-e2e", action="store_true")
