@@ -114,6 +114,18 @@ typedef enum pr_group {
     PR_GROUP_SINGLE = 2   /* one column per job (W = 1) */
 } pr_group;
 
+/* How an iteration pass runs on the device. */
+typedef enum pr_kernels {
+    PR_KERNELS_AUTO = 0,   /* default: split passes when a sub-solve's work (in-edges
+                              x column width, summed over its jobs) is at least
+                              4 million, one fused kernel below that (launch-bound
+                              sizes, where one launch per pass is cheaper) */
+    PR_KERNELS_FUSED = 1,  /* one kernel per pass: gathers, row sums, updates,
+                              norms and stopping rules */
+    PR_KERNELS_SPLIT = 2   /* two kernels per pass: a gather kernel that forms the
+                              row sums, then a streaming update kernel */
+} pr_kernels;
+
 typedef struct pr_mlp pr_mlp;   /* learned warm start, see pr_mlp_* below */
 
 typedef struct pr_options {
@@ -141,7 +153,8 @@ typedef struct pr_options {
                                    with PR_ETIMEOUT (the device stops itself;
                                    the context stays usable); 0 (default) =
                                    the largest max_iter + 3 */
-    int32_t reserved[6];        /* zero */
+    int32_t kernels;            /* pr_kernels; default PR_KERNELS_AUTO */
+    int32_t reserved[5];        /* zero */
 } pr_options;
 
 /* Fill *opt with the defaults listed above. */

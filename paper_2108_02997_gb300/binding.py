@@ -28,6 +28,8 @@ PR_INIT_UNIFORM, PR_INIT_USER, PR_INIT_LEARNED = 0, 1, 2
 PR_LOOP_GRAPH, PR_LOOP_HOST = 0, 1
 PR_GROUP_AUTO, PR_GROUP_PACK, PR_GROUP_SINGLE = 0, 1, 2
 GROUPS = {"auto": PR_GROUP_AUTO, "pack": PR_GROUP_PACK, "single": PR_GROUP_SINGLE}
+PR_KERNELS_AUTO, PR_KERNELS_FUSED, PR_KERNELS_SPLIT = 0, 1, 2
+KERNELS = {"auto": PR_KERNELS_AUTO, "fused": PR_KERNELS_FUSED, "split": PR_KERNELS_SPLIT}
 PRECISIONS = {"df64": PR_PREC_DF64, "fp64": PR_PREC_FP64, "mixed": PR_PREC_MIXED, "fp32": PR_PREC_FP32}
 NORMS = {"L1": 1, "L2": 2, "Linf": 3, 1: 1, 2: 2, 3: 3}
 MLP_PARAMS = 64 * 5 + 64 + 64 * 64 + 64 + 64 + 1
@@ -39,7 +41,7 @@ class pr_options(C.Structure):
                 ("switch_tol", C.c_double), ("stream", C.c_void_p),
                 ("share_trajectories", C.c_int32), ("loop", C.c_int32), ("mlp", C.c_void_p),
                 ("err_history", C.c_void_p), ("group", C.c_int32), ("max_passes", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("kernels", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class pr_instance(C.Structure):
@@ -188,8 +190,9 @@ class SolveResult:
 
 
 def _make_options(precision="df64", init=None, loop="graph", stream=None, share=True, switch_tol=1e-6,
-                  outputs_on_device=False, mlp=None, group="auto", max_passes=0):
+                  outputs_on_device=False, mlp=None, group="auto", max_passes=0, kernels="auto"):
     o = default_options()
+    o.kernels = KERNELS[kernels] if isinstance(kernels, str) else int(kernels)
     o.group = GROUPS[group] if isinstance(group, str) else int(group)
     o.max_passes = int(max_passes)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -213,7 +216,7 @@ def _make_options(precision="df64", init=None, loop="graph", stream=None, share=
 
 def pr_solve(g: Graph, alpha: float, tol: float, norm=PR_NORM_L1, max_iter: int = 500, *,
              precision="df64", init=None, out=None, loop="graph", stream=None, history=False,
-             switch_tol=1e-6, mlp=None) -> SolveResult:
+             switch_tol=1e-6, mlp=None, kernels="auto") -> SolveResult:
     """Solve one instance. ``out``: numpy array (host) or torch CUDA tensor
     (device) of n float64; allocated as numpy when omitted."""
     if out is None:
@@ -221,7 +224,7 @@ def pr_solve(g: Graph, alpha: float, tol: float, norm=PR_NORM_L1, max_iter: int 
     addr, dev = _ptr_of(out)
     if stream is None and dev:
         stream = current_stream_ptr()
-    o, keep = _make_options(precision, init, loop, stream, True, switch_tol, dev, mlp)
+    o, keep = _make_options(precision, init, loop, stream, True, switch_tol, dev, mlp, kernels=kernels)
     hist = np.zeros((max_iter, 3), np.float64) if history else None
     if hist is not None:
         o.err_history = hist.ctypes.data
@@ -251,7 +254,8 @@ class Instance:
 
 
 def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=None, share=True,
-                   switch_tol=1e-6, outputs_on_device=False, mlp=None, check=True, group="auto", max_passes=0):
+                   switch_tol=1e-6, outputs_on_device=False, mlp=None, check=True, group="auto", max_passes=0,
+                   kernels="auto"):
     """Solve many instances together. Fills ``out`` (allocated as numpy, or as
     torch CUDA tensors when ``outputs_on_device``), ``iters``, ``err``,
     ``converged`` and ``status`` of every :class:`Instance`; returns the
@@ -283,7 +287,7 @@ def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=N
     if stream is None and any_dev:
         stream = current_stream_ptr()
     o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, outputs_on_device, mlp, group,
-                             max_passes)
+                             max_passes, kernels)
     if any(x.init is not None for x in insts) and o.init == PR_INIT_UNIFORM:
         o.init = PR_INIT_USER
     st = lib().pr_solve_batch(arr, len(insts), C.byref(o))

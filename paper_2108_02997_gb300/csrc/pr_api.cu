@@ -84,6 +84,7 @@ pr_status check_options(const pr_options &o) {
     if (o.loop != PR_LOOP_GRAPH && o.loop != PR_LOOP_HOST) return pr_fail(PR_EINVAL, "unknown loop mode");
     if (o.group < PR_GROUP_AUTO || o.group > PR_GROUP_SINGLE) return pr_fail(PR_EINVAL, "unknown group mode");
     if (o.max_passes < 0) return pr_fail(PR_EINVAL, "max_passes must be >= 0");
+    if (o.kernels < PR_KERNELS_AUTO || o.kernels > PR_KERNELS_SPLIT) return pr_fail(PR_EINVAL, "unknown kernels mode");
     if (o.precision == PR_PREC_MIXED && !(o.switch_tol > 0.0 && std::isfinite(o.switch_tol)))
         return pr_fail(PR_EINVAL, "switch_tol must be positive and finite");
     if (o.init == PR_INIT_LEARNED && !pr_mlp_valid(o.mlp)) return pr_fail(PR_EINVAL, "PR_INIT_LEARNED needs a live pr_mlp");
@@ -173,6 +174,7 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
     req.switch_tol = opt.switch_tol;
     req.stream = st;
     req.max_passes = opt.max_passes;
+    req.kernels = opt.kernels;
     std::map<std::tuple<const pr_graph *, uint64_t, const double *>, int> col_of;
     std::vector<std::vector<std::pair<int, int>>> col_taps;   // (instance, tap index)
     for (int i : ok) {
@@ -234,6 +236,7 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
             sub.switch_tol = req.switch_tol;
             sub.stream = req.stream;
             sub.max_passes = req.max_passes;
+            sub.kernels = req.kernels;
             std::vector<int> cmap;   // sub-request column -> request column
             for (const auto &jc : sp.jobs) {
                 std::vector<int> local;

@@ -88,6 +88,7 @@ struct SolveRequest {
     // 32 each; empty = the columns of each graph packed 32 at a time.
     std::vector<std::vector<int>> jobs;
     int max_passes = 0;     // 0: the largest max_iter + 3
+    int kernels = PR_KERNELS_AUTO;
     SolveStats stats;       // out
 };
 

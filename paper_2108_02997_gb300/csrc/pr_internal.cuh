@@ -69,6 +69,9 @@ constexpr bool kTileUpdate = PR_TILE_UPDATE != 0;
 // (fewer registers, more resident warps) and a streaming update kernel (new
 // ranks, contributions, norms, stopping rules).
 constexpr bool kSplitPasses = PR_SPLIT_PASSES != 0;
+// PR_KERNELS_AUTO splits passes from this many in-edge columns per sub-solve
+// (smaller solves are launch-bound and one launch per pass is cheaper).
+constexpr double kSplitMinWork = 4.0e6;
 constexpr int kGatherMinBlocks = PR_GATHER_MIN_BLOCKS;
 constexpr int kUpdateMinBlocks = PR_UPDATE_MIN_BLOCKS;
 #ifndef PR_VEC_GATHER_MIN_BLOCKS

@@ -261,10 +261,9 @@ extern "C" pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, dou
 namespace {
 
 // One phase of a solve in one value type: init pass + loop of iteration passes.
-pr_status run_phase(int prec, int W, std::vector<HostJob> &jobs, Arena &ar, size_t off_jobs, size_t off_glob,
-                    size_t off_ctajob, int total_ctas, size_t off_gctajob, int total_gctas, int pass_cap, int loop,
-                    cudaStream_t st, LoopStats &stats) {
-    const bool split = kSplitPasses;
+pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Arena &ar, size_t off_jobs,
+                    size_t off_glob, size_t off_ctajob, int total_ctas, size_t off_gctajob, int total_gctas,
+                    int pass_cap, int loop, cudaStream_t st, LoopStats &stats) {
     // split passes: the pass is the gather kernel then the update kernel
     void *kiter = split ? update_kernel_for(prec, W) : pr_iter_kernel_for(prec, W);
     void *kgather = split ? gather_kernel_for(prec, W) : nullptr;
@@ -440,7 +439,12 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         if ((s = pr_kernel_setup(PR_PREC_DF64, W, &occ2)) != PR_OK) return s;
         occ = std::min(occ, occ2);
     }
-    const bool split = kSplitPasses;
+    // split passes or one fused kernel per pass (PR_KERNELS_AUTO: split from
+    // kSplitMinWork in-edge columns on)
+    double edge_cols = 0.0;
+    for (auto &j : jobs) edge_cols += (double)j.g->nnz * W;
+    const bool split = req.kernels == PR_KERNELS_SPLIT ||
+                       (req.kernels == PR_KERNELS_AUTO && kSplitPasses && edge_cols >= kSplitMinWork);
     int occ_gather = 1;
     if (split) {
         // split passes: the update kernel's grid carries the pass bookkeeping,
@@ -615,8 +619,8 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     PR_CUDA(cudaMemcpyAsync(ar.at<int32_t>(off_gctajob), gctajob.data(), gctajob.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     const int pass_cap = req.max_passes > 0 ? req.max_passes : max_iter_all + 3;
     // ---- phase 1 (or the only phase)
-    s = run_phase(prec1, W, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, off_gctajob, total_gctas, pass_cap,
-                  req.loop, st, stats);
+    s = run_phase(prec1, W, split, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, off_gctajob, total_gctas,
+                  pass_cap, req.loop, st, stats);
     if (s != PR_OK) return s;
     // ---- mixed precision: refinement phase in DF64 from the FP32 iterates
     if (mixed) {
@@ -655,8 +659,8 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         if (any) {
             PR_CUDA(cudaMemcpyAsync(ar.at<JobDev>(off_jobs), hjobs.data(), hjobs.size() * sizeof(JobDev),
                                     cudaMemcpyHostToDevice, st));
-            s = run_phase(PR_PREC_DF64, W, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, off_gctajob, total_gctas,
-                          pass_cap, req.loop, st, stats);
+            s = run_phase(PR_PREC_DF64, W, split, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, off_gctajob,
+                          total_gctas, pass_cap, req.loop, st, stats);
             if (s != PR_OK) return s;
         }
     }

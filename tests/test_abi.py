@@ -95,6 +95,9 @@ def test_solve_rejects_bad_handles_and_arguments(L):
     o = binding.default_options()
     o.group = 7
     assert L.pr_solve_batch(None, 0, C.byref(o)) == 1 and b"group" in L.pr_last_error()
+    o = binding.default_options()
+    o.kernels = 3
+    assert L.pr_solve_batch(None, 0, C.byref(o)) == 1 and b"kernels" in L.pr_last_error()
     assert L.pr_solve_batch(None, -1, None) == 1
 
 

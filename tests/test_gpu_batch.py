@@ -167,3 +167,19 @@ def test_graph_tune_measures_and_caches(B, gg):
             assert B.pr_graph_tune(dg2, "df64", 4)[:3] == t1[:3]
         with pytest.raises(B.PageRankError):
             B.pr_graph_tune(dg, "df64", 3)
+
+
+@pytest.mark.parametrize("kernels", ["fused", "split"])
+@pytest.mark.parametrize("width", [2, 4, 8, 16])
+def test_multi_column_kernels_match_oracle(B, orc, gg, kernels, width):
+    """One job of `width` columns (distinct alphas, PR_GROUP_PACK) with one
+    fused kernel per pass or split passes, df64 and fp64."""
+    g = gg.rmat(15, 16, seed=47)
+    alphas = [0.5 + 0.45 * k / max(width - 1, 1) for k in range(width)]
+    refs = {a: orc.pagerank(g, a, 1e-10, 1, 500, history=True, threads=orc.default_threads()) for a in alphas}
+    with B.Graph.from_csr(g) as dg:
+        for prec in ("df64", "fp64"):
+            insts = [B.Instance(dg, a, 1e-10, 1, 500) for a in alphas]
+            B.pr_solve_batch(insts, group="pack", kernels=kernels, precision=prec)
+            for a, x in zip(alphas, insts):
+                assert_fp64_parity(x.out, x.iters, x.err, refs[a], 1e-10, 1, f"W {width} {kernels} {prec} alpha {a}")

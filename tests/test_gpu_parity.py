@@ -49,10 +49,11 @@ def adversarial(gg):
     return out
 
 
+@pytest.mark.parametrize("kernels", ["fused", "split"])
 @pytest.mark.parametrize("precision", ["df64", "fp64"])
-def test_er10k_plain_matches_oracle(B, orc, er10k, er10k_dev, precision):
+def test_er10k_plain_matches_oracle(B, orc, er10k, er10k_dev, precision, kernels):
     ref = orc.pagerank(er10k, 0.85, 1e-10, 1, 500, history=True)
-    res = B.pr_solve(er10k_dev, 0.85, 1e-10, 1, 500, precision=precision, history=True)
+    res = B.pr_solve(er10k_dev, 0.85, 1e-10, 1, 500, precision=precision, history=True, kernels=kernels)
     assert_fp64_parity(res.ranks, res.iters, res.err, ref, 1e-10, 1, f"er10k {precision}")
     assert res.converged == ref.converged
     # per-iteration norms follow the oracle's within the bound that the rank
@@ -77,14 +78,16 @@ def test_er10k_alpha_extremes(B, orc, er10k, er10k_dev, alpha):
     assert_fp64_parity(res.ranks, res.iters, res.err, ref, 1e-9, 1, f"alpha {alpha}")
 
 
-def test_adversarial_graphs(B, orc, gg):
+@pytest.mark.parametrize("kernels", ["fused", "split"])
+def test_adversarial_graphs(B, orc, gg, kernels):
     for name, g in adversarial(gg).items():
         dg = B.Graph.from_csr(g)
         for norm in (1, 3):
             for prec in ("df64", "fp64"):
                 ref = orc.pagerank(g, 0.85, 1e-10, norm, 500, history=True)
-                res = B.pr_solve(dg, 0.85, 1e-10, norm, 500, precision=prec)
-                assert_fp64_parity(res.ranks, res.iters, res.err, ref, 1e-10, norm, f"{name} {prec} norm {norm}")
+                res = B.pr_solve(dg, 0.85, 1e-10, norm, 500, precision=prec, kernels=kernels)
+                assert_fp64_parity(res.ranks, res.iters, res.err, ref, 1e-10, norm,
+                                   f"{name} {prec} norm {norm} {kernels}")
         dg.close()
 
 
@@ -124,14 +127,15 @@ def test_device_buffers(B, orc, er10k, er10k_dev):
     assert_fp64_parity(out.cpu().numpy(), res.iters, res.err, ref, 1e-10, 1, "device buffers")
 
 
+@pytest.mark.parametrize("kernels", ["fused", "split"])
 @pytest.mark.parametrize("scale", [14, 17])
-def test_rmat_matches_oracle(B, orc, gg, scale):
+def test_rmat_matches_oracle(B, orc, gg, scale, kernels):
     g = gg.rmat(scale, 16, seed=scale)
     dg = B.Graph.from_csr(g)
     for norm, tau in ((1, 1e-10), (2, 1e-8), (3, 1e-10)):
         ref = orc.pagerank(g, 0.85, tau, norm, 500, history=True, threads=orc.default_threads())
-        res = B.pr_solve(dg, 0.85, tau, norm, 500)
-        assert_fp64_parity(res.ranks, res.iters, res.err, ref, tau, norm, f"rmat{scale} norm {norm}")
+        res = B.pr_solve(dg, 0.85, tau, norm, 500, kernels=kernels)
+        assert_fp64_parity(res.ranks, res.iters, res.err, ref, tau, norm, f"rmat{scale} norm {norm} {kernels}")
     dg.close()
 
 
