@@ -71,7 +71,7 @@ constexpr bool kTileUpdate = PR_TILE_UPDATE != 0;
 constexpr bool kSplitPasses = PR_SPLIT_PASSES != 0;
 // PR_KERNELS_AUTO splits passes from this many in-edge columns per sub-solve
 // (smaller solves are launch-bound and one launch per pass is cheaper).
-constexpr double kSplitMinWork = 4.0e6;
+constexpr double kSplitMinWork = 16.0e6;
 constexpr int kGatherMinBlocks = PR_GATHER_MIN_BLOCKS;
 constexpr int kUpdateMinBlocks = PR_UPDATE_MIN_BLOCKS;
 #ifndef PR_VEC_GATHER_MIN_BLOCKS
@@ -214,7 +214,7 @@ struct GlobalDev {
     int32_t error;            // nonzero: a device-side check failed
     unsigned long long cond;  // cudaGraphConditionalHandle (0 in host-loop mode)
     uint32_t body_count;      // iteration launches started (independent loop guard)
-    uint32_t pad;
+    uint32_t alive_jobs;      // jobs still alive after the current pass (counted by their finalizers)
 };
 
 // Error codes a kernel can leave in GlobalDev::error.

@@ -237,79 +237,99 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
         }
         __syncthreads();
     }
-    // ---- column decisions (one thread per column)
-    if (tid < job.ncols) {
-        ColState &cs = job.cols[tid];
-        const double l1 = s_fin[tid * kPartials + 0];
-        const double l2 = sqrt(s_fin[tid * kPartials + 1]);
-        const double li = s_fin[tid * kPartials + 2];
-        const double D = s_fin[tid * kPartials + 3];
-        const double S = s_fin[tid * kPartials + 4];
+    // ---- column decisions: one warp per column, its lanes over the column's
+    // stopping rules (taps, in order)
+    __shared__ int s_colalive[W];
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int c = warp; c < job.ncols; c += kWarps) {
+        ColState &cs = job.cols[c];
+        const double l1 = s_fin[c * kPartials + 0];
+        const double l2 = sqrt(s_fin[c * kPartials + 1]);
+        const double li = s_fin[c * kPartials + 2];
+        const double D = s_fin[c * kPartials + 3];
+        const double S = s_fin[c * kPartials + 4];
         const double Nn = (double)job.n;
+        int col_alive = 0;
         if (mode == kPassInit) {
-            cs.c0 = (1.0 - cs.alpha) / Nn + cs.alpha * D / Nn;
-            store_raw<V>(cs.v_c0, N::from_double(cs.c0));
-            cs.last_sum = S;
-            cs.copy_dst = nullptr;
-        } else if (cs.active) {
-            const int it = ++cs.iters;
-            cs.cur ^= 1;
-            cs.last_err[0] = l1; cs.last_err[1] = l2; cs.last_err[2] = li;
-            cs.last_sum = S;
-            if (cs.hist && it <= cs.hist_cap) {
-                cs.hist[3 * (it - 1) + 0] = l1;
-                cs.hist[3 * (it - 1) + 1] = l2;
-                cs.hist[3 * (it - 1) + 2] = li;
+            col_alive = cs.active;
+            if (lane == 0) {
+                cs.c0 = (1.0 - cs.alpha) / Nn + cs.alpha * D / Nn;
+                store_raw<V>(cs.v_c0, N::from_double(cs.c0));
+                cs.last_sum = S;
+                cs.copy_dst = nullptr;
             }
+        } else if (cs.active) {
+            const int it = cs.iters + 1;
             const double errs[3] = {l1, l2, li};
+            const int tb = cs.tap_begin, te = cs.tap_end;
             int primary = -1;
             bool pending = false;
-            for (int q = cs.tap_begin; q < cs.tap_end; q++) {
-                Tap &tp = job.taps[q];
-                if (tp.fired) continue;
-                const double e = errs[tp.norm - 1];
-                if (e < tp.tau || it >= tp.max_iter) {
-                    tp.fired = 1;
-                    tp.iters = it;
-                    tp.err = e;
-                    tp.err_l1 = l1;
-                    tp.converged = e < tp.tau;
-                    tp.alias_of = primary;
-                    if (primary < 0) primary = q;
-                } else {
-                    pending = true;
+            for (int q0 = tb; q0 < te; q0 += 32) {
+                const int q = q0 + lane;
+                bool fires = false, pend = false;
+                double e = 0.0;
+                if (q < te && !job.taps[q].fired) {
+                    const Tap &tp = job.taps[q];
+                    e = errs[tp.norm - 1];
+                    if (e < tp.tau || it >= tp.max_iter) fires = true;
+                    else pend = true;
+                }
+                const unsigned int fm = __ballot_sync(0xffffffffu, fires);
+                if (__any_sync(0xffffffffu, pend)) pending = true;
+                if (fm) {
+                    if (primary < 0) primary = q0 + __ffs(fm) - 1;
+                    if (fires) {
+                        Tap &tp = job.taps[q];
+                        tp.fired = 1;
+                        tp.iters = it;
+                        tp.err = e;
+                        tp.err_l1 = l1;
+                        tp.converged = e < tp.tau;
+                        tp.alias_of = q == primary ? -1 : primary;
+                    }
                 }
             }
-            cs.copy_dst = primary >= 0 ? job.taps[primary].out : nullptr;
-            if (!pending) cs.active = 0;
-            if (cs.switch_norm && !cs.switched && errs[cs.switch_norm - 1] <= cs.switch_tol) {
-                cs.switched = 1;
-                cs.active = 0;   // hand over to the refinement phase
+            bool active = pending;
+            if (cs.switch_norm && !cs.switched && errs[cs.switch_norm - 1] <= cs.switch_tol) active = false;
+            double *copy = primary >= 0 ? job.taps[primary].out : nullptr;
+            col_alive = active || copy != nullptr;
+            __syncwarp();
+            if (lane == 0) {
+                cs.iters = it;
+                cs.cur ^= 1;
+                cs.last_err[0] = l1; cs.last_err[1] = l2; cs.last_err[2] = li;
+                cs.last_sum = S;
+                if (cs.hist && it <= cs.hist_cap) {
+                    cs.hist[3 * (it - 1) + 0] = l1;
+                    cs.hist[3 * (it - 1) + 1] = l2;
+                    cs.hist[3 * (it - 1) + 2] = li;
+                }
+                cs.copy_dst = copy;
+                if (cs.switch_norm && !cs.switched && errs[cs.switch_norm - 1] <= cs.switch_tol)
+                    cs.switched = 1;   // hand over to the refinement phase
+                cs.active = active ? 1 : 0;
+                cs.c0 = (1.0 - cs.alpha) / Nn + cs.alpha * D / Nn;
+                store_raw<V>(cs.v_c0, N::from_double(cs.c0));
             }
-            cs.c0 = (1.0 - cs.alpha) / Nn + cs.alpha * D / Nn;
-            store_raw<V>(cs.v_c0, N::from_double(cs.c0));
         } else {
-            cs.copy_dst = nullptr;
+            if (lane == 0) cs.copy_dst = nullptr;
         }
+        if (lane == 0) s_colalive[c] = col_alive;
     }
     __syncthreads();
     if (tid == 0) {
         int alive = 0;
-        for (int c = 0; c < job.ncols; c++) {
-            const volatile ColState &cs = job.cols[c];
-            if (cs.active || cs.copy_dst) alive = 1;
-        }
+        for (int c = 0; c < job.ncols; c++) alive |= s_colalive[c];
         job.alive = alive;
         if (mode == kPassIterate) job.cur ^= 1;   // parity shared by the columns still active
         job.arrive = 0;
+        if (alive) atomicAdd(&glob->alive_jobs, 1u);
         __threadfence();
         unsigned int old = atomicAdd(&glob->jobs_arrive, 1u);
         if (old == (unsigned int)(glob->njobs - 1)) {
             __threadfence();
             glob->jobs_arrive = 0;
-            int any = 0;
-            for (int q = 0; q < glob->njobs; q++)
-                if (*(volatile int32_t *)&jobs[q].alive) any = 1;
+            int any = atomicExch(&glob->alive_jobs, 0u) > 0u;
             if (mode == kPassIterate) {
                 glob->pass += 1;
                 if (*(volatile int32_t *)&glob->error) any = 0;
