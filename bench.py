@@ -211,8 +211,20 @@ def sweep_report(B, torch, dgs, specs, last, outs, sptr):
     for nm, name in ((1, "L1"), (2, "L2"), (3, "Linf")):
         hit = [t for (gi, a, t, n2, mi), x in zip(specs, xs) if n2 == nm and a < 1.0 and not x.converged]
         stall[name] = max(hit) if hit else None
+    # alpha continuation (tau 1e-10, L1, df64): each alpha starts from the
+    # previous alpha's ranks instead of 1/N
+    uni, cont, prev = [], [], None
+    for a in alphas:
+        r_u = B.pr_solve(dgs[0], a, 1e-10, 1, 500, out=torch.empty(dgs[0].n, dtype=torch.float64, device="cuda"))
+        uni.append(r_u.iters)
+        out = torch.empty(dgs[0].n, dtype=torch.float64, device="cuda")
+        r_c = B.pr_solve(dgs[0], a, 1e-10, 1, 500, out=out, init=prev) if prev is not None else r_u
+        cont.append(r_c.iters)
+        prev = out if prev is not None else r_u.ranks
     return {"alpha": alphas, "l1_vs_alpha_085": l1, "iterations_vs_alpha_085": ratio,
-            "fp32_largest_tau_hitting_cap": stall}
+            "fp32_largest_tau_hitting_cap": stall,
+            "continuation": {"iterations_uniform": uni, "iterations_from_previous_alpha": cont,
+                             "saved": sum(uni) - sum(cont)}}
 
 
 def dist_init(n_gpus):

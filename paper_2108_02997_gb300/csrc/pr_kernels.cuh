@@ -51,6 +51,14 @@ template <> __device__ __forceinline__ df64 ld_cg_v<df64>(const df64 *p) {
     return {f.x, f.y};
 }
 
+// An in-edge index of the one-column kernels (read once per pass: with
+// kStreamIndex, marked evict-first so that it does not displace contributions
+// from L1).
+__device__ __forceinline__ int32_t ld_idx(const int32_t *p) {
+    if constexpr (kStreamIndex) return __ldcs(p);
+    else return *p;
+}
+
 // A work tile's descriptor: two 16-byte loads.
 __device__ __forceinline__ Tile load_tile(const Tile *p) {
     const int4 a = __ldg(reinterpret_cast<const int4 *>(p));
@@ -457,6 +465,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
     // several columns: the active columns read the job's shared buffer parity
     const unsigned int act_mask = __ballot_sync(0xffffffffu, cv.active);
     const V *c_all = reinterpret_cast<const V *>(job.contrib[job.cur]);
+    auto gather1 = [&](int32_t u) -> V { return cv.c_prev[(size_t)u * W + col]; };
 
     if (work) {
         const int wstride = cta_count * kWarps;
@@ -544,7 +553,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
 #pragma unroll
                 for (int k = 0; k < PER; k++) {
                     const int idx = lane + 32 * k;
-                    u[k] = (cv.active && idx < ne * W) ? src[T.e0 + idx / W] : -1;
+                    u[k] = (cv.active && idx < ne * W) ? ld_idx(src + T.e0 + idx / W) : -1;
                 }
                 for (int i = lane; i <= nr; i += 32) s_off[warp][i] = off[T.r0 + i] - T.e0;
                 // element i of the rows belongs to column i % W == lane % W
@@ -556,7 +565,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                 {
                     V x[PER];
 #pragma unroll
-                    for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? cv.c_prev[(size_t)u[k] * W + col] : N::zero();
+                    for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
 #pragma unroll
                     for (int k = 0; k < PER; k++)
                         if (u[k] >= 0) s_vals[warp][lane + 32 * k] = x[k];
@@ -649,17 +658,17 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
 #pragma unroll
                     for (int k = 0; k < PER; k++) {
                         const int idx = lane + 32 * k;
-                        u[k] = idx < nv ? src[T.e0 + idx] : -1;
+                        u[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
                     }
                     for (int base = lane; base < nv; base += VT) {
                         V x[PER];
 #pragma unroll
-                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? cv.c_prev[u[k]] : N::zero();
+                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
                         int32_t un[PER];
 #pragma unroll
                         for (int k = 0; k < PER; k++) {
                             const int idx = base + VT + 32 * k;
-                            un[k] = idx < nv ? src[T.e0 + idx] : -1;
+                            un[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
                         }
 #pragma unroll
                         for (int k = 0; k < PER; k++)
@@ -677,7 +686,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                         }
                         V x[PER];
 #pragma unroll
-                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? cv.c_prev[(size_t)u[k] * W + col] : N::zero();
+                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
 #pragma unroll
                         for (int k = 0; k < PER; k++)
                             if (u[k] >= 0) sum.add(x[k]);
