@@ -150,10 +150,15 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # sampling is live before the timed region starts
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.005)
+            self.lines.clear()
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -350,6 +355,15 @@ def run_ours(args, world, rank, local):
         learned["iterations_uniform"] = [x.iters for x in xs_u]
         learned["iterations_learned"] = inst_iters
         learned["iterations_saved_total"] = sum(x.iters for x in xs_u) - sum(inst_iters)
+        if precision != "df64":
+            # the same comparison with df64 throughout (no FP32 phase)
+            its = {}
+            for mode, kw in (("uniform", {}), ("learned", init_kw)):
+                xs_d = [B.Instance(dgs[gi], a, t, nm, mi, out=outs[k]) for k, (gi, a, t, nm, mi) in enumerate(specs)]
+                B.pr_solve_batch(xs_d, precision="df64", outputs_on_device=True, stream=sptr, **kw)
+                its[mode] = [x.iters for x in xs_d]
+            learned["df64"] = {"iterations_uniform": its["uniform"], "iterations_learned": its["learned"],
+                               "iterations_saved_total": sum(its["uniform"]) - sum(its["learned"])}
     sweep = sweep_report(B, torch, dgs, specs, last, outs, sptr) if args.workload.startswith("sweep330") else None
     # ---- plain per-instance GPU solver on the same resident graphs: every
     # instance alone through pr_solve, one launch per iteration and a host read
