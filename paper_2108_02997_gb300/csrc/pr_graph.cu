@@ -12,7 +12,10 @@
 //     low ids, so their cache lines are shared instead of scattered.
 // Rank vectors cross the ABI in caller order; the kernels map through perm.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <system_error>
+#include <thread>
 #include <new>
 
 #include "pr_internal.cuh"
@@ -88,45 +91,98 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     }
     const int TE = tile_edges(W), TR = tile_rows(W), CH = chunk_edges(W);
     const int max_es = 32;
-    std::vector<Tile> tiles;
-    std::vector<int32_t> slot_base;
-    int32_t n_chunk_slots = 0;
-    double work = 0.0;
     const std::vector<int32_t> &off = g->h_off;
-    for (const ClassRange &cr : g->classes) {
-        if (cr.end <= cr.begin) continue;
+    // Work items: slices of at most kSliceRows rows of one class, tiled
+    // independently (a rows tile never spans two slices; a row's sum does not
+    // depend on the tile it sits in) on up to 16 host threads, then merged in
+    // order with the chunk slots renumbered.
+    constexpr int32_t kSliceRows = 1 << 18;
+    struct Slice {
+        const ClassRange *cr;
+        int32_t r0, r1;
+        std::vector<Tile> tiles;
+        std::vector<int32_t> slot_base;   // local chunk-slot offsets
+        int32_t n_chunk_slots = 0;
+        double work = 0.0;
+    };
+    std::vector<Slice> slices;
+    for (const ClassRange &cr : g->classes)
+        for (int32_t r = cr.begin; r < cr.end; r += kSliceRows) {
+            Slice sl;
+            sl.cr = &cr;
+            sl.r0 = r;
+            sl.r1 = (int32_t)std::min<int64_t>((int64_t)r + kSliceRows, cr.end);
+            slices.push_back(std::move(sl));
+        }
+    auto build_slice = [&](Slice &sl) {
+        const ClassRange &cr = *sl.cr;
         if (cr.max_deg > TE) {
-            for (int32_t v = cr.begin; v < cr.end; v++) {
+            for (int32_t v = sl.r0; v < sl.r1; v++) {
                 int32_t e0 = off[v], e1 = off[v + 1];
                 int32_t deg = e1 - e0;
                 int32_t nch = std::max<int32_t>(1, (deg + CH - 1) / CH);
                 int32_t slot = -1;
                 if (nch > 1) {
-                    slot = (int32_t)slot_base.size();
-                    slot_base.push_back(n_chunk_slots);
-                    n_chunk_slots += nch;
+                    slot = (int32_t)sl.slot_base.size();
+                    sl.slot_base.push_back(sl.n_chunk_slots);
+                    sl.n_chunk_slots += nch;
                 }
                 for (int32_t k = 0; k < nch; k++) {
                     int32_t a = e0 + k * CH, b = std::min(e1, a + CH);
-                    tiles.push_back({v, v + 1, a, b, -1, slot, k, nch});
+                    sl.tiles.push_back({v, v + 1, a, b, -1, slot, k, nch});
                 }
-                work += (double)deg * W + W * 4.0;
+                sl.work += (double)deg * W + W * 4.0;
             }
-            continue;
+            return;
         }
         int es = 1;
         while (es < max_es && es * 4 < cr.max_deg) es <<= 1;
         int glog = 0;
         while ((1 << glog) < es) glog++;
-        int32_t r = cr.begin;
-        while (r < cr.end) {
+        int32_t r = sl.r0;
+        while (r < sl.r1) {
             int32_t r1 = r;
-            while (r1 < cr.end && r1 - r < TR && off[r1 + 1] - off[r] <= TE) r1++;
+            while (r1 < sl.r1 && r1 - r < TR && off[r1 + 1] - off[r] <= TE) r1++;
             if (r1 == r) r1 = r + 1;   // cannot happen (deg <= TE), kept for safety
-            tiles.push_back({r, r1, off[r], off[r1], glog, -1, 0, 0});
-            work += (double)(off[r1] - off[r]) * W + (double)(r1 - r) * W * 4.0;
+            sl.tiles.push_back({r, r1, off[r], off[r1], glog, -1, 0, 0});
+            sl.work += (double)(off[r1] - off[r]) * W + (double)(r1 - r) * W * 4.0;
             r = r1;
         }
+    };
+    {
+        const unsigned int hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        const size_t nthreads = std::min<size_t>(hw, slices.size());
+        std::atomic<size_t> next{0};
+        auto worker = [&]() {
+            for (size_t i = next++; i < slices.size(); i = next++) build_slice(slices[i]);
+        };
+        std::vector<std::thread> pool;
+        try {
+            for (size_t k = 1; k < nthreads; k++) pool.emplace_back(worker);
+        } catch (const std::system_error &) {
+            // fewer threads: the calling thread does the rest
+        }
+        worker();
+        for (auto &th : pool) th.join();
+    }
+    std::vector<Tile> tiles;
+    std::vector<int32_t> slot_base;
+    int32_t n_chunk_slots = 0;
+    double work = 0.0;
+    {
+        size_t nt_total = 0;
+        for (auto &sl : slices) nt_total += sl.tiles.size();
+        tiles.reserve(nt_total);
+    }
+    for (auto &sl : slices) {
+        const int32_t slot_shift = (int32_t)slot_base.size();
+        for (Tile t : sl.tiles) {
+            if (t.slot >= 0) t.slot += slot_shift;
+            tiles.push_back(t);
+        }
+        for (int32_t b : sl.slot_base) slot_base.push_back(b + n_chunk_slots);
+        n_chunk_slots += sl.n_chunk_slots;
+        work += sl.work;
     }
     TileTable nt;
     nt.W = W;
@@ -172,7 +228,18 @@ __global__ void check_outdeg_kernel(const int32_t *__restrict__ count, const int
         if (count[v] != outdeg[v]) atomicMin(bad_vertex, (unsigned long long)v);
 }
 // Relabelled rows: row i of the new CSR is caller row perm[i], its sources
-// mapped through inv. One warp per row.
+// mapped through inv. One warp per row (rows of 32 or more in-edges, which the
+// relabelling puts first) or one thread per row (the rest, from row i0 on).
+__global__ void remap_short_rows_kernel(const int32_t *__restrict__ old_off, const int32_t *__restrict__ old_src,
+                                        const int32_t *__restrict__ new_off, const int32_t *__restrict__ perm,
+                                        const int32_t *__restrict__ inv, int32_t i0, int32_t n,
+                                        int32_t *__restrict__ new_src) {
+    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = perm[i];
+        const int32_t a = old_off[v], len = old_off[v + 1] - a, o = new_off[i];
+        for (int32_t k = 0; k < len; k++) new_src[o + k] = inv[old_src[a + k]];
+    }
+}
 __global__ void remap_rows_kernel(const int32_t *__restrict__ old_off, const int32_t *__restrict__ old_src,
                                   const int32_t *__restrict__ new_off, const int32_t *__restrict__ perm,
                                   const int32_t *__restrict__ inv, int32_t n, int32_t *__restrict__ new_src) {
@@ -399,13 +466,41 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     // ---- O(n) checks on the host
     if (in_offsets[0] != 0) return pr_fail(PR_EINVAL, "in_offsets[0] must be 0");
     if ((int64_t)in_offsets[n] != nnz) return pr_fail(PR_EINVAL, "in_offsets[n] must equal nnz");
+    // (split over host threads for large n; the first offending row is reported)
     int64_t deg_sum = 0;
     int32_t n_dangling = 0;
-    for (int32_t v = 0; v < n; v++) {
-        if (in_offsets[v + 1] < in_offsets[v]) return pr_fail(PR_EINVAL, "in_offsets is not non-decreasing at row " + std::to_string(v));
-        if (out_degree[v] < 0) return pr_fail(PR_EINVAL, "out_degree[" + std::to_string(v) + "] is negative");
-        deg_sum += out_degree[v];
-        if (out_degree[v] == 0) n_dangling++;
+    {
+        struct Part { int64_t sum = 0; int32_t dangling = 0, bad_off = INT32_MAX, bad_od = INT32_MAX; };
+        const int nthreads = n >= (1 << 20) ? (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())) : 1;
+        std::vector<Part> parts((size_t)nthreads);
+        auto scan = [&](int k) {
+            const int32_t a = (int32_t)((int64_t)n * k / nthreads), b = (int32_t)((int64_t)n * (k + 1) / nthreads);
+            Part &p = parts[(size_t)k];
+            for (int32_t v = a; v < b; v++) {
+                if (in_offsets[v + 1] < in_offsets[v] && p.bad_off == INT32_MAX) p.bad_off = v;
+                if (out_degree[v] < 0 && p.bad_od == INT32_MAX) p.bad_od = v;
+                p.sum += out_degree[v];
+                p.dangling += out_degree[v] == 0;
+            }
+        };
+        std::vector<std::thread> pool;
+        try {
+            for (int k = 1; k < nthreads; k++) pool.emplace_back(scan, k);
+        } catch (const std::system_error &) {
+            for (int k = 1 + (int)pool.size(); k < nthreads; k++) scan(k);
+        }
+        scan(0);
+        for (auto &th : pool) th.join();
+        int32_t bad_off = INT32_MAX, bad_od = INT32_MAX;
+        for (const Part &p : parts) {
+            deg_sum += p.sum;
+            n_dangling += p.dangling;
+            bad_off = std::min(bad_off, p.bad_off);
+            bad_od = std::min(bad_od, p.bad_od);
+        }
+        if (bad_off != INT32_MAX && bad_off <= bad_od)
+            return pr_fail(PR_EINVAL, "in_offsets is not non-decreasing at row " + std::to_string(bad_off));
+        if (bad_od != INT32_MAX) return pr_fail(PR_EINVAL, "out_degree[" + std::to_string(bad_od) + "] is negative");
     }
     if (deg_sum != nnz) return pr_fail(PR_EINVAL, "out_degree does not sum to nnz (it must match the edges in in_sources)");
     // ---- caller arrays on the device, sources validated there
@@ -510,8 +605,14 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     if (e == cudaSuccess) e = cudaMemcpy(h_starts, d_starts.p, sizeof(h_starts), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(h_cmax, d_cmax.p, sizeof(h_cmax), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && nnz > 0) {
-        remap_rows_kernel<<<blocks_for((int64_t)n * 32, 256), 256>>>(old_off, static_cast<const int32_t *>(d_old_src.p),
-                                                                     g->d_off, g->d_perm, g->d_inv, n, g->d_src);
+        // rows with 32 or more in-edges (classes 6 and up) come first in the new order
+        const int32_t i_short = h_starts[32 - 5];
+        if (i_short > 0)
+            remap_rows_kernel<<<blocks_for((int64_t)i_short * 32, 256), 256>>>(
+                old_off, static_cast<const int32_t *>(d_old_src.p), g->d_off, g->d_perm, g->d_inv, i_short, g->d_src);
+        if (i_short < n)
+            remap_short_rows_kernel<<<blocks_for((int64_t)(n - i_short), 256), 256>>>(
+                old_off, static_cast<const int32_t *>(d_old_src.p), g->d_off, g->d_perm, g->d_inv, i_short, n, g->d_src);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
