@@ -19,18 +19,64 @@ size_t gather_smem_bytes(int prec, int W);   // below, beside pr_tile_smem_bytes
 
 namespace {
 
+// Per-device memory pool of the solve workspaces: stream-ordered allocations
+// that return to the pool when a solve ends, so that repeated solves reuse the
+// memory instead of paying cudaMalloc/cudaFree (which synchronise). Up to
+// kPoolKeepBytes stay reserved between solves; the rest goes back to the device.
+constexpr unsigned long long kPoolKeepBytes = 4ull << 30;
+
+cudaMemPool_t workspace_pool(int dev) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    unsigned long long keep = kPoolKeepBytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+    return pool;
+}
+
 struct Arena {
     char *base = nullptr;
     size_t size = 0;
-    ~Arena() { if (base) cudaFree(base); }
+    cudaStream_t stream = nullptr;
+    bool pooled = false;
+    ~Arena() {
+        if (!base) return;
+        if (pooled) cudaFreeAsync(base, stream);
+        else cudaFree(base);
+    }
     size_t reserve(size_t bytes) {   // returns offset
         size_t off = (size + 255) & ~size_t(255);
         size = off + bytes;
         return off;
     }
-    pr_status alloc() {
+    pr_status alloc(cudaStream_t st) {
         if (size == 0) size = 256;
-        cudaError_t e = cudaMalloc((void **)&base, size);
+        stream = st;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaMemPool_t pool = workspace_pool(dev);
+        cudaError_t e = cudaErrorMemoryAllocation;
+        if (pool) {
+            e = cudaMallocFromPoolAsync((void **)&base, size, pool, st);
+            pooled = e == cudaSuccess;
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            e = cudaMalloc((void **)&base, size);
+        }
         if (e != cudaSuccess) {
             base = nullptr;
             cudaGetLastError();
@@ -520,7 +566,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     const size_t off_glob = ar.reserve(sizeof(GlobalDev));
     const size_t off_ctajob = ar.reserve((size_t)total_ctas * sizeof(int32_t));
     const size_t off_gctajob = ar.reserve((size_t)std::max(total_gctas, 1) * sizeof(int32_t));
-    s = ar.alloc();
+    s = ar.alloc(st);
     if (s != PR_OK) return s;
     // ---- fill job and column state on the host
     std::vector<JobDev> hjobs(jobs.size());
