@@ -228,8 +228,19 @@ __global__ void check_outdeg_kernel(const int32_t *__restrict__ count, const int
         if (count[v] != outdeg[v]) atomicMin(bad_vertex, (unsigned long long)v);
 }
 // Relabelled rows: row i of the new CSR is caller row perm[i], its sources
-// mapped through inv. One warp per row (rows of 32 or more in-edges, which the
-// relabelling puts first) or one thread per row (the rest, from row i0 on).
+// mapped through inv: one warp per row for rows of 32 to 1023 in-edges, one
+// thread per row below (the relabelling orders rows by in-degree class, longest
+// first; the longest rows get a CTA each, remap_hub_rows_kernel).
+// Rows of 1024 or more in-edges (first in the new order): one CTA per row.
+__global__ void remap_hub_rows_kernel(const int32_t *__restrict__ old_off, const int32_t *__restrict__ old_src,
+                                      const int32_t *__restrict__ new_off, const int32_t *__restrict__ perm,
+                                      const int32_t *__restrict__ inv, int32_t n_hub, int32_t *__restrict__ new_src) {
+    for (int32_t i = blockIdx.x; i < n_hub; i += gridDim.x) {
+        const int32_t v = perm[i];
+        const int32_t a = old_off[v], len = old_off[v + 1] - a, o = new_off[i];
+        for (int32_t k = threadIdx.x; k < len; k += blockDim.x) new_src[o + k] = inv[old_src[a + k]];
+    }
+}
 __global__ void remap_short_rows_kernel(const int32_t *__restrict__ old_off, const int32_t *__restrict__ old_src,
                                         const int32_t *__restrict__ new_off, const int32_t *__restrict__ perm,
                                         const int32_t *__restrict__ inv, int32_t i0, int32_t n,
@@ -242,11 +253,11 @@ __global__ void remap_short_rows_kernel(const int32_t *__restrict__ old_off, con
 }
 __global__ void remap_rows_kernel(const int32_t *__restrict__ old_off, const int32_t *__restrict__ old_src,
                                   const int32_t *__restrict__ new_off, const int32_t *__restrict__ perm,
-                                  const int32_t *__restrict__ inv, int32_t n, int32_t *__restrict__ new_src) {
+                                  const int32_t *__restrict__ inv, int32_t i0, int32_t n, int32_t *__restrict__ new_src) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = w0; i < n; i += nw) {
+    for (int64_t i = i0 + w0; i < n; i += nw) {
         const int32_t v = perm[i];
         const int32_t a = old_off[v], len = old_off[v + 1] - a, o = new_off[i];
         for (int32_t k = lane; k < len; k += 32) new_src[o + k] = inv[old_src[a + k]];
@@ -605,11 +616,16 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     if (e == cudaSuccess) e = cudaMemcpy(h_starts, d_starts.p, sizeof(h_starts), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(h_cmax, d_cmax.p, sizeof(h_cmax), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && nnz > 0) {
-        // rows with 32 or more in-edges (classes 6 and up) come first in the new order
-        const int32_t i_short = h_starts[32 - 5];
-        if (i_short > 0)
-            remap_rows_kernel<<<blocks_for((int64_t)i_short * 32, 256), 256>>>(
-                old_off, static_cast<const int32_t *>(d_old_src.p), g->d_off, g->d_perm, g->d_inv, i_short, g->d_src);
+        // rows in the new order: 1024+ in-edges (classes 11 and up), then
+        // 32..1023 (classes 6..10), then the rest
+        const int32_t i_hub = h_starts[32 - 10], i_short = h_starts[32 - 5];
+        if (i_hub > 0)
+            remap_hub_rows_kernel<<<std::min<int32_t>(i_hub, 65535), 256>>>(
+                old_off, static_cast<const int32_t *>(d_old_src.p), g->d_off, g->d_perm, g->d_inv, i_hub, g->d_src);
+        if (i_short > i_hub)
+            remap_rows_kernel<<<blocks_for((int64_t)(i_short - i_hub) * 32, 256), 256>>>(
+                old_off, static_cast<const int32_t *>(d_old_src.p), g->d_off, g->d_perm, g->d_inv, i_hub, i_short,
+                g->d_src);
         if (i_short < n)
             remap_short_rows_kernel<<<blocks_for((int64_t)(n - i_short), 256), 256>>>(
                 old_off, static_cast<const int32_t *>(d_old_src.p), g->d_off, g->d_perm, g->d_inv, i_short, n, g->d_src);
