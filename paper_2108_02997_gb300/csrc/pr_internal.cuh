@@ -26,12 +26,6 @@ constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, 
 #ifndef PR_MIN_BLOCKS
 #define PR_MIN_BLOCKS 3
 #endif
-#ifndef PR_PREFETCH_TILE
-#define PR_PREFETCH_TILE 1
-#endif
-#ifndef PR_CHUNK_PIPE
-#define PR_CHUNK_PIPE 1
-#endif
 #ifndef PR_SPLIT_PASSES
 #define PR_SPLIT_PASSES 1
 #endif
@@ -59,10 +53,6 @@ constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, 
 #ifndef PR_VEC_GATHER_BATCH
 #define PR_VEC_GATHER_BATCH 4
 #endif
-constexpr bool kPrefetchTile = PR_PREFETCH_TILE != 0;  // load the next tile's descriptor a tile ahead
-// One column, chunks of long rows: the next step's in-edge indices are loaded
-// while the current step's gathers are in flight.
-constexpr bool kChunkPipe = PR_CHUNK_PIPE != 0;
 // One column, 8-byte values: a rows tile's row sums go to shared memory and all
 // 32 lanes then update the tile's rows (consecutive rows on consecutive lanes),
 // instead of the one lane per lane group that formed each sum (measured: 2-3 %

@@ -651,46 +651,29 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                 __syncwarp();
             }
             if (kStaged && cv.active) {
-                if constexpr (kChunkPipe) {
-                    // the next step's indices are requested while this step's
-                    // gathers are in flight
-                    int32_t u[PER];
+                // the next step's indices are requested while this step's
+                // gathers are in flight
+                int32_t u[PER];
+#pragma unroll
+                for (int k = 0; k < PER; k++) {
+                    const int idx = lane + 32 * k;
+                    u[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
+                }
+                for (int base = lane; base < nv; base += VT) {
+                    V x[PER];
+#pragma unroll
+                    for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
+                    int32_t un[PER];
 #pragma unroll
                     for (int k = 0; k < PER; k++) {
-                        const int idx = lane + 32 * k;
-                        u[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
+                        const int idx = base + VT + 32 * k;
+                        un[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
                     }
-                    for (int base = lane; base < nv; base += VT) {
-                        V x[PER];
 #pragma unroll
-                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
-                        int32_t un[PER];
+                    for (int k = 0; k < PER; k++)
+                        if (u[k] >= 0) sum.add(x[k]);
 #pragma unroll
-                        for (int k = 0; k < PER; k++) {
-                            const int idx = base + VT + 32 * k;
-                            un[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
-                        }
-#pragma unroll
-                        for (int k = 0; k < PER; k++)
-                            if (u[k] >= 0) sum.add(x[k]);
-#pragma unroll
-                        for (int k = 0; k < PER; k++) u[k] = un[k];
-                    }
-                } else {
-                    for (int base = lane; base < nv; base += VT) {
-                        int32_t u[PER];
-#pragma unroll
-                        for (int k = 0; k < PER; k++) {
-                            const int idx = base + 32 * k;
-                            u[k] = idx < nv ? src[T.e0 + idx / W] : -1;
-                        }
-                        V x[PER];
-#pragma unroll
-                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
-#pragma unroll
-                        for (int k = 0; k < PER; k++)
-                            if (u[k] >= 0) sum.add(x[k]);
-                    }
+                    for (int k = 0; k < PER; k++) u[k] = un[k];
                 }
             }
             V sv = sum.get();
@@ -736,15 +719,10 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
 
         // the next tile's descriptor is requested while this tile is worked on
         Tile T_next{};
-        if (kPrefetchTile && local * kWarps + warp < ntiles) T_next = load_tile(tiles + local * kWarps + warp);
+        if (local * kWarps + warp < ntiles) T_next = load_tile(tiles + local * kWarps + warp);
         for (int t = local * kWarps + warp; t < ntiles; t += wstride) {
-            Tile T;
-            if constexpr (kPrefetchTile) {
-                T = T_next;
-                if (t + wstride < ntiles) T_next = load_tile(tiles + t + wstride);
-            } else {
-                T = tiles[t];
-            }
+            const Tile T = T_next;
+            if (t + wstride < ntiles) T_next = load_tile(tiles + t + wstride);
             if (T.glog >= 0) {
                 if constexpr (kStaged) rows_tile_w1(T);
                 else rows_tile_vec(T);
