@@ -176,3 +176,23 @@ def test_road_grid_matches_oracle(B, orc, gg):
             ref = orc.pagerank(g, 0.85, tau, norm, 500, history=True, threads=orc.default_threads())
             res = B.pr_solve(dg, 0.85, tau, norm, 500)
             assert_fp64_parity(res.ranks, res.iters, res.err, ref, tau, norm, f"road norm {norm}")
+
+
+def test_kernel_occupancy_and_split_times(B, er10k_dev):
+    """pr_kernel_occupancy reports resident CTAs for every width; a split
+    host-loop solve reports its gather and update kernel times, which add up
+    to the pass time."""
+    for prec in ("df64", "fp64", "fp32"):
+        for w in (1, 2, 4, 8, 16, 32):
+            assert 1 <= B.kernel_occupancy(prec, w) <= 8
+    with pytest.raises(B.PageRankError):
+        B.kernel_occupancy("df64", 3)
+    with pytest.raises(B.PageRankError):
+        B.kernel_occupancy("mixed", 1)
+    B.pr_solve(er10k_dev, 0.85, 1e-10, 1, 500, loop="host", kernels="split")
+    st = B.pr_last_solve_stats()
+    assert st["gather_ms"] > 0 and st["update_ms"] > 0
+    assert abs(st["gather_ms"] + st["update_ms"] - st["kernel_ms"]) <= 1e-6 * max(1.0, st["kernel_ms"])
+    B.pr_solve(er10k_dev, 0.85, 1e-10, 1, 500, loop="host", kernels="fused")
+    st = B.pr_last_solve_stats()
+    assert st["gather_ms"] == 0 and st["update_ms"] == 0 and st["kernel_ms"] > 0
