@@ -355,6 +355,18 @@ def run_ours(args, world, rank, local):
         learned["iterations_uniform"] = [x.iters for x in xs_u]
         learned["iterations_learned"] = inst_iters
         learned["iterations_saved_total"] = sum(x.iters for x in xs_u) - sum(inst_iters)
+        # cost of the start itself: features + MLP + softmax, per graph (CUDA events)
+        ws = []
+        for gi, dg in enumerate(dgs):
+            buf = torch.empty(dg.n, dtype=torch.float64, device="cuda")
+            mlp.warm_start(dg, 0.85, out=buf, stream=sptr)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mlp.warm_start(dg, 0.85, out=buf, stream=sptr)
+            e1.record(stream)
+            e1.synchronize()
+            ws.append({"n": dg.n, "ms": e0.elapsed_time(e1)})
+        learned["warm_start_ms"] = ws
         if precision != "df64":
             # the same comparison with df64 throughout (no FP32 phase)
             its = {}
