@@ -1,20 +1,26 @@
-// pr_kernels.cuh — the fused PageRank iteration kernel and its init pass.
+// pr_kernels.cuh — the PageRank iteration kernels and the init pass.
 //
-// One launch of pr_iter_kernel performs one update of every active column of
-// every job (Section 2) and decides, on the device, which columns stop
-// (Sections 3-4). Work is cut into warp tiles; every warp runs its tiles
-// independently (no block-wide barrier until the end of the pass):
+// One pass updates every active column of every job once (Section 2) and
+// decides, on the device, which columns stop (Sections 3-4). A pass is either
+// two kernels, the gather kernel (pr_iter_kernel in its gather form: row sums
+// only) followed by the streaming update kernel (pr_update_kernel), or, for
+// small solves, one fused pr_iter_kernel that does both.
 //
-//   rows tile (a run of rows of one in-degree class, at most 128 gathered
-//   values): coalesced loads of the tile's in-edge indices and row offsets,
-//   four independent gathers contrib[u] = r[u]/d_u per lane into a per-warp
-//   shared buffer, then lane groups add each row's values:
+// Gather work is cut into warp tiles; every warp runs its tiles independently
+// (no block-wide barrier until the end of the pass):
+//   rows tile, one column (a run of rows of one in-degree class, at most 256
+//   in-edges): coalesced loads of the tile's in-edge indices and row offsets,
+//   eight independent gathers contrib[u] = r[u]/d_u per lane into a per-warp
+//   shared buffer, then lane groups add each row's values in a fixed order;
+//   rows tile, W columns: the same with one 8- or 16-byte vector gather per
+//   in-edge and column group;
+//   chunk tile (part of a long row): the warp strides over the chunk with the
+//   next step's indices in flight; the last chunk of a row to finish adds the
+//   chunk sums in chunk order.
+// The update of a row (fused kernel, or update kernel from the row sums):
 //     r'[v]  = c0 + alpha * sum                                    (SpMV)
 //     accumulate |r'-r|, (r'-r)^2, max|r'-r|                         (norms)
 //     contrib'[v] = r'[v]/d_v, or add r'[v] to the dangling sum when d_v = 0
-//   chunk tile (part of a long row): the warp strides over the chunk with four
-//   gathers in flight per lane; the last chunk of a row to finish adds the
-//   chunk sums in chunk order and updates the row.
 //
 // At the end of the pass the last CTA of a job reduces the CTA partials in a
 // fixed order (FP64), forms L1, L2 = sqrt(sum of squares) and Linf, applies
@@ -27,8 +33,8 @@
 #include "pr_internal.cuh"
 
 enum PassMode { kPassInit = 0, kPassIterate = 1 };
-// Iteration kernel flavours: the whole pass in one kernel, or (one column,
-// split passes) the gather half that only writes row sums.
+// Iteration kernel forms: the whole pass in one kernel, or the gather half of
+// a split pass that only writes row sums.
 enum KernelMode { kModeFused = 0, kModeGather = 1 };
 
 // ---------------------------------------------------------------- small helpers

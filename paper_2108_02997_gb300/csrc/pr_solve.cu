@@ -1,12 +1,14 @@
 // pr_solve.cu — the solve driver: lays out jobs, runs the device loop.
 //
-// A request is a list of columns (iterate sequences) with their stopping taps.
-// Columns on the same graph are packed, up to 32 at a time, into jobs whose
-// rank matrices are N x W vertex-major (W = columns padded to a power of two),
-// so that one read of a row's in-edge indices serves W gathers. All jobs of a
-// request advance together, one fused kernel launch per iteration, inside a
-// CUDA graph whose while-node repeats the launch until the device reports that
-// every column has stopped and every answer has been copied out.
+// A request is a list of columns (iterate sequences) with their stopping taps,
+// and its jobs: columns of one graph, at most 32, whose rank matrices are
+// N x W vertex-major (W = columns padded to a power of two), so that one read
+// of a row's in-edge indices serves W gathers (the planner in pr_plan.cu
+// chooses the jobs). All jobs of a request advance together, one pass per
+// iteration (a gather kernel and an update kernel, or one fused kernel for
+// small requests), inside a CUDA graph whose while-node repeats the pass until
+// the device reports that every column has stopped and every answer has been
+// copied out.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
