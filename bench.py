@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -226,7 +227,15 @@ def sweep_report(B, torch, dgs, specs, last, outs, sptr):
         r_c = B.pr_solve(dgs[0], a, 1e-10, 1, 500, out=out, init=prev) if prev is not None else r_u
         cont.append(r_c.iters)
         prev = out if prev is not None else r_u.ranks
+    # the paper's norm comparison over the tau sweep at alpha 0.85: geometric
+    # mean over tau of iterations, each norm relative to L1 (Section 4)
+    def gm(v):
+        v = [float(x) for x in v]
+        return math.exp(sum(math.log(x) for x in v) / len(v))
+    its = {nm: [x.iters for (gi, a, t, n2, mi), x in zip(specs, last) if a == 0.85 and n2 == nm] for nm in (1, 2, 3)}
+    norm_gm = {name: gm(its[nm]) / gm(its[1]) for nm, name in ((1, "L1"), (2, "L2"), (3, "Linf"))}
     return {"alpha": alphas, "l1_vs_alpha_085": l1, "iterations_vs_alpha_085": ratio,
+            "tau_sweep_iteration_gm_ratio_alpha_085": norm_gm,
             "fp32_largest_tau_hitting_cap": stall,
             "continuation": {"iterations_uniform": uni, "iterations_from_previous_alpha": cont,
                              "saved": sum(uni) - sum(cont)}}
