@@ -118,8 +118,8 @@ typedef enum pr_group {
 typedef enum pr_kernels {
     PR_KERNELS_AUTO = 0,   /* default: split passes when a sub-solve's work (in-edges
                               x column width, summed over its jobs) is at least
-                              4 million, one fused kernel below that (launch-bound
-                              sizes, where one launch per pass is cheaper) */
+                              16 million, one fused kernel below that (where one
+                              launch per pass is cheaper) */
     PR_KERNELS_FUSED = 1,  /* one kernel per pass: gathers, row sums, updates,
                               norms and stopping rules */
     PR_KERNELS_SPLIT = 2   /* two kernels per pass: a gather kernel that forms the
