@@ -73,7 +73,8 @@ extern "C" void pr_options_default(pr_options *opt) {
 }
 
 // Implemented in pr_learn.cu.
-pr_status pr_learned_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_out, cudaStream_t st);
+pr_status pr_learned_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_out, bool relabelled,
+                           cudaStream_t st);
 bool pr_mlp_valid(const pr_mlp *m);
 
 namespace {
@@ -101,10 +102,6 @@ pr_status check_instance(const pr_instance &in) {
     return PR_OK;
 }
 
-struct DevBuf {
-    void *p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
-};
 
 }  // namespace
 
@@ -134,7 +131,7 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
         ok.push_back(i);
     }
     // ---- start vectors on the device (caller order)
-    std::vector<std::unique_ptr<DevBuf>> bufs;
+    std::vector<std::unique_ptr<PoolBuf>> bufs;
     std::map<std::pair<const void *, const void *>, const double *> init_dev;   // (graph, src) -> device copy
     std::map<std::pair<const pr_graph *, uint64_t>, const double *> learned;
     auto start_for = [&](const pr_instance &in, const double **out) -> pr_status {
@@ -147,8 +144,9 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
             auto key = std::make_pair((const void *)in.g, (const void *)src);
             auto it = init_dev.find(key);
             if (it != init_dev.end()) { *out = it->second; return PR_OK; }
-            bufs.emplace_back(new DevBuf());
-            PR_CUDA(cudaMalloc(&bufs.back()->p, bytes));
+            bufs.emplace_back(new PoolBuf());
+            pr_status a = bufs.back()->alloc(bytes, st);
+            if (a != PR_OK) return a;
             PR_CUDA(cudaMemcpyAsync(bufs.back()->p, src, bytes, cudaMemcpyHostToDevice, st));
             *out = (const double *)bufs.back()->p;
             init_dev[key] = *out;
@@ -159,9 +157,10 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
         auto key = std::make_pair(in.g, abits);
         auto it = learned.find(key);
         if (it != learned.end()) { *out = it->second; return PR_OK; }
-        bufs.emplace_back(new DevBuf());
-        PR_CUDA(cudaMalloc(&bufs.back()->p, bytes));
-        pr_status ls = pr_learned_start(opt.mlp, in.g, in.alpha, (double *)bufs.back()->p, st);
+        bufs.emplace_back(new PoolBuf());
+        pr_status ls = bufs.back()->alloc(bytes, st);
+        if (ls != PR_OK) return ls;
+        ls = pr_learned_start(opt.mlp, in.g, in.alpha, (double *)bufs.back()->p, true, st);
         if (ls != PR_OK) return ls;
         *out = (const double *)bufs.back()->p;
         learned[key] = *out;
@@ -200,6 +199,7 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
             sc.g = in.g;
             sc.alpha = in.alpha;
             sc.init_dev = start;
+            sc.init_relabelled = opt.init == PR_INIT_LEARNED;   // learned starts come in relabelled order
             if (opt.share_trajectories) col_of[key] = c;
         }
         SolveColumn &sc = req.cols[c];

@@ -59,7 +59,8 @@ struct SolveColumn {
     std::vector<Tap> taps;          // filled with out pointers (device, caller order)
     std::vector<int32_t> inst;      // instance index of each tap
     std::vector<double *> host_dst; // per tap: host buffer to receive the answer, or null
-    const double *init_dev = nullptr;   // device start vector in caller order, or null
+    const double *init_dev = nullptr;   // device start vector, or null
+    bool init_relabelled = false;       // init_dev in relabelled order (else caller order)
     double *hist_host = nullptr;
     int32_t hist_cap = 0;
 };
@@ -108,6 +109,22 @@ void *pr_iter_kernel_for(int precision, int W);
 void *pr_init_kernel_for(int precision, int W);
 size_t pr_tile_smem_bytes(int precision, int W);
 pr_status pr_kernel_setup(int precision, int W, int *blocks_per_sm);
+
+// Stream-ordered device buffer from the per-device workspace pool
+// (pr_solve.cu): released with cudaFreeAsync on the stream it was taken on,
+// so repeated calls reuse memory without the synchronising cudaMalloc and
+// cudaFree. Falls back to cudaMalloc when the pool cannot serve the request.
+struct PoolBuf {
+    void *p = nullptr;
+    cudaStream_t stream = nullptr;
+    bool pooled = false;
+    PoolBuf() = default;
+    PoolBuf(const PoolBuf &) = delete;
+    PoolBuf &operator=(const PoolBuf &) = delete;
+    ~PoolBuf() { release(); }
+    pr_status alloc(size_t bytes, cudaStream_t st);
+    void release();
+};
 
 // Live-handle registry: guards every entry point against stale handles.
 void registry_add(const void *p);

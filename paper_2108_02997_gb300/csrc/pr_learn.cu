@@ -180,16 +180,53 @@ __device__ void block_forward(MlpShared &S, int nrows, float c2[8][4]) {
 // ------------------------------------------------------------------ features
 // f = [log(1+indeg), log(1+outdeg), mean and max over in-neighbours u of
 // log(1+outdeg(u)) (0 without in-neighbours), alpha], relabelled order.
-__global__ void features_kernel(const int32_t *__restrict__ off, const int32_t *__restrict__ src,
-                                const int32_t *__restrict__ outdeg, int32_t n, float alpha, float *feat) {
-    const int lane = threadIdx.x & 31;
-    const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long v = warp_id; v < n; v += nwarps) {
+// Rows are relabelled by descending in-degree class, so each of three row
+// ranges gets its own worker size: rows with at least kHubDeg in-edges a CTA
+// each, rows with at least kWarpDeg a warp each, the rest a thread each.
+constexpr int kHubDeg = 2048;
+constexpr int kWarpDeg = 32;
+constexpr int kFeatThreads = 512;
+constexpr int kFeatWarps = kFeatThreads / 32;
+
+// lo[v] = log(1 + outdeg(v)), gathered once per in-edge by the features kernel
+__global__ void log_outdeg_kernel(const int32_t *__restrict__ outdeg, int32_t n, float *__restrict__ lo) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+        lo[v] = log1pf((float)outdeg[v]);
+}
+
+// One feature row: S = 8 floats (training layout, alpha in f[4], zero pad) or
+// S = 4 floats (inference layout, alpha passed to the network kernel).
+template <int S>
+__device__ __forceinline__ void put_features(float *feat, long long v, int32_t d, float lov, float s, float mx,
+                                             float alpha) {
+    float *f = feat + (size_t)v * S;
+    *reinterpret_cast<float4 *>(f) =
+        make_float4(log1pf((float)d), lov, d > 0 ? s / (float)d : 0.0f, d > 0 ? mx : 0.0f);
+    if (S == 8) *reinterpret_cast<float4 *>(f + 4) = make_float4(alpha, 0.0f, 0.0f, 0.0f);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kFeatThreads) features_kernel(const int32_t *__restrict__ off,
+                                                                const int32_t *__restrict__ src,
+                                                                const float *__restrict__ lo, int32_t n,
+                                                                int32_t hub_end, int32_t warp_end, float alpha,
+                                                                float *__restrict__ feat) {
+    __shared__ float red_s[kFeatWarps], red_m[kFeatWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // rows [0, hub_end): one CTA per row, four independent gathers per thread in flight
+    for (int32_t v = blockIdx.x; v < hub_end; v += gridDim.x) {
         const int32_t e0 = off[v], e1 = off[v + 1];
         float s = 0.0f, mx = 0.0f;
-        for (int32_t e = e0 + lane; e < e1; e += 32) {
-            const float x = log1pf((float)outdeg[src[e]]);
+        int32_t e = e0 + tid;
+        for (; e + 3 * kFeatThreads < e1; e += 4 * kFeatThreads) {
+            const int32_t u0 = src[e], u1 = src[e + kFeatThreads], u2 = src[e + 2 * kFeatThreads],
+                          u3 = src[e + 3 * kFeatThreads];
+            const float x0 = lo[u0], x1 = lo[u1], x2 = lo[u2], x3 = lo[u3];
+            s += (x0 + x1) + (x2 + x3);
+            mx = fmaxf(mx, fmaxf(fmaxf(x0, x1), fmaxf(x2, x3)));
+        }
+        for (; e < e1; e += kFeatThreads) {
+            const float x = lo[src[e]];
             s += x;
             mx = fmaxf(mx, x);
         }
@@ -198,15 +235,59 @@ __global__ void features_kernel(const int32_t *__restrict__ off, const int32_t *
             mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, m));
         }
         if (lane == 0) {
-            const int32_t d = e1 - e0;
-            float *f = feat + (size_t)v * kFS;
-            f[0] = log1pf((float)d);
-            f[1] = log1pf((float)outdeg[v]);
-            f[2] = d > 0 ? s / (float)d : 0.0f;
-            f[3] = d > 0 ? mx : 0.0f;
-            f[4] = alpha;
-            f[5] = f[6] = f[7] = 0.0f;
+            red_s[warp] = s;
+            red_m[warp] = mx;
         }
+        __syncthreads();
+        if (tid == 0) {
+            float ts = 0.0f, tm = 0.0f;
+            for (int w = 0; w < kFeatWarps; w++) {
+                ts += red_s[w];
+                tm = fmaxf(tm, red_m[w]);
+            }
+            put_features<S>(feat, v, e1 - e0, lo[v], ts, tm, alpha);
+        }
+        __syncthreads();
+    }
+    // rows [hub_end, warp_end): one warp per row
+    const long long nw = (long long)gridDim.x * kFeatWarps;
+    for (long long v = hub_end + (long long)blockIdx.x * kFeatWarps + warp; v < warp_end; v += nw) {
+        const int32_t e0 = off[v], e1 = off[v + 1];
+        float s = 0.0f, mx = 0.0f;
+        int32_t e = e0 + lane;
+        for (; e + 32 < e1; e += 64) {
+            const float x0 = lo[src[e]], x1 = lo[src[e + 32]];
+            s += x0 + x1;
+            mx = fmaxf(mx, fmaxf(x0, x1));
+        }
+        if (e < e1) {
+            const float x = lo[src[e]];
+            s += x;
+            mx = fmaxf(mx, x);
+        }
+        for (int m = 16; m > 0; m >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, m);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, m));
+        }
+        if (lane == 0) put_features<S>(feat, v, e1 - e0, lo[v], s, mx, alpha);
+    }
+    // rows [warp_end, n): one thread per row (fewer than kWarpDeg in-edges each)
+    const long long nt = (long long)gridDim.x * kFeatThreads;
+    for (long long v = warp_end + (long long)blockIdx.x * kFeatThreads + tid; v < n; v += nt) {
+        const int32_t e0 = off[v], e1 = off[v + 1];
+        float s = 0.0f, mx = 0.0f;
+        int32_t e = e0;
+        for (; e + 1 < e1; e += 2) {
+            const float x0 = lo[src[e]], x1 = lo[src[e + 1]];
+            s += x0 + x1;
+            mx = fmaxf(mx, fmaxf(x0, x1));
+        }
+        if (e < e1) {
+            const float x = lo[src[e]];
+            s += x;
+            mx = fmaxf(mx, x);
+        }
+        put_features<S>(feat, v, e1 - e0, lo[v], s, mx, alpha);
     }
 }
 
@@ -226,40 +307,129 @@ __global__ void targets_kernel(const double *r_caller, const int32_t *perm, int3
 }
 
 // ------------------------------------------------------------------ inference
-__global__ void __launch_bounds__(kMlpThreads) mlp_forward_kernel(const float *master, const __nv_bfloat16 *wbf,
-                                                                  const float *feat, int32_t n, float *y) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    MlpShared &S = *reinterpret_cast<MlpShared *>(smem_raw);
-    load_weights(S, master, wbf);
-    for (long long b0 = (long long)blockIdx.x * kRowsPerBlock; b0 < n; b0 += (long long)gridDim.x * kRowsPerBlock) {
-        const int nrows = (int)min((long long)kRowsPerBlock, (long long)n - b0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < kRowsPerBlock * kFS; i += blockDim.x) {
-            const int r = i / kFS;
-            S.f[i] = r < nrows ? feat[(size_t)(b0 + r) * kFS + (i % kFS)] : 0.0f;
-        }
-        __syncthreads();
+// Forward pass without shared-memory activations: each warp takes 16-row
+// tiles in turn; a lane computes the layer-1 activations of exactly the
+// entries its mma.sync A fragments hold (rows g and g+8, columns 2t, 2t+1,
+// 2t+8, 2t+9 of each 16-column block) straight into registers, so only the
+// weights sit in shared memory and no CTA-wide barrier separates the layers.
+// The arithmetic, and its order, is that of block_forward. Each CTA also
+// writes the largest y it produced (for the softmax).
+constexpr int kInferThreads = 256;
+constexpr int kInferWarps = kInferThreads / 32;
+
+struct InferShared {
+    __nv_bfloat16 w2[kH * kLd];   // W2[n][k]
+    float4 w1[kH];                // W1[j][0..3]
+    float w1a[kH];                // W1[j][4] (the alpha weight)
+    float b1[kH], b2[kH], w3[kH];
+    float b3;
+    float wmax[kInferWarps];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const float *master, const __nv_bfloat16 *wbf,
+                                                                     const float4 *__restrict__ feat, int32_t n,
+                                                                     float alpha, float *__restrict__ y,
+                                                                     float *__restrict__ cta_max) {
+    __shared__ __align__(16) InferShared S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kH * kH; i += kInferThreads) S.w2[(i / kH) * kLd + (i % kH)] = wbf[oW2 + i];
+    for (int j = tid; j < kH; j += kInferThreads) {
+        const __nv_bfloat16 *w = wbf + oW1 + j * kF;
+        S.w1[j] = make_float4(__bfloat162float(w[0]), __bfloat162float(w[1]), __bfloat162float(w[2]),
+                              __bfloat162float(w[3]));
+        S.w1a[j] = __bfloat162float(w[4]);
+        S.b1[j] = master[oB1 + j];
+        S.b2[j] = master[oB2 + j];
+        S.w3[j] = __bfloat162float(wbf[oW3 + j]);
+    }
+    if (tid == 0) S.b3 = master[oB3];
+    __syncthreads();
+    const int g = lane >> 2, t = lane & 3;
+    float ymax = -INFINITY;
+    const long long ntiles = ((long long)n + 15) / 16;
+    for (long long tile = (long long)blockIdx.x * kInferWarps + warp; tile < ntiles;
+         tile += (long long)gridDim.x * kInferWarps) {
+        const long long ra = tile * 16 + g, rb = ra + 8;
+        const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const float4 fa = ra < n ? feat[ra] : zero, fb = rb < n ? feat[rb] : zero;
         float c2[8][4];
-        block_forward(S, nrows, c2);
-        __syncthreads();
-        for (int r = threadIdx.x; r < nrows; r += blockDim.x) y[b0 + r] = S.y[r];
+#pragma unroll
+        for (int nt = 0; nt < 8; nt++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) c2[nt][q] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < 4; ks++) {
+            float ha[4], hb[4];   // columns ks*16 + 2t + {0, 1, 8, 9}
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int j = ks * 16 + 2 * t + (q & 1) + (q >> 1) * 8;
+                const float4 w = S.w1[j];
+                const float wa = S.w1a[j];
+                float za = S.b1[j], zb = za;
+                za = fmaf(w.x, fa.x, za);
+                zb = fmaf(w.x, fb.x, zb);
+                za = fmaf(w.y, fa.y, za);
+                zb = fmaf(w.y, fb.y, zb);
+                za = fmaf(w.z, fa.z, za);
+                zb = fmaf(w.z, fb.z, zb);
+                za = fmaf(w.w, fa.w, za);
+                zb = fmaf(w.w, fb.w, zb);
+                za = fmaf(wa, ra < n ? alpha : 0.0f, za);
+                zb = fmaf(wa, rb < n ? alpha : 0.0f, zb);
+                ha[q] = gelu(za);
+                hb[q] = gelu(zb);
+            }
+            const uint32_t a[4] = {pack_bf16(ha[0], ha[1]), pack_bf16(hb[0], hb[1]), pack_bf16(ha[2], ha[3]),
+                                   pack_bf16(hb[2], hb[3])};
+#pragma unroll
+            for (int nt = 0; nt < 8; nt++) {
+                uint32_t b[2];
+                load_b(b, S.w2, kLd, nt * 8, ks * 16, lane);
+                mma16816(c2[nt], a, b);
+            }
+        }
+        float ylo = 0.0f, yhi = 0.0f;
+#pragma unroll
+        for (int nt = 0; nt < 8; nt++) {
+            const int j = nt * 8 + 2 * t;
+            ylo = fmaf(gelu(c2[nt][0] + S.b2[j]), S.w3[j], ylo);
+            ylo = fmaf(gelu(c2[nt][1] + S.b2[j + 1]), S.w3[j + 1], ylo);
+            yhi = fmaf(gelu(c2[nt][2] + S.b2[j]), S.w3[j], yhi);
+            yhi = fmaf(gelu(c2[nt][3] + S.b2[j + 1]), S.w3[j + 1], yhi);
+        }
+        ylo += __shfl_xor_sync(0xffffffffu, ylo, 1);
+        yhi += __shfl_xor_sync(0xffffffffu, yhi, 1);
+        ylo += __shfl_xor_sync(0xffffffffu, ylo, 2);
+        yhi += __shfl_xor_sync(0xffffffffu, yhi, 2);
+        ylo += S.b3;
+        yhi += S.b3;
+        if (t == 0) {
+            if (ra < n) {
+                y[ra] = ylo;
+                ymax = fmaxf(ymax, ylo);
+            }
+            if (rb < n) {
+                y[rb] = yhi;
+                ymax = fmaxf(ymax, yhi);
+            }
+        }
+    }
+    for (int m = 16; m > 0; m >>= 1) ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, m));
+    if (lane == 0) S.wmax[warp] = ymax;
+    __syncthreads();
+    if (tid == 0) {
+        float m = -INFINITY;
+        for (int w = 0; w < kInferWarps; w++) m = fmaxf(m, S.wmax[w]);
+        cta_max[blockIdx.x] = m;
     }
 }
 
-// block max of y, then exp(y - max) summed in FP64, then r0 in caller order
-__global__ void max_kernel(const float *y, int32_t n, float *block_max) {
-    __shared__ float s[256];
-    float m = -INFINITY;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        m = fmaxf(m, y[i]);
-    s[threadIdx.x] = m;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) s[threadIdx.x] = fmaxf(s[threadIdx.x], s[threadIdx.x + w]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) block_max[blockIdx.x] = s[0];
-}
+// exp(y - max) summed in FP64 per CTA, then r0 = exp(y - max) / sum
 __global__ void expsum_kernel(const float *y, int32_t n, const float *block_max, int nblocks, double *block_sum) {
     __shared__ double s[256];
     __shared__ float gmax;
@@ -280,24 +450,25 @@ __global__ void expsum_kernel(const float *y, int32_t n, const float *block_max,
     }
     if (threadIdx.x == 0) block_sum[blockIdx.x] = s[0];
 }
-__global__ void normalise_kernel(const float *y, int32_t n, const float *block_max, const double *block_sum, int nblocks,
-                                 const int32_t *perm, double *r0) {
+// perm == nullptr: r0 in relabelled order; else r0[perm[v]] (caller order)
+__global__ void normalise_kernel(const float *y, int32_t n, const float *block_max, int nmax, const double *block_sum,
+                                 int nsum, const int32_t *perm, double *r0) {
     __shared__ float gmax;
     __shared__ double total;
     if (threadIdx.x == 0) {
         float m = -INFINITY;
+        for (int b = 0; b < nmax; b++) m = fmaxf(m, block_max[b]);
         double t = 0.0;
-        for (int b = 0; b < nblocks; b++) {
-            m = fmaxf(m, block_max[b]);
-            t += block_sum[b];
-        }
+        for (int b = 0; b < nsum; b++) t += block_sum[b];
         gmax = m;
         total = t;
     }
     __syncthreads();
     const bool ok = total > 0.0 && isfinite(total) && isfinite(gmax);
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
-        r0[perm[v]] = ok ? (double)expf(y[v] - gmax) / total : 1.0 / (double)n;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        const double x = ok ? (double)expf(y[v] - gmax) / total : 1.0 / (double)n;
+        r0[perm ? perm[v] : v] = x;
+    }
 }
 
 // ------------------------------------------------------------------ training
@@ -520,19 +691,9 @@ __global__ void to_bf16_kernel(const float *master, __nv_bfloat16 *wbf) {
 }
 
 // ------------------------------------------------------------------ host helpers
-struct DBuf {
-    void *p = nullptr;
-    ~DBuf() { if (p) cudaFree(p); }
-};
+using DBuf = PoolBuf;
 
-pr_status dmalloc(DBuf &b, size_t bytes) {
-    cudaError_t e = cudaMalloc(&b.p, bytes ? bytes : 16);
-    if (e != cudaSuccess) {
-        b.p = nullptr;
-        return pr_cuda_fail(e, "cudaMalloc");
-    }
-    return PR_OK;
-}
+pr_status dmalloc(DBuf &b, size_t bytes, cudaStream_t st) { return b.alloc(bytes ? bytes : 16, st); }
 
 int grid_for(long long work, int threads) {
     int dev = 0, sms = 0;
@@ -545,19 +706,46 @@ int grid_for(long long work, int threads) {
 pr_status mlp_setup_smem() {
     static bool done = false;
     if (!done) {
-        PR_CUDA(cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpShared)));
         PR_CUDA(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpShared)));
         done = true;
     }
     return PR_OK;
 }
 
-// features of g at alpha into feat (relabelled order, n x kFS floats)
-pr_status compute_features(const pr_graph *g, double alpha, float *feat, cudaStream_t st) {
-    const int blocks = grid_for((long long)g->n * 32, 256);
-    features_kernel<<<blocks, 256, 0, st>>>(g->d_off, g->d_src, g->d_outdeg, g->n, (float)alpha, feat);
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// Features of g at alpha into feat (relabelled order, S floats per row; see
+// put_features). The row ranges of the three worker sizes follow from the
+// in-degree classes, which are in descending order.
+template <int S>
+pr_status compute_features_t(const pr_graph *g, double alpha, float *feat, cudaStream_t st) {
+    const int32_t n = g->n;
+    int32_t hub_end = n, warp_end = n;
+    for (const ClassRange &c : g->classes) {
+        if (c.max_deg < kHubDeg && hub_end == n) hub_end = c.begin;
+        if (c.max_deg < kWarpDeg && warp_end == n) warp_end = c.begin;
+    }
+    if (hub_end > warp_end) hub_end = warp_end;
+    DBuf lo;
+    pr_status s = dmalloc(lo, (size_t)n * sizeof(float), st);
+    if (s != PR_OK) return s;
+    log_outdeg_kernel<<<grid_for(n, 256), 256, 0, st>>>(g->d_outdeg, n, (float *)lo.p);
+    PR_CUDA(cudaGetLastError());
+    const int blocks = std::max(1, sm_count() * (2048 / kFeatThreads));
+    features_kernel<S><<<blocks, kFeatThreads, 0, st>>>(g->d_off, g->d_src, (const float *)lo.p, n, hub_end, warp_end,
+                                                        (float)alpha, feat);
     PR_CUDA(cudaGetLastError());
     return PR_OK;
+}
+
+// training layout: n x kFS floats
+pr_status compute_features(const pr_graph *g, double alpha, float *feat, cudaStream_t st) {
+    return compute_features_t<kFS>(g, alpha, feat, st);
 }
 
 int mlp_grid(int32_t n) {
@@ -605,29 +793,32 @@ void free_mlp(pr_mlp *m) {
 
 }  // namespace
 
-// Start vector for (g, alpha): features -> MLP -> exp(y - max) / sum (caller order, device)
-pr_status pr_learned_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_out, cudaStream_t st) {
+// Start vector for (g, alpha): features -> MLP -> exp(y - max) / sum, FP64 on
+// the device, in relabelled order (relabelled = true) or caller order.
+// Stream-ordered: the caller synchronises when it needs the values on the host.
+pr_status pr_learned_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_out, bool relabelled,
+                           cudaStream_t st) {
     if (!pr_mlp_valid(m)) return pr_fail(PR_ESTATE, "not a live pr_mlp handle");
     if (!pr_graph_valid(g)) return pr_fail(PR_ESTATE, "not a live graph handle");
-    pr_status s = mlp_setup_smem();
-    if (s != PR_OK) return s;
     const int32_t n = g->n;
     DBuf feat, y, bmax, bsum;
-    if ((s = dmalloc(feat, (size_t)n * kFS * sizeof(float))) != PR_OK) return s;
-    if ((s = dmalloc(y, (size_t)n * sizeof(float))) != PR_OK) return s;
+    pr_status s;
+    const long long ntiles = ((long long)n + 15) / 16;
+    const int ictas = (int)std::max<long long>(
+        1, std::min<long long>((ntiles + kInferWarps - 1) / kInferWarps, (long long)sm_count() * 2));
     const int rb = grid_for(n, 256);
-    if ((s = dmalloc(bmax, rb * sizeof(float))) != PR_OK) return s;
-    if ((s = dmalloc(bsum, rb * sizeof(double))) != PR_OK) return s;
-    if ((s = compute_features(g, alpha, (float *)feat.p, st)) != PR_OK) return s;
-    mlp_forward_kernel<<<mlp_grid(n), kMlpThreads, sizeof(MlpShared), st>>>(m->d.master, m->d.wbf, (const float *)feat.p,
-                                                                          n, (float *)y.p);
+    if ((s = dmalloc(feat, (size_t)n * 4 * sizeof(float), st)) != PR_OK) return s;
+    if ((s = dmalloc(y, (size_t)n * sizeof(float), st)) != PR_OK) return s;
+    if ((s = dmalloc(bmax, ictas * sizeof(float), st)) != PR_OK) return s;
+    if ((s = dmalloc(bsum, rb * sizeof(double), st)) != PR_OK) return s;
+    if ((s = compute_features_t<4>(g, alpha, (float *)feat.p, st)) != PR_OK) return s;
+    mlp_infer_kernel<<<ictas, kInferThreads, 0, st>>>(m->d.master, m->d.wbf, (const float4 *)feat.p, n, (float)alpha,
+                                                      (float *)y.p, (float *)bmax.p);
     PR_CUDA(cudaGetLastError());
-    max_kernel<<<rb, 256, 0, st>>>((const float *)y.p, n, (float *)bmax.p);
-    expsum_kernel<<<rb, 256, 0, st>>>((const float *)y.p, n, (const float *)bmax.p, rb, (double *)bsum.p);
-    normalise_kernel<<<rb, 256, 0, st>>>((const float *)y.p, n, (const float *)bmax.p, (const double *)bsum.p, rb,
-                                         g->d_perm, d_out);
+    expsum_kernel<<<rb, 256, 0, st>>>((const float *)y.p, n, (const float *)bmax.p, ictas, (double *)bsum.p);
+    normalise_kernel<<<rb, 256, 0, st>>>((const float *)y.p, n, (const float *)bmax.p, ictas, (const double *)bsum.p,
+                                         rb, relabelled ? nullptr : g->d_perm, d_out);
     PR_CUDA(cudaGetLastError());
-    PR_CUDA(cudaStreamSynchronize(st));
     return PR_OK;
 }
 
@@ -687,7 +878,7 @@ extern "C" pr_status pr_features(const pr_graph *g, double alpha, float *d_feat_
     if (!d_feat_out) return pr_fail(PR_EINVAL, "d_feat_out is NULL");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     DBuf feat;
-    pr_status s = dmalloc(feat, (size_t)g->n * kFS * sizeof(float));
+    pr_status s = dmalloc(feat, (size_t)g->n * kFS * sizeof(float), st);
     if (s != PR_OK) return s;
     if ((s = compute_features(g, alpha, (float *)feat.p, st)) != PR_OK) return s;
     features_out_kernel<<<grid_for((long long)g->n * kF, 256), 256, 0, st>>>((const float *)feat.p, g->d_perm, g->n, d_feat_out);
@@ -700,7 +891,11 @@ extern "C" pr_status pr_mlp_warm_start(const pr_mlp *m, const pr_graph *g, doubl
     pr_clear_error();
     if (!d_r0_out) return pr_fail(PR_EINVAL, "d_r0_out is NULL");
     if (!(alpha >= 0.0 && alpha <= 1.0)) return pr_fail(PR_EINVAL, "alpha must be in [0, 1]");
-    return pr_learned_start(m, g, alpha, d_r0_out, reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    pr_status s = pr_learned_start(m, g, alpha, d_r0_out, false, st);
+    if (s != PR_OK) return s;
+    PR_CUDA(cudaStreamSynchronize(st));
+    return PR_OK;
 }
 
 extern "C" pr_status pr_mlp_loss_grad(const pr_mlp *m, const pr_graph *g, double alpha, const double *d_target_r,
@@ -712,9 +907,9 @@ extern "C" pr_status pr_mlp_loss_grad(const pr_mlp *m, const pr_graph *g, double
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int32_t n = g->n;
     DBuf feat, tgt;
-    pr_status s = dmalloc(feat, (size_t)n * kFS * sizeof(float));
+    pr_status s = dmalloc(feat, (size_t)n * kFS * sizeof(float), st);
     if (s != PR_OK) return s;
-    if ((s = dmalloc(tgt, (size_t)n * sizeof(float))) != PR_OK) return s;
+    if ((s = dmalloc(tgt, (size_t)n * sizeof(float), st)) != PR_OK) return s;
     if ((s = compute_features(g, alpha, (float *)feat.p, st)) != PR_OK) return s;
     targets_kernel<<<grid_for(n, 256), 256, 0, st>>>(d_target_r, g->d_perm, n, (float *)tgt.p);
     PR_CUDA(cudaGetLastError());
@@ -746,8 +941,8 @@ extern "C" pr_status pr_mlp_train(pr_mlp *m, const pr_graph *const *graphs, cons
     pr_status s;
     for (int i = 0; i < nsets; i++) {
         const int32_t n = graphs[i]->n;
-        if ((s = dmalloc(feats[i], (size_t)n * kFS * sizeof(float))) != PR_OK) return s;
-        if ((s = dmalloc(tgts[i], (size_t)n * sizeof(float))) != PR_OK) return s;
+        if ((s = dmalloc(feats[i], (size_t)n * kFS * sizeof(float), st)) != PR_OK) return s;
+        if ((s = dmalloc(tgts[i], (size_t)n * sizeof(float), st)) != PR_OK) return s;
         if ((s = compute_features(graphs[i], alphas[i], (float *)feats[i].p, st)) != PR_OK) return s;
         targets_kernel<<<grid_for(n, 256), 256, 0, st>>>(targets[i], graphs[i]->d_perm, n, (float *)tgts[i].p);
         PR_CUDA(cudaGetLastError());

@@ -50,15 +50,9 @@ cudaMemPool_t workspace_pool(int dev) {
 }
 
 struct Arena {
+    PoolBuf buf;
     char *base = nullptr;
     size_t size = 0;
-    cudaStream_t stream = nullptr;
-    bool pooled = false;
-    ~Arena() {
-        if (!base) return;
-        if (pooled) cudaFreeAsync(base, stream);
-        else cudaFree(base);
-    }
     size_t reserve(size_t bytes) {   // returns offset
         size_t off = (size + 255) & ~size_t(255);
         size = off + bytes;
@@ -66,29 +60,49 @@ struct Arena {
     }
     pr_status alloc(cudaStream_t st) {
         if (size == 0) size = 256;
-        stream = st;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaMemPool_t pool = workspace_pool(dev);
-        cudaError_t e = cudaErrorMemoryAllocation;
-        if (pool) {
-            e = cudaMallocFromPoolAsync((void **)&base, size, pool, st);
-            pooled = e == cudaSuccess;
-        }
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            e = cudaMalloc((void **)&base, size);
-        }
-        if (e != cudaSuccess) {
-            base = nullptr;
-            cudaGetLastError();
-            return pr_fail(e == cudaErrorMemoryAllocation ? PR_ENOMEM : PR_ECUDA,
-                           "device workspace of " + std::to_string(size) + " bytes: " + cudaGetErrorString(e));
-        }
-        return PR_OK;
+        pr_status s = buf.alloc(size, st);
+        base = static_cast<char *>(buf.p);
+        return s;
     }
     template <typename T> T *at(size_t off) { return reinterpret_cast<T *>(base + off); }
 };
+
+}  // namespace
+
+pr_status PoolBuf::alloc(size_t bytes, cudaStream_t st) {
+    release();
+    if (bytes == 0) bytes = 256;
+    stream = st;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool = workspace_pool(dev);
+    cudaError_t e = cudaErrorMemoryAllocation;
+    if (pool) {
+        e = cudaMallocFromPoolAsync(&p, bytes, pool, st);
+        pooled = e == cudaSuccess;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&p, bytes);
+    }
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return pr_fail(e == cudaErrorMemoryAllocation ? PR_ENOMEM : PR_ECUDA,
+                       "device workspace of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+    return PR_OK;
+}
+
+void PoolBuf::release() {
+    if (!p) return;
+    if (pooled) cudaFreeAsync(p, stream);
+    else cudaFree(p);
+    p = nullptr;
+    pooled = false;
+}
+
+namespace {
 
 template <typename V>
 void *iter_ptr(int W) {
@@ -645,7 +659,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
                 hist_at += sc.hist_cap;
             }
             cs.init_src = sc.init_dev;
-            cs.init_order = 0;
+            cs.init_order = sc.init_relabelled ? 1 : 0;
             cs.init_col_stride = 1;
             cs.init_col = 0;
             if (mixed) {
