@@ -74,8 +74,11 @@ constexpr int kVecGatherMinBlocks = PR_VEC_GATHER_MIN_BLOCKS;   // several colum
 // One column: in-edge indices loaded evict-first (read once per pass; 1-4 %
 // faster than default caching, measured).
 constexpr bool kStreamIndex = PR_STREAM_INDEX != 0;
-// Shared-memory carveout requested for kernels with dynamic shared memory
-// (percent; -1 leaves the driver's choice).
+// Shared-memory carveout of the iteration kernels: -1 (default) asks, for the
+// one-column gather kernel, for the smallest share of the unified L1/shared
+// storage that still holds as many CTAs per SM as the registers allow (the
+// rest caches the random gathers in L1) and leaves the driver's choice for the
+// others; -2 leaves the driver's choice everywhere; 0..100 forces a percentage.
 constexpr int kSmemCarveout = PR_SMEM_CARVEOUT;
 constexpr int kTileValues = PR_TILE_VALUES;
 // Resident CTAs per SM asked of the compiler for W > 1, by value size: with

@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
     const int ntiles = job.ntiles, cta_count = kGather ? job.gcta_count : job.cta_count;
     __shared__ V s_vals[kWarps][kStaged ? VT : 1];
     __shared__ V s_prev[kWarps][kStaged && !kGather ? TR * W : 1];
-    __shared__ int32_t s_off[kWarps][kStaged ? TR + 1 : 1];
+    constexpr int kOffRegs = kStaged ? TR / 32 + 1 : 1;   // one column: row offsets held in registers
     __shared__ int32_t s_od[kWarps][kStaged && !kGather ? TR : 1];
     __shared__ V s_sum[kWarps][kStaged && kTU && !kGather ? TR : 1];
     // several columns: per-warp buffers in dynamic shared memory
@@ -561,7 +561,13 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                     const int idx = lane + 32 * k;
                     u[k] = (cv.active && idx < ne * W) ? ld_idx(src + T.e0 + idx / W) : -1;
                 }
-                for (int i = lane; i <= nr; i += 32) s_off[warp][i] = off[T.r0 + i] - T.e0;
+                // row offsets relative to e0 in registers: lane l holds rows l, l + 32, ...
+                int32_t o[kOffRegs];
+#pragma unroll
+                for (int j = 0; j < kOffRegs; j++) {
+                    const int i = lane + 32 * j;
+                    o[j] = i <= nr ? off[T.r0 + i] - T.e0 : 0;
+                }
                 // element i of the rows belongs to column i % W == lane % W
                 if constexpr (!kGather) {
                     if (need_prev)
@@ -584,10 +590,23 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                 for (int rb = 0; rb < nr; rb += rpp) {
                     const int r = rb + (lane >> T.glog);
                     const bool valid = r < nr;
+                    // rows r and r + 1 lie in [rb, rb + 32]: registers j0 and j0 + 1 of their lanes
+                    const int j0 = rb >> 5;
+                    int32_t oa = o[0], ob = o[kOffRegs > 1 ? 1 : 0];
+#pragma unroll
+                    for (int j = 1; j + 1 < kOffRegs; j++) {
+                        if (j0 == j) {
+                            oa = o[j];
+                            ob = o[j + 1];
+                        }
+                    }
+                    const int32_t la = __shfl_sync(0xffffffffu, oa, r & 31), lb = __shfl_sync(0xffffffffu, ob, r & 31);
+                    const int32_t ha = __shfl_sync(0xffffffffu, oa, (r + 1) & 31),
+                                  hb = __shfl_sync(0xffffffffu, ob, (r + 1) & 31);
                     EdgeSum<V> sum;
                     sum.init();
                     if (valid && cv.active) {
-                        const int lo = s_off[warp][r], hi = s_off[warp][r + 1];
+                        const int lo = (r >> 5) == j0 ? la : lb, hi = ((r + 1) >> 5) == j0 ? ha : hb;
                         for (int e = lo + es; e < hi; e += ES) sum.add(s_vals[warp][e * W + col]);
                     }
                     V sv = sum.get();
