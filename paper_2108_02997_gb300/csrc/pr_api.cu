@@ -73,9 +73,6 @@ extern "C" void pr_options_default(pr_options *opt) {
 }
 
 // Implemented in pr_learn.cu.
-pr_status pr_learned_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_out, bool relabelled,
-                           cudaStream_t st);
-bool pr_mlp_valid(const pr_mlp *m);
 
 namespace {
 
@@ -134,6 +131,7 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
     std::vector<std::unique_ptr<PoolBuf>> bufs;
     std::map<std::pair<const void *, const void *>, const double *> init_dev;   // (graph, src) -> device copy
     std::map<std::pair<const pr_graph *, uint64_t>, const double *> learned;
+    std::map<const pr_graph *, const void *> learned_feat;
     auto start_for = [&](const pr_instance &in, const double **out) -> pr_status {
         *out = nullptr;
         if (opt.init == PR_INIT_UNIFORM) return PR_OK;
@@ -157,10 +155,19 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
         auto key = std::make_pair(in.g, abits);
         auto it = learned.find(key);
         if (it != learned.end()) { *out = it->second; return PR_OK; }
+        // the features depend on the graph only: one pass per graph serves every alpha
+        auto fit = learned_feat.find(in.g);
+        if (fit == learned_feat.end()) {
+            bufs.emplace_back(new PoolBuf());
+            pr_status fs = bufs.back()->alloc(pr_learned_features_bytes(in.g), st);
+            if (fs == PR_OK) fs = pr_learned_features(in.g, bufs.back()->p, st);
+            if (fs != PR_OK) return fs;
+            fit = learned_feat.emplace(in.g, bufs.back()->p).first;
+        }
         bufs.emplace_back(new PoolBuf());
         pr_status ls = bufs.back()->alloc(bytes, st);
         if (ls != PR_OK) return ls;
-        ls = pr_learned_start(opt.mlp, in.g, in.alpha, (double *)bufs.back()->p, true, st);
+        ls = pr_learned_start(opt.mlp, in.g, in.alpha, (double *)bufs.back()->p, true, st, fit->second);
         if (ls != PR_OK) return ls;
         *out = (const double *)bufs.back()->p;
         learned[key] = *out;

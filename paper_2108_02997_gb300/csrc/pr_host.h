@@ -126,6 +126,18 @@ struct PoolBuf {
     void release();
 };
 
+// Learned warm start (pr_learn.cu). The features of the network's input
+// depend on the graph only (alpha enters the network separately), so a batch
+// computes them once per graph: pr_learned_features writes them (relabelled
+// order, pr_learned_features_bytes(g) bytes) and pr_learned_start takes them
+// (or computes its own when feat is null). The start vector is FP64 on the
+// device, in relabelled order when `relabelled`, else caller order.
+bool pr_mlp_valid(const pr_mlp *m);
+size_t pr_learned_features_bytes(const pr_graph *g);
+pr_status pr_learned_features(const pr_graph *g, void *feat, cudaStream_t st);
+pr_status pr_learned_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_out, bool relabelled,
+                           cudaStream_t st, const void *feat = nullptr);
+
 // Live-handle registry: guards every entry point against stale handles.
 void registry_add(const void *p);
 void registry_remove(const void *p);

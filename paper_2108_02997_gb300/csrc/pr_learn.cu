@@ -11,7 +11,9 @@
 // dW2 = dZ2^T H1) run on tensor cores with warp-level mma.sync m16n8k16
 // (BF16 inputs, FP32 accumulation); the 5-wide first layer and the 64-wide
 // output layer run on CUDA cores in FP32; biases FP32. Gradients are summed
-// per CTA and then over CTAs in a fixed order (deterministic).
+// per CTA and then over CTAs in a fixed order (deterministic). Training uses
+// the exact (erf) GELU; inference, which only has to produce a start vector,
+// evaluates GELU by its tanh approximation on the hardware tanh.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -55,6 +57,19 @@ namespace {
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU by its tanh approximation (Hendrycks and Gimpel, 2016),
+// 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))), with the hardware
+// tanh.approx.f32 (one special-function instruction instead of an erf). The
+// form is within 4.8e-4 of the exact GELU; with the approximate tanh the
+// difference stays far below the BF16 rounding of the hidden activations.
+// Used by inference only; training differentiates the exact form.
+__device__ __forceinline__ float gelu_tanh(float x) {
+    const float u = x * fmaf(0.0356774081f * x, x, 0.7978845608f);
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+    const float hx = 0.5f * x;
+    return fmaf(hx, t, hx);
+}
 __device__ __forceinline__ float gelu_grad(float x) {
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
@@ -312,8 +327,8 @@ __global__ void targets_kernel(const double *r_caller, const int32_t *perm, int3
 // entries its mma.sync A fragments hold (rows g and g+8, columns 2t, 2t+1,
 // 2t+8, 2t+9 of each 16-column block) straight into registers, so only the
 // weights sit in shared memory and no CTA-wide barrier separates the layers.
-// The arithmetic, and its order, is that of block_forward. Each CTA also
-// writes the largest y it produced (for the softmax).
+// The arithmetic, and its order, is that of block_forward, with GELU evaluated
+// by gelu_tanh. Each CTA also writes the largest y it produced (for the softmax).
 constexpr int kInferThreads = 256;
 constexpr int kInferWarps = kInferThreads / 32;
 
@@ -381,8 +396,8 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const float
                 zb = fmaf(w.w, fb.w, zb);
                 za = fmaf(wa, ra < n ? alpha : 0.0f, za);
                 zb = fmaf(wa, rb < n ? alpha : 0.0f, zb);
-                ha[q] = gelu(za);
-                hb[q] = gelu(zb);
+                ha[q] = gelu_tanh(za);
+                hb[q] = gelu_tanh(zb);
             }
             const uint32_t a[4] = {pack_bf16(ha[0], ha[1]), pack_bf16(hb[0], hb[1]), pack_bf16(ha[2], ha[3]),
                                    pack_bf16(hb[2], hb[3])};
@@ -397,10 +412,10 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const float
 #pragma unroll
         for (int nt = 0; nt < 8; nt++) {
             const int j = nt * 8 + 2 * t;
-            ylo = fmaf(gelu(c2[nt][0] + S.b2[j]), S.w3[j], ylo);
-            ylo = fmaf(gelu(c2[nt][1] + S.b2[j + 1]), S.w3[j + 1], ylo);
-            yhi = fmaf(gelu(c2[nt][2] + S.b2[j]), S.w3[j], yhi);
-            yhi = fmaf(gelu(c2[nt][3] + S.b2[j + 1]), S.w3[j + 1], yhi);
+            ylo = fmaf(gelu_tanh(c2[nt][0] + S.b2[j]), S.w3[j], ylo);
+            ylo = fmaf(gelu_tanh(c2[nt][1] + S.b2[j + 1]), S.w3[j + 1], ylo);
+            yhi = fmaf(gelu_tanh(c2[nt][2] + S.b2[j]), S.w3[j], yhi);
+            yhi = fmaf(gelu_tanh(c2[nt][3] + S.b2[j + 1]), S.w3[j + 1], yhi);
         }
         ylo += __shfl_xor_sync(0xffffffffu, ylo, 1);
         yhi += __shfl_xor_sync(0xffffffffu, yhi, 1);
@@ -793,26 +808,35 @@ void free_mlp(pr_mlp *m) {
 
 }  // namespace
 
-// Start vector for (g, alpha): features -> MLP -> exp(y - max) / sum, FP64 on
-// the device, in relabelled order (relabelled = true) or caller order.
+size_t pr_learned_features_bytes(const pr_graph *g) { return (size_t)g->n * 4 * sizeof(float); }
+
+// inference layout: n rows of 4 floats (alpha passed to the network kernel)
+pr_status pr_learned_features(const pr_graph *g, void *feat, cudaStream_t st) {
+    return compute_features_t<4>(g, 0.0, static_cast<float *>(feat), st);
+}
+
+// Start vector for (g, alpha): features -> MLP -> exp(y - max) / sum.
 // Stream-ordered: the caller synchronises when it needs the values on the host.
 pr_status pr_learned_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_out, bool relabelled,
-                           cudaStream_t st) {
+                           cudaStream_t st, const void *feat_in) {
     if (!pr_mlp_valid(m)) return pr_fail(PR_ESTATE, "not a live pr_mlp handle");
     if (!pr_graph_valid(g)) return pr_fail(PR_ESTATE, "not a live graph handle");
     const int32_t n = g->n;
     DBuf feat, y, bmax, bsum;
     pr_status s;
+    if (!feat_in) {
+        if ((s = dmalloc(feat, pr_learned_features_bytes(g), st)) != PR_OK) return s;
+        if ((s = pr_learned_features(g, feat.p, st)) != PR_OK) return s;
+        feat_in = feat.p;
+    }
     const long long ntiles = ((long long)n + 15) / 16;
     const int ictas = (int)std::max<long long>(
         1, std::min<long long>((ntiles + kInferWarps - 1) / kInferWarps, (long long)sm_count() * 2));
     const int rb = grid_for(n, 256);
-    if ((s = dmalloc(feat, (size_t)n * 4 * sizeof(float), st)) != PR_OK) return s;
     if ((s = dmalloc(y, (size_t)n * sizeof(float), st)) != PR_OK) return s;
     if ((s = dmalloc(bmax, ictas * sizeof(float), st)) != PR_OK) return s;
     if ((s = dmalloc(bsum, rb * sizeof(double), st)) != PR_OK) return s;
-    if ((s = compute_features_t<4>(g, alpha, (float *)feat.p, st)) != PR_OK) return s;
-    mlp_infer_kernel<<<ictas, kInferThreads, 0, st>>>(m->d.master, m->d.wbf, (const float4 *)feat.p, n, (float)alpha,
+    mlp_infer_kernel<<<ictas, kInferThreads, 0, st>>>(m->d.master, m->d.wbf, (const float4 *)feat_in, n, (float)alpha,
                                                       (float *)y.p, (float *)bmax.p);
     PR_CUDA(cudaGetLastError());
     expsum_kernel<<<rb, 256, 0, st>>>((const float *)y.p, n, (const float *)bmax.p, ictas, (double *)bsum.p);

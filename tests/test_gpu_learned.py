@@ -70,6 +70,44 @@ def test_warm_start_matches_oracle_forward(B, orc, setup):
     m.close()
 
 
+@pytest.fixture(scope="module")
+def tiered(B, gg):
+    """R-MAT scale 13 plus three hub vertices with 2,100, 4,000 and 8,000
+    in-edges: rows for every feature worker size (a CTA per row from 2,048
+    in-edges, a warp per row from 32, a thread per row below, empty rows)."""
+    base = gg.rmat(13, 8, seed=43)
+    s, d = base.edges()
+    extra_s, extra_d = [], []
+    for hub, k in ((11, 2100), (222, 4000), (3333, 8000)):
+        srcs = (np.arange(k, dtype=np.int64) * 7 + hub + 1) % base.n
+        srcs = srcs[srcs != hub]
+        extra_s.append(srcs)
+        extra_d.append(np.full(srcs.size, hub))
+    g = gg.from_edges(base.n, np.concatenate([s] + extra_s), np.concatenate([d] + extra_d))
+    deg = np.diff(g.offsets)
+    assert (deg >= 2048).sum() >= 3 and ((deg >= 32) & (deg < 2048)).any() and (deg == 0).any()
+    return g, B.Graph.from_csr(g)
+
+
+def test_features_every_worker_size(B, orc, tiered):
+    g, dg = tiered
+    f = B.pr_features(dg, 0.9).cpu().numpy()
+    ref = orc.features(g, 0.9)
+    assert np.abs(f - ref).max() <= 2e-6 * max(1.0, np.abs(ref).max())
+
+
+def test_warm_start_every_worker_size(B, orc, tiered):
+    g, dg = tiered
+    flat = B.init_mlp_params(seed=9)
+    m = B.MLP(flat)
+    r0 = m.warm_start(dg, 0.6).cpu().numpy()
+    y, _ = orc.mlp_forward(orc.features(g, 0.6), oracle_params(orc, flat))
+    ref = orc.warm_start_from_logits(y)
+    assert abs(r0.sum() - 1.0) < 1e-12
+    assert np.abs(r0 - ref).sum() <= 2e-2, np.abs(r0 - ref).sum()
+    m.close()
+
+
 def test_gradients_match_oracle(B, orc, setup):
     g, dg, ref_r, target = setup
     flat = B.init_mlp_params(seed=6)
