@@ -12,7 +12,6 @@
 //     low ids, so their cache lines are shared instead of scattered.
 // Rank vectors cross the ABI in caller order; the kernels map through perm.
 #include <algorithm>
-#include <atomic>
 #include <cstring>
 #include <system_error>
 #include <thread>
@@ -81,6 +80,84 @@ bool pr_graph_valid(const pr_graph *g) { return g && registry_has(g) && g->magic
 // per column group), es sized so that each lane adds about four in-edges.
 // Classes with rows longer than tile_edges(W) are cut into chunks of
 // chunk_edges(W) in-edges, each chunk a warp's tile.
+namespace {
+
+// Tile builder segment: rows [r0, r1) of one in-degree class, tiled
+// independently of the other segments (a rows tile never spans two segments;
+// a row's sum does not depend on the tile it sits in). glog >= 0: rows tiles
+// with 2^glog lanes per row; -1: the class's rows are cut into chunks.
+struct TileSeg {
+    int32_t r0, r1, glog;
+};
+constexpr int32_t kSegRows = 1024;
+
+// One thread per segment. Pass 1 (kWrite = false) counts the segment's tiles,
+// chunk partial slots and long rows (cnt, 3 per segment); pass 2 writes them
+// from the segment's exclusive sums (base, 3 per segment): tiles in row order,
+// and for every row cut into several chunks its long-row index (the chunks'
+// slot) and its first chunk partial (slot_base).
+template <bool kWrite>
+__global__ void tile_segments_kernel(const TileSeg *__restrict__ segs, int32_t nseg, const int32_t *__restrict__ off,
+                                     int TE, int TR, int CH, int32_t *__restrict__ cnt,
+                                     const int64_t *__restrict__ base, Tile *__restrict__ tiles,
+                                     int32_t *__restrict__ slot_base) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nseg) return;
+    const TileSeg sg = segs[i];
+    int64_t nt = 0, ns = 0, nl = 0;
+    const int64_t t0 = kWrite ? base[3 * (int64_t)i] : 0;
+    const int64_t s0 = kWrite ? base[3 * (int64_t)i + 1] : 0;
+    const int64_t l0 = kWrite ? base[3 * (int64_t)i + 2] : 0;
+    if (sg.glog < 0) {
+        for (int32_t v = sg.r0; v < sg.r1; v++) {
+            const int32_t e0 = off[v], e1 = off[v + 1];
+            const int32_t nch = max(1, (e1 - e0 + CH - 1) / CH);
+            int32_t slot = -1;
+            if (nch > 1) {
+                slot = (int32_t)(l0 + nl);
+                if (kWrite) slot_base[slot] = (int32_t)(s0 + ns);
+                ns += nch;
+                nl++;
+            }
+            if (kWrite)
+                for (int32_t k = 0; k < nch; k++) {
+                    const int32_t a = e0 + k * CH;
+                    tiles[t0 + nt + k] = Tile{v, v + 1, a, min(e1, a + CH), -1, slot, k, nch};
+                }
+            nt += nch;
+        }
+    } else {
+        int32_t r = sg.r0;
+        while (r < sg.r1) {
+            const int32_t e0 = off[r];
+            int32_t r1 = r;
+            while (r1 < sg.r1 && r1 - r < TR && off[r1 + 1] - e0 <= TE) r1++;
+            if (r1 == r) r1 = r + 1;   // cannot happen (in-degree <= TE), kept for safety
+            if (kWrite) tiles[t0 + nt] = Tile{r, r1, e0, off[r1], sg.glog, -1, 0, 0};
+            nt++;
+            r = r1;
+        }
+    }
+    if (!kWrite) {
+        cnt[3 * (int64_t)i] = (int32_t)nt;
+        cnt[3 * (int64_t)i + 1] = (int32_t)ns;
+        cnt[3 * (int64_t)i + 2] = (int32_t)nl;
+    }
+}
+
+struct TmpBuf {
+    void *p = nullptr;
+    ~TmpBuf() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+// Work table of width W, built on the device from the relabelled offsets:
+// classes whose rows fit a rows tile (at most tile_edges(W) in-edges) get
+// rows tiles of consecutive rows (at most tile_rows(W) rows and
+// tile_edges(W) in-edges each), lanes per row the smallest power of two
+// (at most 32) with four in-edges per lane for the class's longest row; the
+// other classes get chunks of chunk_edges(W) in-edges per row.
 pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     int wi = w_index(W);
     if (wi < 0) return pr_fail(PR_EINVAL, "unsupported column width");
@@ -91,118 +168,69 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     }
     const int TE = tile_edges(W), TR = tile_rows(W), CH = chunk_edges(W);
     const int max_es = 32;
-    const std::vector<int32_t> &off = g->h_off;
-    // Work items: slices of at most kSliceRows rows of one class, tiled
-    // independently (a rows tile never spans two slices; a row's sum does not
-    // depend on the tile it sits in) on up to 16 host threads, then merged in
-    // order with the chunk slots renumbered.
-    constexpr int32_t kSliceRows = 1 << 18;
-    struct Slice {
-        const ClassRange *cr;
-        int32_t r0, r1;
-        std::vector<Tile> tiles;
-        std::vector<int32_t> slot_base;   // local chunk-slot offsets
-        int32_t n_chunk_slots = 0;
-        double work = 0.0;
-    };
-    std::vector<Slice> slices;
-    for (const ClassRange &cr : g->classes)
-        for (int32_t r = cr.begin; r < cr.end; r += kSliceRows) {
-            Slice sl;
-            sl.cr = &cr;
-            sl.r0 = r;
-            sl.r1 = (int32_t)std::min<int64_t>((int64_t)r + kSliceRows, cr.end);
-            slices.push_back(std::move(sl));
-        }
-    auto build_slice = [&](Slice &sl) {
-        const ClassRange &cr = *sl.cr;
-        if (cr.max_deg > TE) {
-            for (int32_t v = sl.r0; v < sl.r1; v++) {
-                int32_t e0 = off[v], e1 = off[v + 1];
-                int32_t deg = e1 - e0;
-                int32_t nch = std::max<int32_t>(1, (deg + CH - 1) / CH);
-                int32_t slot = -1;
-                if (nch > 1) {
-                    slot = (int32_t)sl.slot_base.size();
-                    sl.slot_base.push_back(sl.n_chunk_slots);
-                    sl.n_chunk_slots += nch;
-                }
-                for (int32_t k = 0; k < nch; k++) {
-                    int32_t a = e0 + k * CH, b = std::min(e1, a + CH);
-                    sl.tiles.push_back({v, v + 1, a, b, -1, slot, k, nch});
-                }
-                sl.work += (double)deg * W + W * 4.0;
+    std::vector<TileSeg> segs;
+    try {
+        for (const ClassRange &cr : g->classes) {
+            int glog = -1;
+            if (cr.max_deg <= TE) {
+                int es = 1;
+                while (es < max_es && es * 4 < cr.max_deg) es <<= 1;
+                glog = 0;
+                while ((1 << glog) < es) glog++;
             }
-            return;
+            for (int32_t r = cr.begin; r < cr.end; r += kSegRows)
+                segs.push_back(TileSeg{r, (int32_t)std::min<int64_t>((int64_t)r + kSegRows, cr.end), glog});
         }
-        int es = 1;
-        while (es < max_es && es * 4 < cr.max_deg) es <<= 1;
-        int glog = 0;
-        while ((1 << glog) < es) glog++;
-        int32_t r = sl.r0;
-        while (r < sl.r1) {
-            int32_t r1 = r;
-            while (r1 < sl.r1 && r1 - r < TR && off[r1 + 1] - off[r] <= TE) r1++;
-            if (r1 == r) r1 = r + 1;   // cannot happen (deg <= TE), kept for safety
-            sl.tiles.push_back({r, r1, off[r], off[r1], glog, -1, 0, 0});
-            sl.work += (double)(off[r1] - off[r]) * W + (double)(r1 - r) * W * 4.0;
-            r = r1;
-        }
-    };
-    {
-        const unsigned int hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-        const size_t nthreads = std::min<size_t>(hw, slices.size());
-        std::atomic<size_t> next{0};
-        auto worker = [&]() {
-            for (size_t i = next++; i < slices.size(); i = next++) build_slice(slices[i]);
-        };
-        std::vector<std::thread> pool;
-        try {
-            for (size_t k = 1; k < nthreads; k++) pool.emplace_back(worker);
-        } catch (const std::system_error &) {
-            // fewer threads: the calling thread does the rest
-        }
-        worker();
-        for (auto &th : pool) th.join();
+    } catch (const std::bad_alloc &) {
+        return pr_fail(PR_ENOMEM, "host allocation failed");
     }
-    std::vector<Tile> tiles;
-    std::vector<int32_t> slot_base;
-    int32_t n_chunk_slots = 0;
-    double work = 0.0;
-    {
-        size_t nt_total = 0;
-        for (auto &sl : slices) nt_total += sl.tiles.size();
-        tiles.reserve(nt_total);
+    const int32_t nseg = (int32_t)segs.size();
+    std::vector<int32_t> cnt((size_t)nseg * 3 + 3, 0);
+    std::vector<int64_t> base((size_t)nseg * 3 + 3, 0);
+    TmpBuf d_segs, d_cnt, d_base;
+    cudaError_t e = cudaMalloc(&d_segs.p, sizeof(TileSeg) * (size_t)std::max(nseg, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_cnt.p, sizeof(int32_t) * cnt.size());
+    if (e == cudaSuccess) e = cudaMalloc(&d_base.p, sizeof(int64_t) * base.size());
+    if (e == cudaSuccess && nseg > 0)
+        e = cudaMemcpy(d_segs.p, segs.data(), sizeof(TileSeg) * (size_t)nseg, cudaMemcpyHostToDevice);
+    const int blocks = std::max(1, (nseg + 127) / 128);
+    if (e == cudaSuccess && nseg > 0) {
+        tile_segments_kernel<false><<<blocks, 128>>>(static_cast<const TileSeg *>(d_segs.p), nseg, g->d_off, TE, TR, CH,
+                                                     static_cast<int32_t *>(d_cnt.p), nullptr, nullptr, nullptr);
+        e = cudaGetLastError();
     }
-    for (auto &sl : slices) {
-        const int32_t slot_shift = (int32_t)slot_base.size();
-        for (Tile t : sl.tiles) {
-            if (t.slot >= 0) t.slot += slot_shift;
-            tiles.push_back(t);
+    if (e == cudaSuccess) e = cudaMemcpy(cnt.data(), d_cnt.p, sizeof(int32_t) * (size_t)nseg * 3, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return pr_cuda_fail(e, "tile table (count)");
+    int64_t tot[3] = {0, 0, 0};
+    for (int32_t i = 0; i < nseg; i++)
+        for (int c = 0; c < 3; c++) {
+            base[3 * (size_t)i + c] = tot[c];
+            tot[c] += cnt[3 * (size_t)i + c];
         }
-        for (int32_t b : sl.slot_base) slot_base.push_back(b + n_chunk_slots);
-        n_chunk_slots += sl.n_chunk_slots;
-        work += sl.work;
-    }
+    if (tot[0] > INT32_MAX || tot[1] > INT32_MAX) return pr_fail(PR_EINVAL, "graph needs more than 2^31 work tiles");
     TileTable nt;
     nt.W = W;
-    nt.ntiles = (int32_t)tiles.size();
-    nt.n_long = (int32_t)slot_base.size();
-    nt.n_chunk_slots = n_chunk_slots;
-    nt.work = work;
-    pr_status s = dalloc(&nt.d_tiles, tiles.size());
+    nt.ntiles = (int32_t)tot[0];
+    nt.n_chunk_slots = (int32_t)tot[1];
+    nt.n_long = (int32_t)tot[2];
+    // every row adds its in-edges and a fixed per-row cost, W columns each
+    nt.work = ((double)g->nnz + 4.0 * (double)g->n) * W;
+    pr_status s = dalloc(&nt.d_tiles, (size_t)nt.ntiles);
     if (s != PR_OK) return s;
-    s = dalloc(&nt.d_slot_base, slot_base.size());
+    s = dalloc(&nt.d_slot_base, (size_t)nt.n_long);
     if (s != PR_OK) { cudaFree(nt.d_tiles); return s; }
-    cudaError_t e = cudaSuccess;
-    if (!tiles.empty())
-        e = cudaMemcpy(nt.d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !slot_base.empty())
-        e = cudaMemcpy(nt.d_slot_base, slot_base.data(), slot_base.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(d_base.p, base.data(), sizeof(int64_t) * (size_t)nseg * 3, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nseg > 0) {
+        tile_segments_kernel<true><<<blocks, 128>>>(static_cast<const TileSeg *>(d_segs.p), nseg, g->d_off, TE, TR, CH,
+                                                    nullptr, static_cast<const int64_t *>(d_base.p), nt.d_tiles,
+                                                    nt.d_slot_base);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(nt.d_tiles);
         cudaFree(nt.d_slot_base);
-        return pr_cuda_fail(e, "cudaMemcpy tiles");
+        return pr_cuda_fail(e, "tile table (write)");
     }
     t = nt;
     *out = &t;
@@ -363,6 +391,12 @@ __global__ void relabel_degrees_kernel(const int32_t *__restrict__ perm, const i
 
 // First relabelled row of every in-degree class (in-key ik = 32 - class),
 // read from the scanned key counts: bucket (ik, out-key 0) of chunk 0.
+// out[ik] = off[starts[ik]] for the 33 in-key classes, out[33] = off[n]
+__global__ void class_bounds_kernel(const int32_t *off, const int32_t *starts, int32_t n, int32_t *out) {
+    const int ik = threadIdx.x;
+    if (ik < kClasses) out[ik] = off[min(max(starts[ik], 0), n)];
+    if (ik == kClasses) out[ik] = off[n];
+}
 __global__ void class_starts_kernel(const int32_t *__restrict__ Mscan, int32_t nchunks, int32_t *__restrict__ starts) {
     const int ik = threadIdx.x;
     if (ik < kClasses) starts[ik] = Mscan[(int64_t)ik * kClasses * nchunks];
@@ -604,15 +638,17 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
         class_starts_kernel<<<1, 64>>>(Ms, nchunks, static_cast<int32_t *>(d_starts.p));
         e = cudaMemcpy(g->d_off + n, &total, sizeof(int32_t), cudaMemcpyHostToDevice);
     }
-    std::vector<int32_t> new_off;
-    int32_t h_starts[kClasses], h_cmax[kClasses];
-    try {
-        new_off.resize((size_t)n + 1);
-    } catch (const std::bad_alloc &) {
-        free_graph(g);
-        return pr_fail(PR_ENOMEM, "host allocation failed");
+    // the new offsets at the class starts (and at n), for the signature
+    int32_t h_starts[kClasses], h_cmax[kClasses], h_bound[kClasses + 1];
+    DevTmp d_bound;
+    if (e == cudaSuccess) {
+        e = cudaMalloc(&d_bound.p, sizeof(h_bound));
+        if (e == cudaSuccess) {
+            class_bounds_kernel<<<1, 64>>>(g->d_off, static_cast<const int32_t *>(d_starts.p), n,
+                                           static_cast<int32_t *>(d_bound.p));
+            e = cudaMemcpy(h_bound, d_bound.p, sizeof(h_bound), cudaMemcpyDeviceToHost);
+        }
     }
-    if (e == cudaSuccess) e = cudaMemcpy(new_off.data(), g->d_off, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(h_starts, d_starts.p, sizeof(h_starts), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(h_cmax, d_cmax.p, sizeof(h_cmax), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && nnz > 0) {
@@ -653,15 +689,16 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
         };
         mix((uint64_t)n);
         mix((uint64_t)nnz);
-        for (const ClassRange &cr : g->classes) {
-            mix((uint64_t)cr.begin);
-            mix((uint64_t)cr.end);
-            mix((uint64_t)cr.max_deg);
-            mix((uint64_t)(new_off[cr.end] - new_off[cr.begin]));
+        for (int ik = 0; ik < kClasses; ik++) {
+            const int32_t begin = h_starts[ik], end = ik + 1 < kClasses ? h_starts[ik + 1] : n;
+            if (end <= begin) continue;
+            mix((uint64_t)begin);
+            mix((uint64_t)end);
+            mix((uint64_t)h_cmax[32 - ik]);
+            mix((uint64_t)(h_bound[ik + 1] - h_bound[ik]));
         }
         g->signature = h;
     }
-    g->h_off.swap(new_off);
     // the single-column work table is built now so that solves on this graph
     // never need to allocate it later
     const TileTable *t1 = nullptr;

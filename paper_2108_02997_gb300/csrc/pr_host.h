@@ -24,7 +24,6 @@ struct pr_graph {
     int32_t *d_perm = nullptr;       // relabelled -> caller
     int32_t *d_inv = nullptr;        // caller -> relabelled
     std::vector<ClassRange> classes; // in-degree classes in relabelled order
-    std::vector<int32_t> h_off;      // relabelled offsets (host copy, for tile tables)
     TileTable tables[6];             // W = 1, 2, 4, 8, 16, 32
     uint64_t signature = 0;          // hash of n, nnz and the in-degree class layout
 };
