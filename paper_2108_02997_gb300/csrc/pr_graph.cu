@@ -82,6 +82,19 @@ bool pr_graph_valid(const pr_graph *g) { return g && registry_has(g) && g->magic
 // chunk_edges(W) in-edges, each chunk a warp's tile.
 namespace {
 
+// Temporary device buffer of graph creation, taken from the stream-ordered
+// workspace pool on the default stream, so that repeated creations reuse the
+// memory instead of paying cudaMalloc and a synchronising cudaFree.
+struct DevTmp {
+    PoolBuf b;
+    void *p = nullptr;
+    cudaError_t alloc(size_t bytes) {
+        if (b.alloc(bytes, 0) != PR_OK) return cudaErrorMemoryAllocation;
+        p = b.p;
+        return cudaSuccess;
+    }
+};
+
 // Tile builder segment: rows [r0, r1) of one in-degree class, tiled
 // independently of the other segments (a rows tile never spans two segments;
 // a row's sum does not depend on the tile it sits in). glog >= 0: rows tiles
@@ -145,10 +158,6 @@ __global__ void tile_segments_kernel(const TileSeg *__restrict__ segs, int32_t n
     }
 }
 
-struct TmpBuf {
-    void *p = nullptr;
-    ~TmpBuf() { if (p) cudaFree(p); }
-};
 
 }  // namespace
 
@@ -187,10 +196,10 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     const int32_t nseg = (int32_t)segs.size();
     std::vector<int32_t> cnt((size_t)nseg * 3 + 3, 0);
     std::vector<int64_t> base((size_t)nseg * 3 + 3, 0);
-    TmpBuf d_segs, d_cnt, d_base;
-    cudaError_t e = cudaMalloc(&d_segs.p, sizeof(TileSeg) * (size_t)std::max(nseg, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&d_cnt.p, sizeof(int32_t) * cnt.size());
-    if (e == cudaSuccess) e = cudaMalloc(&d_base.p, sizeof(int64_t) * base.size());
+    DevTmp d_segs, d_cnt, d_base;
+    cudaError_t e = d_segs.alloc(sizeof(TileSeg) * (size_t)std::max(nseg, 1));
+    if (e == cudaSuccess) e = d_cnt.alloc(sizeof(int32_t) * cnt.size());
+    if (e == cudaSuccess) e = d_base.alloc(sizeof(int64_t) * base.size());
     if (e == cudaSuccess && nseg > 0)
         e = cudaMemcpy(d_segs.p, segs.data(), sizeof(TileSeg) * (size_t)nseg, cudaMemcpyHostToDevice);
     const int blocks = std::max(1, (nseg + 127) / 128);
@@ -476,10 +485,6 @@ int blocks_for(int64_t work, int threads) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 16));
 }
 
-struct DevTmp {
-    void *p = nullptr;
-    ~DevTmp() { if (p) cudaFree(p); }
-};
 
 // out[i] = in[0] + .. + in[i-1] for i < len (int32; the caller guarantees the
 // total fits); sums: scratch of at least ceil(len / kScanTile) int32.
@@ -566,11 +571,11 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
         free_graph(g);
         return s;
     }
-    e = cudaMalloc(&d_old_off.p, sizeof(int32_t) * ((size_t)n + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&d_old_src.p, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&d_old_od.p, sizeof(int32_t) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMalloc(&d_cnt.p, sizeof(int32_t) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMalloc(&d_bad.p, 2 * sizeof(unsigned long long));
+    e = d_old_off.alloc(sizeof(int32_t) * ((size_t)n + 1));
+    if (e == cudaSuccess) e = d_old_src.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1));
+    if (e == cudaSuccess) e = d_old_od.alloc(sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess) e = d_cnt.alloc(sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess) e = d_bad.alloc(2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(d_old_off.p, in_offsets, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(d_old_src.p, in_sources, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(d_cnt.p, 0, sizeof(int32_t) * (size_t)n);
@@ -609,13 +614,13 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     const int64_t mlen = (int64_t)kKeys * nchunks;
     const int64_t nsums = std::max<int64_t>((mlen + kScanTile - 1) / kScanTile, ((int64_t)n + kScanTile - 1) / kScanTile);
     DevTmp d_key, d_M, d_Ms, d_sums, d_cmax, d_starts, d_newdeg;
-    e = cudaMalloc(&d_key.p, sizeof(int32_t) * (size_t)n);
+    e = d_key.alloc(sizeof(int32_t) * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&d_M.p, sizeof(int32_t) * (size_t)mlen);
     if (e == cudaSuccess) e = cudaMalloc(&d_Ms.p, sizeof(int32_t) * (size_t)mlen);
-    if (e == cudaSuccess) e = cudaMalloc(&d_sums.p, sizeof(int32_t) * (size_t)nsums);
-    if (e == cudaSuccess) e = cudaMalloc(&d_cmax.p, sizeof(int32_t) * kClasses);
-    if (e == cudaSuccess) e = cudaMalloc(&d_starts.p, sizeof(int32_t) * kClasses);
-    if (e == cudaSuccess) e = cudaMalloc(&d_newdeg.p, sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess) e = d_sums.alloc(sizeof(int32_t) * (size_t)nsums);
+    if (e == cudaSuccess) e = d_cmax.alloc(sizeof(int32_t) * kClasses);
+    if (e == cudaSuccess) e = d_starts.alloc(sizeof(int32_t) * kClasses);
+    if (e == cudaSuccess) e = d_newdeg.alloc(sizeof(int32_t) * (size_t)n);
     if (e == cudaSuccess) e = cudaMemset(d_cmax.p, 0, sizeof(int32_t) * kClasses);
     if (e == cudaSuccess) e = cudaMemset(g->d_off, 0, sizeof(int32_t) * n_off);
     if (e == cudaSuccess) e = cudaMemset(g->d_src, 0, sizeof(int32_t) * n_src);
@@ -642,7 +647,7 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     int32_t h_starts[kClasses], h_cmax[kClasses], h_bound[kClasses + 1];
     DevTmp d_bound;
     if (e == cudaSuccess) {
-        e = cudaMalloc(&d_bound.p, sizeof(h_bound));
+        e = d_bound.alloc(sizeof(h_bound));
         if (e == cudaSuccess) {
             class_bounds_kernel<<<1, 64>>>(g->d_off, static_cast<const int32_t *>(d_starts.p), n,
                                            static_cast<int32_t *>(d_bound.p));
