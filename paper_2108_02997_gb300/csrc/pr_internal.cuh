@@ -89,6 +89,12 @@ constexpr int kTileValues = PR_TILE_VALUES;
 // than the third CTA gains (measured: 1.4-1.8x slower per launch).
 __host__ __device__ constexpr int vec_min_blocks(int vbytes) { return vbytes == 4 ? PR_VEC_MIN_BLOCKS_4B : PR_VEC_MIN_BLOCKS_8B; }
 constexpr int kVecGatherBatch = PR_VEC_GATHER_BATCH;  // vector gathers per lane issued together (W > 1)
+// A job gets at most one CTA per kMinTilesPerWarp * kWarps of its warp tiles
+// (0: one CTA per tile).
+#ifndef PR_MIN_TILES_PER_WARP
+#define PR_MIN_TILES_PER_WARP 1
+#endif
+constexpr int kMinTilesPerWarp = PR_MIN_TILES_PER_WARP;
 constexpr int kChunkValues = PR_CHUNK_VALUES;
 constexpr int kMinBlocks = PR_MIN_BLOCKS;
 constexpr int kVecTileEdges = 256;

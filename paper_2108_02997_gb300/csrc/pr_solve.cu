@@ -195,6 +195,14 @@ pr_status set_carveout(void *k, size_t smem, bool minimal) {
     return PR_OK;
 }
 
+// CTAs worth giving a job of ntiles warp tiles: at least kMinTilesPerWarp
+// tiles per warp, so that small graphs do not spread over idle CTAs whose
+// partials the job's finalizer must then reduce.
+int tile_ctas(int32_t ntiles) {
+    const int64_t per_cta = kMinTilesPerWarp > 0 ? (int64_t)kWarps * kMinTilesPerWarp : 1;
+    return (int)std::max<int64_t>(1, ((int64_t)std::max(ntiles, 1) + per_cta - 1) / per_cta);
+}
+
 // Split passes: opt the gather kernel into its dynamic shared memory (once per
 // process, precision and width) and report both kernels' residency.
 pr_status setup_split(int prec, int W, int *occ_gather, int *occ_update) {
@@ -568,10 +576,10 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             // update kernel: rows grid-stride
             j.cta_count = std::max(1, std::min<int>(want, (int)(((int64_t)j.g->n * W + kBlock - 1) / kBlock)));
             int gwant = (int)std::lround(gbudget * share);
-            j.gcta_count = std::max(1, std::min(gwant, std::max(j.tt->ntiles, 1)));
+            j.gcta_count = std::max(1, std::min(gwant, tile_ctas(j.tt->ntiles)));
             total_gctas += j.gcta_count;
         } else {
-            j.cta_count = std::max(1, std::min(want, std::max(j.tt->ntiles, 1)));
+            j.cta_count = std::max(1, std::min(want, tile_ctas(j.tt->ntiles)));
         }
         total_ctas += j.cta_count;
     }
