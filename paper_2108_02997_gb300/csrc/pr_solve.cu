@@ -492,6 +492,25 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
 
 }  // namespace
 
+namespace {
+
+// One device-to-device copy of a stopping rule's answer that aliases another
+// rule's (both fired on the same iterate).
+struct CopyItem {
+    double *dst;
+    const double *src;
+    int64_t n;
+};
+// All alias copies of a solve in one launch: blockIdx.y picks the copy,
+// blockIdx.x strides over its elements.
+__global__ void alias_copy_kernel(const CopyItem *__restrict__ items) {
+    const CopyItem it = items[blockIdx.y];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < it.n; i += (int64_t)gridDim.x * blockDim.x)
+        it.dst[i] = it.src[i];
+}
+
+}  // namespace
+
 pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out) {
     LoopStats stats;
     const int ncols = (int)req.cols.size();
@@ -729,14 +748,20 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     // ---- mixed precision: refinement phase in DF64 from the FP32 iterates
     if (mixed) {
         bool any = false;
+        std::vector<std::vector<ColState>> backs(jobs.size(), std::vector<ColState>(W));
+        std::vector<std::vector<Tap>> tbacks(jobs.size());
+        for (size_t ji = 0; ji < jobs.size(); ji++) {
+            PR_CUDA(cudaMemcpyAsync(backs[ji].data(), hjobs[ji].cols, W * sizeof(ColState), cudaMemcpyDeviceToHost, st));
+            tbacks[ji].resize(htaps[ji].size());
+            if (!tbacks[ji].empty())
+                PR_CUDA(cudaMemcpyAsync(tbacks[ji].data(), hjobs[ji].taps, tbacks[ji].size() * sizeof(Tap),
+                                        cudaMemcpyDeviceToHost, st));
+        }
+        PR_CUDA(cudaStreamSynchronize(st));
         for (size_t ji = 0; ji < jobs.size(); ji++) {
             HostJob &j = jobs[ji];
-            std::vector<ColState> back(W);
-            PR_CUDA(cudaMemcpyAsync(back.data(), hjobs[ji].cols, W * sizeof(ColState), cudaMemcpyDeviceToHost, st));
-            std::vector<Tap> tback(htaps[ji].size());
-            if (!tback.empty())
-                PR_CUDA(cudaMemcpyAsync(tback.data(), hjobs[ji].taps, tback.size() * sizeof(Tap), cudaMemcpyDeviceToHost, st));
-            PR_CUDA(cudaStreamSynchronize(st));
+            std::vector<ColState> &back = backs[ji];
+            const std::vector<Tap> &tback = tbacks[ji];
             for (size_t k = 0; k < j.cols.size(); k++) {
                 ColState &cs = back[k];
                 bool pending = false;
@@ -768,26 +793,48 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             if (s != PR_OK) return s;
         }
     }
-    // ---- results: taps, aliases, host copies, histories
+    // ---- results: taps, aliases, host copies, histories (one synchronisation
+    // for all jobs' tap and column states, one launch for all alias copies)
     tap_out.assign(ncols, {});
+    std::vector<std::vector<Tap>> tbacks(jobs.size());
+    std::vector<std::vector<ColState>> cbacks(jobs.size());
+    for (size_t ji = 0; ji < jobs.size(); ji++) {
+        tbacks[ji].resize(htaps[ji].size());
+        cbacks[ji].resize(W);
+        if (!tbacks[ji].empty())
+            PR_CUDA(cudaMemcpyAsync(tbacks[ji].data(), hjobs[ji].taps, tbacks[ji].size() * sizeof(Tap),
+                                    cudaMemcpyDeviceToHost, st));
+        PR_CUDA(cudaMemcpyAsync(cbacks[ji].data(), hjobs[ji].cols, W * sizeof(ColState), cudaMemcpyDeviceToHost, st));
+    }
+    PR_CUDA(cudaStreamSynchronize(st));
+    std::vector<CopyItem> copies;
+    int64_t max_n = 0;
+    for (size_t ji = 0; ji < jobs.size(); ji++) {
+        for (auto &t : tbacks[ji]) {
+            if (!t.fired) return pr_fail(PR_ETIMEOUT, "a stopping rule never fired");
+            if (t.alias_of >= 0) {
+                copies.push_back(CopyItem{t.out, tbacks[ji][t.alias_of].out, (int64_t)jobs[ji].g->n});
+                max_n = std::max<int64_t>(max_n, jobs[ji].g->n);
+            }
+        }
+    }
+    PoolBuf d_copies;
+    for (size_t c0 = 0; c0 < copies.size(); c0 += 65535) {
+        const size_t nc = std::min<size_t>(65535, copies.size() - c0);
+        if (c0 == 0 && (s = d_copies.alloc(std::min<size_t>(copies.size(), 65535) * sizeof(CopyItem), st)) != PR_OK)
+            return s;
+        PR_CUDA(cudaMemcpyAsync(d_copies.p, copies.data() + c0, nc * sizeof(CopyItem), cudaMemcpyHostToDevice, st));
+        const dim3 grid((unsigned)std::min<int64_t>((max_n + 1023) / 1024, 64), (unsigned)nc);
+        alias_copy_kernel<<<grid, 256, 0, st>>>(static_cast<const CopyItem *>(d_copies.p));
+        PR_CUDA(cudaGetLastError());
+        if (c0 + nc < copies.size()) PR_CUDA(cudaStreamSynchronize(st));   // the item buffer is reused
+    }
     for (size_t ji = 0; ji < jobs.size(); ji++) {
         HostJob &j = jobs[ji];
-        std::vector<Tap> tback(htaps[ji].size());
-        if (!tback.empty())
-            PR_CUDA(cudaMemcpyAsync(tback.data(), hjobs[ji].taps, tback.size() * sizeof(Tap), cudaMemcpyDeviceToHost, st));
-        std::vector<ColState> back(W);
-        PR_CUDA(cudaMemcpyAsync(back.data(), hjobs[ji].cols, W * sizeof(ColState), cudaMemcpyDeviceToHost, st));
-        PR_CUDA(cudaStreamSynchronize(st));
-        for (auto &t : tback) {
-            if (!t.fired) return pr_fail(PR_ETIMEOUT, "a stopping rule never fired");
-            if (t.alias_of >= 0)
-                PR_CUDA(cudaMemcpyAsync(t.out, tback[t.alias_of].out, (size_t)j.g->n * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, st));
-        }
         for (size_t k = 0; k < j.cols.size(); k++) {
             SolveColumn &sc = req.cols[j.cols[k]];
-            const ColState &cs = back[k];
-            std::vector<Tap> mine(tback.begin() + cs.tap_begin, tback.begin() + cs.tap_end);
+            const ColState &cs = cbacks[ji][k];
+            std::vector<Tap> mine(tbacks[ji].begin() + cs.tap_begin, tbacks[ji].begin() + cs.tap_end);
             for (size_t q = 0; q < mine.size() && q < sc.host_dst.size(); q++)
                 if (sc.host_dst[q])
                     PR_CUDA(cudaMemcpyAsync(sc.host_dst[q], mine[q].out, (size_t)j.g->n * sizeof(double),
