@@ -7,7 +7,14 @@
 // estimates each column's iterations; it then cuts the columns of each graph,
 // sorted by estimated iterations, into the contiguous jobs that minimise
 //     sum over jobs  max(iterations in the job) x t(W of the job)
-// by dynamic programming. Jobs run as sub-solves (one kernel launch per
+// by dynamic programming. Jobs of one width share the launches of a
+// sub-solve, and with them each launch's latency (measured once per signature
+// as well, with four single-column jobs in one launch), so the planner also
+// forms the partition for the launch times less that latency and one job per
+// column, and keeps the cheapest of the three under
+//     sum over widths  latency x max(iterations)
+//   + sum over jobs    max(iterations in the job) x (t(W) - latency).
+// Jobs run as sub-solves (one kernel launch per
 // iteration for all jobs of a sub-solve): jobs of one width share a sub-solve
 // while their gathered vectors together fit in half of the L2 cache, since
 // jobs sharing launches also share the cache, and a job larger than that runs
@@ -46,6 +53,7 @@ struct Decay {
 struct TuneEntry {
     Table us{};
     Decay decay;
+    double lat = -1.0;   // per-launch latency shared by concurrent jobs (us; < 0 unknown)
 };
 
 std::mutex g_tune_mu;
@@ -209,6 +217,51 @@ pr_status time_width(const pr_graph *g, int precision, int W, cudaStream_t st, d
     return PR_OK;
 }
 
+// Latency share of a launch: one solve of kMultiJobs single-column jobs in
+// the same launches against one job alone. The jobs' work adds, the pass's
+// latency (launch, finalizer, loop) does not: t(k jobs) = lat + k v.
+constexpr int kMultiJobs = 4;
+pr_status time_latency(const pr_graph *g, int precision, double us1, cudaStream_t st, double *lat) {
+    SolveRequest r;
+    r.precision = precision;
+    r.loop = PR_LOOP_HOST;
+    r.stream = st;
+    // the kernel form one job alone gets, so that both timings use the same kernels
+    r.kernels = kSplitPasses && (double)g->nnz >= kSplitMinWork ? PR_KERNELS_SPLIT : PR_KERNELS_FUSED;
+    for (int c = 0; c < kMultiJobs; c++) {
+        SolveColumn sc;
+        sc.g = g;
+        sc.alpha = kTuneAlpha - 0.01 * c;
+        Tap t{};
+        t.tau = 1e-300;
+        t.norm = PR_NORM_L1;
+        t.max_iter = kTuneIters;
+        t.alias_of = -1;
+        t.out = nullptr;
+        sc.taps.push_back(t);
+        sc.inst.push_back(c);
+        sc.host_dst.push_back(nullptr);
+        r.cols.push_back(sc);
+        r.jobs.push_back({c});
+    }
+    std::vector<std::vector<Tap>> taps;
+    pr_status s = pr_run_solve(r, taps);
+    if (s != PR_OK) return s;
+    const double usk = r.stats.kernel_ms * 1000.0 / std::max(r.stats.passes, 1);
+    const double v = std::max(0.0, (usk - us1) / (kMultiJobs - 1));
+    *lat = std::max(0.0, us1 - v);
+    return PR_OK;
+}
+
+size_t free_device_bytes() {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return free_b;
+}
+
 // Fills `out` with the launch times of `precision` on g for widths up to
 // max_width, timing those not yet known for g's signature.
 pr_status tune(const pr_graph *g, int precision, int max_width, cudaStream_t st, TuneEntry &out) {
@@ -236,12 +289,18 @@ pr_status tune(const pr_graph *g, int precision, int max_width, cudaStream_t st,
         }
         changed = true;
     }
+    if (te.lat < 0.0 && te.us[0] > 0.0 && tune_bytes(g, kMultiJobs) <= 0.25 * (double)free_device_bytes()) {
+        pr_status s = time_latency(g, precision, te.us[0], st, &te.lat);
+        if (s != PR_OK) return s;
+        changed = true;
+    }
     if (changed) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         TuneEntry &dst = g_tune[key];
         for (int w = 0; w < kWidths; w++)
             if (dst.us[w] == 0.0) dst.us[w] = te.us[w];
         if (dst.decay.rho[0] == 0.0) dst.decay = te.decay;
+        if (dst.lat < 0.0) dst.lat = te.lat;
     }
     out = te;
     return PR_OK;
@@ -298,10 +357,64 @@ pr_status pr_plan_request(const SolveRequest &req, int group, std::vector<SubSol
         if (mixed && (s = tune(g, PR_PREC_DF64, maxw, req.stream, t1)) != PR_OK) return s;
         std::vector<std::array<double, 2>> it;
         for (int c : v) it.push_back(column_iterations(req.cols[c], req.precision, req.switch_tol, &t0.decay));
+        const int np = mixed ? 2 : 1;
         const double *tp[2] = {t0.us.data(), t1.us.data()};
         std::vector<int> job_of, width_of;
-        if (!plan_partition(it, tp, mixed ? 2 : 1, job_of, width_of, nullptr))
+        if (!plan_partition(it, tp, np, job_of, width_of, nullptr))
             return pr_fail(PR_ECUDA, "internal: no column plan (width 1 untimed)");
+        // Jobs of one width share each launch, and with it the launch's
+        // latency. Candidates: the plan above (each job pays a whole launch
+        // time), the plan for the marginal times t(W) - latency, and one job
+        // per column; kept: the cheapest under
+        //     sum over widths  latency x max(iterations)
+        //   + sum over jobs    max(iterations in the job) x (t(W) - latency)
+        const double lat[2] = {std::max(0.0, t0.lat), std::max(0.0, mixed ? t1.lat : 0.0)};
+        Table vt[2];
+        for (int p = 0; p < np; p++)
+            for (int w = 0; w < kWidths; w++)
+                vt[p][w] = tp[p][w] > 0.0 ? std::max(tp[p][w] - lat[p], 0.05 * tp[p][w]) : tp[p][w];
+        auto model = [&](const std::vector<int> &jo, const std::vector<int> &wo) {
+            std::map<int, std::array<double, 2>> job_it;   // job -> per-phase max iterations
+            std::map<int, int> job_w;
+            for (size_t k = 0; k < jo.size(); k++) {
+                auto &m = job_it[jo[k]];
+                for (int p = 0; p < np; p++) m[p] = std::max(m[p], it[k][p]);
+                job_w[jo[k]] = wo[k];
+            }
+            std::map<int, std::array<double, 2>> width_it;
+            double cost = 0.0;
+            for (auto &kv : job_it) {
+                int wi = 0;
+                while ((1 << wi) < job_w[kv.first]) wi++;
+                auto &m = width_it[wi];
+                for (int p = 0; p < np; p++) {
+                    m[p] = std::max(m[p], kv.second[p]);
+                    cost += kv.second[p] * vt[p][wi];
+                }
+            }
+            for (auto &kv : width_it)
+                for (int p = 0; p < np; p++) cost += kv.second[p] * lat[p];
+            return cost;
+        };
+        if (lat[0] > 0.0) {
+            double best = model(job_of, width_of);
+            const double *vp[2] = {vt[0].data(), vt[1].data()};
+            std::vector<int> jo2, wo2;
+            if (plan_partition(it, vp, np, jo2, wo2, nullptr)) {
+                const double c2 = model(jo2, wo2);
+                if (c2 < best) {
+                    best = c2;
+                    job_of = jo2;
+                    width_of = wo2;
+                }
+            }
+            std::vector<int> jo3(v.size()), wo3(v.size(), 1);
+            for (size_t k = 0; k < v.size(); k++) jo3[k] = (int)k;
+            if (model(jo3, wo3) < best) {
+                job_of = jo3;
+                width_of = wo3;
+            }
+        }
         std::map<int, std::pair<int, std::vector<int>>> jobs;   // job index -> (width, request columns)
         for (size_t k = 0; k < v.size(); k++) {
             jobs[job_of[k]].first = width_of[k];
