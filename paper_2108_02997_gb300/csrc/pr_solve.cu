@@ -262,7 +262,7 @@ struct HostJob {
     const TileTable *tt = nullptr;
     int cta_count = 0;
     int gcta_count = 0;              // split passes: CTAs of the gather kernel
-    size_t off_r[2], off_c[2], off_cp, off_cnt, off_part, off_cols, off_taps, off_hist, off_rowsum = 0;
+    size_t off_r[2], off_c[2], off_cp, off_part, off_hist, off_rowsum = 0;
     int ntaps = 0;
     int hist_total = 0;
 };
@@ -615,15 +615,26 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             j.off_c[b] = ar.reserve((n * W + kPad) * vs_max);
         }
         j.off_cp = ar.reserve((size_t)std::max(j.tt->n_chunk_slots, 1) * W * vs_max);
-        j.off_cnt = ar.reserve((size_t)std::max(j.tt->n_long, 1) * sizeof(uint32_t));
         j.off_part = ar.reserve((size_t)j.cta_count * W * kPartials * sizeof(double));
         if (split) j.off_rowsum = ar.reserve((n * W + kPad) * vs_max);
-        j.off_cols = ar.reserve((size_t)W * sizeof(ColState));
         for (int c : j.cols) j.ntaps += (int)req.cols[c].taps.size();
-        j.off_taps = ar.reserve((size_t)std::max(j.ntaps, 1) * sizeof(Tap));
         for (int c : j.cols) j.hist_total += req.cols[c].hist_host ? req.cols[c].hist_cap : 0;
         j.off_hist = ar.reserve((size_t)std::max(j.hist_total, 1) * 3 * sizeof(double));
     }
+    // all jobs' column states and stopping taps in one block (one upload, one
+    // read-back), and all chunk counters in another (one memset)
+    size_t total_taps = 0, total_cnt = 0;
+    std::vector<size_t> tap_base(jobs.size()), cnt_base(jobs.size());
+    for (size_t ji = 0; ji < jobs.size(); ji++) {
+        tap_base[ji] = total_taps;
+        total_taps += (size_t)jobs[ji].ntaps;
+        cnt_base[ji] = total_cnt;
+        total_cnt += (size_t)std::max(jobs[ji].tt->n_long, 1);
+    }
+    const size_t cols_bytes = jobs.size() * (size_t)W * sizeof(ColState);
+    const size_t state_bytes = cols_bytes + std::max<size_t>(total_taps, 1) * sizeof(Tap);
+    const size_t off_state = ar.reserve(state_bytes);
+    const size_t off_cnt = ar.reserve(total_cnt * sizeof(uint32_t));
     // mixed precision keeps the FP32 phase buffers alive while the refinement
     // phase starts from them
     std::vector<size_t> off_r32;
@@ -649,8 +660,11 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     std::vector<JobDev> hjobs(jobs.size());
     std::vector<int32_t> ctajob(total_ctas), gctajob(std::max(total_gctas, 1), 0);
     int gcta_at = 0;
-    std::vector<std::vector<ColState>> hcols(jobs.size());
-    std::vector<std::vector<Tap>> htaps(jobs.size());
+    std::vector<unsigned char> hstate(state_bytes, 0);
+    ColState *hcols_all = reinterpret_cast<ColState *>(hstate.data());
+    Tap *htaps_all = reinterpret_cast<Tap *>(hstate.data() + cols_bytes);
+    ColState *dcols_all = ar.at<ColState>(off_state);
+    Tap *dtaps_all = reinterpret_cast<Tap *>(ar.at<unsigned char>(off_state) + cols_bytes);
     size_t stage_i = 0;
     int cta_at = 0;
     for (size_t ji = 0; ji < jobs.size(); ji++) {
@@ -689,16 +703,16 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         d.contrib[0] = ar.at<void>(j.off_c[0]);
         d.contrib[1] = ar.at<void>(j.off_c[1]);
         d.chunk_part = ar.at<void>(j.off_cp);
-        d.chunk_cnt = ar.at<uint32_t>(j.off_cnt);
+        d.chunk_cnt = ar.at<uint32_t>(off_cnt) + cnt_base[ji];
         d.cta_part = ar.at<double>(j.off_part);
-        d.cols = ar.at<ColState>(j.off_cols);
-        d.taps = ar.at<Tap>(j.off_taps);
-        hcols[ji].assign(W, ColState{});
+        d.cols = dcols_all + ji * (size_t)W;
+        d.taps = dtaps_all + tap_base[ji];
+        ColState *hcols = hcols_all + ji * (size_t)W;
+        Tap *htaps = htaps_all + tap_base[ji];
         int tap_at = 0, hist_at = 0;
         for (size_t k = 0; k < j.cols.size(); k++) {
             SolveColumn &sc = req.cols[j.cols[k]];
-            ColState &cs = hcols[ji][k];
-            std::memset(&cs, 0, sizeof(cs));
+            ColState &cs = hcols[k];
             cs.alpha = sc.alpha;
             store_value(cs.v_alpha, prec1, sc.alpha);
             store_value(cs.v_c0, prec1, 1.0 / (double)j.g->n);   // init pass: uniform start value
@@ -710,7 +724,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
                 tt.fired = 0;
                 tt.alias_of = -1;
                 if (!tt.out) tt.out = ar.at<double>(stage_off[stage_i++]);
-                htaps[ji].push_back(tt);
+                htaps[tap_at] = tt;
                 tap_at++;
             }
             cs.tap_end = tap_at;
@@ -731,12 +745,9 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
                 cs.switch_tol = req.switch_tol;
             }
         }
-        cudaError_t e = cudaMemcpyAsync(d.cols, hcols[ji].data(), W * sizeof(ColState), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && !htaps[ji].empty())
-            e = cudaMemcpyAsync(d.taps, htaps[ji].data(), htaps[ji].size() * sizeof(Tap), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(d.chunk_cnt, 0, (size_t)std::max(j.tt->n_long, 1) * sizeof(uint32_t), st);
-        if (e != cudaSuccess) return pr_cuda_fail(e, "workspace upload");
     }
+    PR_CUDA(cudaMemcpyAsync(dcols_all, hstate.data(), state_bytes, cudaMemcpyHostToDevice, st));
+    PR_CUDA(cudaMemsetAsync(ar.at<uint32_t>(off_cnt), 0, total_cnt * sizeof(uint32_t), st));
     PR_CUDA(cudaMemcpyAsync(ar.at<JobDev>(off_jobs), hjobs.data(), hjobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice, st));
     PR_CUDA(cudaMemcpyAsync(ar.at<int32_t>(off_ctajob), ctajob.data(), ctajob.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     PR_CUDA(cudaMemcpyAsync(ar.at<int32_t>(off_gctajob), gctajob.data(), gctajob.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -748,20 +759,12 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     // ---- mixed precision: refinement phase in DF64 from the FP32 iterates
     if (mixed) {
         bool any = false;
-        std::vector<std::vector<ColState>> backs(jobs.size(), std::vector<ColState>(W));
-        std::vector<std::vector<Tap>> tbacks(jobs.size());
-        for (size_t ji = 0; ji < jobs.size(); ji++) {
-            PR_CUDA(cudaMemcpyAsync(backs[ji].data(), hjobs[ji].cols, W * sizeof(ColState), cudaMemcpyDeviceToHost, st));
-            tbacks[ji].resize(htaps[ji].size());
-            if (!tbacks[ji].empty())
-                PR_CUDA(cudaMemcpyAsync(tbacks[ji].data(), hjobs[ji].taps, tbacks[ji].size() * sizeof(Tap),
-                                        cudaMemcpyDeviceToHost, st));
-        }
+        PR_CUDA(cudaMemcpyAsync(hstate.data(), dcols_all, state_bytes, cudaMemcpyDeviceToHost, st));
         PR_CUDA(cudaStreamSynchronize(st));
         for (size_t ji = 0; ji < jobs.size(); ji++) {
             HostJob &j = jobs[ji];
-            std::vector<ColState> &back = backs[ji];
-            const std::vector<Tap> &tback = tbacks[ji];
+            ColState *back = hcols_all + ji * (size_t)W;
+            const Tap *tback = htaps_all + tap_base[ji];
             for (size_t k = 0; k < j.cols.size(); k++) {
                 ColState &cs = back[k];
                 bool pending = false;
@@ -783,8 +786,8 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             hjobs[ji].alive = 1;
             hjobs[ji].arrive = 0;
             hjobs[ji].cur = 0;
-            PR_CUDA(cudaMemcpyAsync(hjobs[ji].cols, back.data(), W * sizeof(ColState), cudaMemcpyHostToDevice, st));
         }
+        PR_CUDA(cudaMemcpyAsync(dcols_all, hstate.data(), cols_bytes, cudaMemcpyHostToDevice, st));
         if (any) {
             PR_CUDA(cudaMemcpyAsync(ar.at<JobDev>(off_jobs), hjobs.data(), hjobs.size() * sizeof(JobDev),
                                     cudaMemcpyHostToDevice, st));
@@ -796,24 +799,17 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     // ---- results: taps, aliases, host copies, histories (one synchronisation
     // for all jobs' tap and column states, one launch for all alias copies)
     tap_out.assign(ncols, {});
-    std::vector<std::vector<Tap>> tbacks(jobs.size());
-    std::vector<std::vector<ColState>> cbacks(jobs.size());
-    for (size_t ji = 0; ji < jobs.size(); ji++) {
-        tbacks[ji].resize(htaps[ji].size());
-        cbacks[ji].resize(W);
-        if (!tbacks[ji].empty())
-            PR_CUDA(cudaMemcpyAsync(tbacks[ji].data(), hjobs[ji].taps, tbacks[ji].size() * sizeof(Tap),
-                                    cudaMemcpyDeviceToHost, st));
-        PR_CUDA(cudaMemcpyAsync(cbacks[ji].data(), hjobs[ji].cols, W * sizeof(ColState), cudaMemcpyDeviceToHost, st));
-    }
+    PR_CUDA(cudaMemcpyAsync(hstate.data(), dcols_all, state_bytes, cudaMemcpyDeviceToHost, st));
     PR_CUDA(cudaStreamSynchronize(st));
     std::vector<CopyItem> copies;
     int64_t max_n = 0;
     for (size_t ji = 0; ji < jobs.size(); ji++) {
-        for (auto &t : tbacks[ji]) {
+        const Tap *tb = htaps_all + tap_base[ji];
+        for (int q = 0; q < jobs[ji].ntaps; q++) {
+            const Tap &t = tb[q];
             if (!t.fired) return pr_fail(PR_ETIMEOUT, "a stopping rule never fired");
             if (t.alias_of >= 0) {
-                copies.push_back(CopyItem{t.out, tbacks[ji][t.alias_of].out, (int64_t)jobs[ji].g->n});
+                copies.push_back(CopyItem{t.out, tb[t.alias_of].out, (int64_t)jobs[ji].g->n});
                 max_n = std::max<int64_t>(max_n, jobs[ji].g->n);
             }
         }
@@ -833,8 +829,9 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         HostJob &j = jobs[ji];
         for (size_t k = 0; k < j.cols.size(); k++) {
             SolveColumn &sc = req.cols[j.cols[k]];
-            const ColState &cs = cbacks[ji][k];
-            std::vector<Tap> mine(tbacks[ji].begin() + cs.tap_begin, tbacks[ji].begin() + cs.tap_end);
+            const ColState &cs = hcols_all[ji * (size_t)W + k];
+            const Tap *tb = htaps_all + tap_base[ji];
+            std::vector<Tap> mine(tb + cs.tap_begin, tb + cs.tap_end);
             for (size_t q = 0; q < mine.size() && q < sc.host_dst.size(); q++)
                 if (sc.host_dst[q])
                     PR_CUDA(cudaMemcpyAsync(sc.host_dst[q], mine[q].out, (size_t)j.g->n * sizeof(double),
