@@ -47,6 +47,23 @@ def test_sweep_matches_oracle(B, orc, er, share):
             assert_fp64_parity(x.out, x.iters, x.err, ref[(a, t, nm)], t, nm, f"alpha {a} tau {t} norm {nm} share {share}")
 
 
+def test_sweep_device_outputs_with_aliases(B, orc, er):
+    """Outputs in device memory: rules that fire on the same iterate as an
+    earlier one (equal tau, or a loose tau in every norm) receive their answer
+    by the batched alias copy; every output is checked."""
+    import torch
+    specs = _sweep_specs([0.6, 0.85], [1e-1, 1e-2, 1e-8]) + [(0.85, 1e-8, 1), (0.85, 1e-8, 3)]
+    ref = _oracle_sweep(orc, er, specs)
+    with B.Graph.from_csr(er) as dg:
+        outs = [torch.full((er.n,), -1.0, dtype=torch.float64, device="cuda") for _ in specs]
+        insts = [B.Instance(dg, a, t, nm, 500, out=o) for (a, t, nm), o in zip(specs, outs)]
+        B.pr_solve_batch(insts, outputs_on_device=True)
+        torch.cuda.synchronize()
+        for (a, t, nm), x, o in zip(specs, insts, outs):
+            assert x.status == 0
+            assert_fp64_parity(o.cpu().numpy(), x.iters, x.err, ref[(a, t, nm)], t, nm, f"alpha {a} tau {t} norm {nm}")
+
+
 def test_full_330_sweep(B, orc, er):
     """The paper's alpha sweep (0.50..1.00 step .05) x tau 1e-1..1e-10 x three
     norms: 330 instances in one call, cap 500."""
