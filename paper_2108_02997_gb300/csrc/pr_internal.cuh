@@ -214,15 +214,18 @@ struct JobDev {
 };
 
 struct GlobalDev {
-    uint32_t jobs_arrive;
+    // jobs that finished the current pass (high 32 bits) and, of those, the
+    // ones still alive (low 32 bits): one atomic per job finalizer
+    unsigned long long arrive_alive;
     int32_t njobs;
     int32_t pass;             // body executions so far
     int32_t pass_cap;         // hard cap on body executions
     int32_t alive;            // set by the last job to finish a pass
     int32_t error;            // nonzero: a device-side check failed
+    int32_t pad;
     unsigned long long cond;  // cudaGraphConditionalHandle (0 in host-loop mode)
     uint32_t body_count;      // iteration launches started (independent loop guard)
-    uint32_t alive_jobs;      // jobs still alive after the current pass (counted by their finalizers)
+    uint32_t pad2;
 };
 
 // Error codes a kernel can leave in GlobalDev::error.

@@ -226,7 +226,16 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
     __syncthreads();
     if (!s_flag) return;
     __threadfence();
-    // ---- last CTA of the job: fixed-order FP64 reduction over its CTAs
+    // ---- last CTA of the job. Its work is a chain of dependent memory round
+    // trips, which sets the latency of every pass: the job's fields, the
+    // column states and the stopping rules are read once, with independent
+    // loads, into registers and shared memory, changed there, and written back.
+    const int ncols = job.ncols, cta_count = job.cta_count, job_cur = job.cur;
+    const int32_t n_rows = job.n;
+    ColState *const cols = job.cols;
+    Tap *const taps = job.taps;
+    const double *const cta_part = job.cta_part;
+    // fixed-order FP64 reduction over the job's CTAs, four loads in flight per thread
     {
         constexpr int P = W * kPartials;
         constexpr int S = kBlock / P;
@@ -234,9 +243,14 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
         const int k = p % kPartials;
         double t = 0.0;
         if (sl < S) {
-            for (int c = sl; c < job.cta_count; c += S) {
-                double x = ld_cg(job.cta_part + (size_t)c * P + p);
-                t = (k == 2) ? fmax(t, x) : t + x;
+            for (int c = sl; c < cta_count; c += 4 * S) {
+                double x[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    x[u] = c + u * S < cta_count ? ld_cg(cta_part + (size_t)(c + u * S) * P + p) : (k == 2 ? 0.0 : 0.0);
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (c + u * S < cta_count) t = (k == 2) ? fmax(t, x[u]) : t + x[u];
             }
         }
         s_tot[tid] = t;
@@ -252,20 +266,30 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
         __syncthreads();
     }
     // ---- column decisions: one warp per column, its lanes over the column's
-    // stopping rules (taps, in order)
+    // stopping rules (taps, in order); the column state is staged in shared memory
+    static_assert(sizeof(ColState) % 8 == 0, "ColState is copied in 8-byte words");
+    constexpr int kCsWords = (int)(sizeof(ColState) / 8);
     __shared__ int s_colalive[W];
+    __shared__ __align__(16) ColState s_cs[kWarps];
     const int lane = tid & 31, warp = tid >> 5;
-    for (int c = warp; c < job.ncols; c += kWarps) {
-        ColState &cs = job.cols[c];
+    for (int c = warp; c < ncols; c += kWarps) {
+        {
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(cols + c);
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(&s_cs[warp]);
+            for (int i = lane; i < kCsWords; i += 32) dst[i] = src[i];
+        }
+        __syncwarp();
+        ColState &cs = s_cs[warp];
         const double l1 = s_fin[c * kPartials + 0];
         const double l2 = sqrt(s_fin[c * kPartials + 1]);
         const double li = s_fin[c * kPartials + 2];
         const double D = s_fin[c * kPartials + 3];
         const double S = s_fin[c * kPartials + 4];
-        const double Nn = (double)job.n;
+        const double Nn = (double)n_rows;
         int col_alive = 0;
         if (mode == kPassInit) {
             col_alive = cs.active;
+            __syncwarp();
             if (lane == 0) {
                 cs.c0 = (1.0 - cs.alpha) / Nn + cs.alpha * D / Nn;
                 store_raw<V>(cs.v_c0, N::from_double(cs.c0));
@@ -277,35 +301,45 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
             const double errs[3] = {l1, l2, li};
             const int tb = cs.tap_begin, te = cs.tap_end;
             int primary = -1;
+            double *copy = nullptr;
             bool pending = false;
             for (int q0 = tb; q0 < te; q0 += 32) {
                 const int q = q0 + lane;
                 bool fires = false, pend = false;
                 double e = 0.0;
-                if (q < te && !job.taps[q].fired) {
-                    const Tap &tp = job.taps[q];
-                    e = errs[tp.norm - 1];
-                    if (e < tp.tau || it >= tp.max_iter) fires = true;
-                    else pend = true;
+                double *out = nullptr;
+                if (q < te) {
+                    const Tap tp = taps[q];
+                    out = tp.out;
+                    if (!tp.fired) {
+                        e = errs[tp.norm - 1];
+                        if (e < tp.tau || it >= tp.max_iter) fires = true;
+                        else pend = true;
+                    }
+                    if (fires) {
+                        // the rule's result fields (the rest of the tap is unchanged)
+                        taps[q].fired = 1;
+                        taps[q].iters = it;
+                        taps[q].err = e;
+                        taps[q].err_l1 = l1;
+                        taps[q].converged = e < tp.tau;
+                    }
                 }
                 const unsigned int fm = __ballot_sync(0xffffffffu, fires);
                 if (__any_sync(0xffffffffu, pend)) pending = true;
                 if (fm) {
-                    if (primary < 0) primary = q0 + __ffs(fm) - 1;
-                    if (fires) {
-                        Tap &tp = job.taps[q];
-                        tp.fired = 1;
-                        tp.iters = it;
-                        tp.err = e;
-                        tp.err_l1 = l1;
-                        tp.converged = e < tp.tau;
-                        tp.alias_of = q == primary ? -1 : primary;
+                    const int first = __ffs(fm) - 1;
+                    double *first_out = reinterpret_cast<double *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(out), first));
+                    if (primary < 0) {
+                        primary = q0 + first;
+                        copy = first_out;
                     }
+                    if (fires) taps[q].alias_of = q == primary ? -1 : primary;
                 }
             }
             bool active = pending;
             if (cs.switch_norm && !cs.switched && errs[cs.switch_norm - 1] <= cs.switch_tol) active = false;
-            double *copy = primary >= 0 ? job.taps[primary].out : nullptr;
             col_alive = active || copy != nullptr;
             __syncwarp();
             if (lane == 0) {
@@ -326,24 +360,33 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
                 store_raw<V>(cs.v_c0, N::from_double(cs.c0));
             }
         } else {
+            __syncwarp();
             if (lane == 0) cs.copy_dst = nullptr;
         }
         if (lane == 0) s_colalive[c] = col_alive;
+        __syncwarp();
+        {
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&s_cs[warp]);
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(cols + c);
+            for (int i = lane; i < kCsWords; i += 32) dst[i] = src[i];
+        }
+        __syncwarp();
     }
     __syncthreads();
     if (tid == 0) {
         int alive = 0;
-        for (int c = 0; c < job.ncols; c++) alive |= s_colalive[c];
+        for (int c = 0; c < ncols; c++) alive |= s_colalive[c];
         job.alive = alive;
-        if (mode == kPassIterate) job.cur ^= 1;   // parity shared by the columns still active
+        if (mode == kPassIterate) job.cur = job_cur ^ 1;   // parity shared by the columns still active
         job.arrive = 0;
-        if (alive) atomicAdd(&glob->alive_jobs, 1u);
         __threadfence();
-        unsigned int old = atomicAdd(&glob->jobs_arrive, 1u);
-        if (old == (unsigned int)(glob->njobs - 1)) {
+        // one atomic: this job's arrival (high word) and whether it is alive (low word)
+        const unsigned long long old =
+            atomicAdd(&glob->arrive_alive, (1ull << 32) | (unsigned long long)(alive ? 1u : 0u));
+        if ((unsigned int)(old >> 32) == (unsigned int)(glob->njobs - 1)) {
             __threadfence();
-            glob->jobs_arrive = 0;
-            int any = atomicExch(&glob->alive_jobs, 0u) > 0u;
+            int any = (unsigned int)(old & 0xffffffffull) + (alive ? 1u : 0u) > 0u;
+            glob->arrive_alive = 0ull;
             if (mode == kPassIterate) {
                 glob->pass += 1;
                 if (*(volatile int32_t *)&glob->error) any = 0;
