@@ -144,7 +144,17 @@ __global__ void tile_segments_kernel(const TileSeg *__restrict__ segs, int32_t n
         while (r < sg.r1) {
             const int32_t e0 = off[r];
             int32_t r1 = r;
-            while (r1 < sg.r1 && r1 - r < TR && off[r1 + 1] - e0 <= TE) r1++;
+            // extend the tile row by row; the next four row ends are loaded together
+            for (bool more = true; more;) {
+                int32_t nx[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) nx[u] = r1 + u < sg.r1 ? off[r1 + u + 1] : 0;
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (more && r1 < sg.r1 && r1 - r < TR && nx[u] - e0 <= TE) r1++;
+                    else more = false;
+                }
+            }
             if (r1 == r) r1 = r + 1;   // cannot happen (in-degree <= TE), kept for safety
             if (kWrite) tiles[t0 + nt] = Tile{r, r1, e0, off[r1], sg.glog, -1, 0, 0};
             nt++;

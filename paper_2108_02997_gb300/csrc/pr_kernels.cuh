@@ -215,9 +215,11 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
             Acc t = s_red[0][c][k];
             for (int w = 1; w < kWarps; w++) t = (k == 2) ? N::acc_max(t, s_red[w][c][k]) : N::acc_add(t, s_red[w][c][k]);
             job.cta_part[((size_t)local * W + c) * kPartials + k] = N::acc_to_double(t);
+            // only the partials are read by another CTA of this launch (the
+            // job's last); the other stores need not drain before arriving
+            __threadfence();
         }
     }
-    __threadfence();
     __syncthreads();
     if (tid == 0) {
         unsigned int old = atomicAdd(&job.arrive, 1u);
@@ -231,6 +233,14 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
     // column states and the stopping rules are read once, with independent
     // loads, into registers and shared memory, changed there, and written back.
     const int ncols = job.ncols, cta_count = job.cta_count, job_cur = job.cur;
+    // the pass bookkeeping the last job needs, requested now (only the last
+    // job of a pass changes it)
+    int g_njobs = 0, g_pass = 0, g_cap = 0;
+    if (tid == 0) {
+        g_njobs = glob->njobs;
+        g_pass = glob->pass;
+        g_cap = glob->pass_cap;
+    }
     const int32_t n_rows = job.n;
     ColState *const cols = job.cols;
     Tap *const taps = job.taps;
@@ -383,14 +393,14 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
         // one atomic: this job's arrival (high word) and whether it is alive (low word)
         const unsigned long long old =
             atomicAdd(&glob->arrive_alive, (1ull << 32) | (unsigned long long)(alive ? 1u : 0u));
-        if ((unsigned int)(old >> 32) == (unsigned int)(glob->njobs - 1)) {
+        if ((unsigned int)(old >> 32) == (unsigned int)(g_njobs - 1)) {
             __threadfence();
             int any = (unsigned int)(old & 0xffffffffull) + (alive ? 1u : 0u) > 0u;
             glob->arrive_alive = 0ull;
             if (mode == kPassIterate) {
-                glob->pass += 1;
+                glob->pass = g_pass + 1;
                 if (*(volatile int32_t *)&glob->error) any = 0;
-                if (any && glob->pass >= glob->pass_cap) {
+                if (any && g_pass + 1 >= g_cap) {
                     glob->error = kErrPassCap;
                     any = 0;
                 }
