@@ -8,10 +8,11 @@
 //
 // Gather work is cut into warp tiles; every warp runs its tiles independently
 // (no block-wide barrier until the end of the pass):
-//   rows tile, one column (a run of rows of one in-degree class, at most 256
-//   in-edges): coalesced loads of the tile's in-edge indices and row offsets,
-//   eight independent gathers contrib[u] = r[u]/d_u per lane into a per-warp
-//   shared buffer, then lane groups add each row's values in a fixed order;
+//   rows tile, one column (a run of rows of one in-degree class, at most 224
+//   in-edges): coalesced loads of the tile's in-edge indices and of its row
+//   offsets (kept in registers, read by shuffles), seven independent gathers
+//   contrib[u] = r[u]/d_u per lane into a per-warp shared buffer, then lane
+//   groups add each row's values in a fixed order;
 //   rows tile, W columns: the same with one 8- or 16-byte vector gather per
 //   in-edge and column group;
 //   chunk tile (part of a long row): the warp strides over the chunk with the
@@ -257,7 +258,7 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
                 double x[4];
 #pragma unroll
                 for (int u = 0; u < 4; u++)
-                    x[u] = c + u * S < cta_count ? ld_cg(cta_part + (size_t)(c + u * S) * P + p) : (k == 2 ? 0.0 : 0.0);
+                    x[u] = c + u * S < cta_count ? ld_cg(cta_part + (size_t)(c + u * S) * P + p) : 0.0;
 #pragma unroll
                 for (int u = 0; u < 4; u++)
                     if (c + u * S < cta_count) t = (k == 2) ? fmax(t, x[u]) : t + x[u];
