@@ -104,70 +104,89 @@ struct TileSeg {
 };
 constexpr int32_t kSegRows = 1024;
 
-// One thread per segment. Pass 1 (kWrite = false) counts the segment's tiles,
+// One warp per segment. Pass 1 (kWrite = false) counts the segment's tiles,
 // chunk partial slots and long rows (cnt, 3 per segment); pass 2 writes them
 // from the segment's exclusive sums (base, 3 per segment): tiles in row order,
 // and for every row cut into several chunks its long-row index (the chunks'
-// slot) and its first chunk partial (slot_base).
+// slot) and its first chunk partial (slot_base). Rows tiles are the greedy
+// runs (extend while the tile keeps at most TR rows and TE in-edges); the
+// lanes test 32 candidate rows at once and a ballot gives the run length.
+// Chunked rows take 32 rows at a time with warp prefix sums.
 template <bool kWrite>
 __global__ void tile_segments_kernel(const TileSeg *__restrict__ segs, int32_t nseg, const int32_t *__restrict__ off,
                                      int TE, int TR, int CH, int32_t *__restrict__ cnt,
                                      const int64_t *__restrict__ base, Tile *__restrict__ tiles,
                                      int32_t *__restrict__ slot_base) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nseg) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= nseg) return;   // whole warps
     const TileSeg sg = segs[i];
-    int64_t nt = 0, ns = 0, nl = 0;
-    const int64_t t0 = kWrite ? base[3 * (int64_t)i] : 0;
-    const int64_t s0 = kWrite ? base[3 * (int64_t)i + 1] : 0;
-    const int64_t l0 = kWrite ? base[3 * (int64_t)i + 2] : 0;
+    int64_t nt = 0, ns = 0, nl = 0;   // the same in every lane
+    const int64_t t0 = kWrite ? base[3 * i] : 0;
+    const int64_t s0 = kWrite ? base[3 * i + 1] : 0;
+    const int64_t l0 = kWrite ? base[3 * i + 2] : 0;
     if (sg.glog < 0) {
-        for (int32_t v = sg.r0; v < sg.r1; v++) {
-            const int32_t e0 = off[v], e1 = off[v + 1];
-            const int32_t nch = max(1, (e1 - e0 + CH - 1) / CH);
-            int32_t slot = -1;
-            if (nch > 1) {
-                slot = (int32_t)(l0 + nl);
-                if (kWrite) slot_base[slot] = (int32_t)(s0 + ns);
-                ns += nch;
-                nl++;
+        for (int32_t v0 = sg.r0; v0 < sg.r1; v0 += 32) {
+            const int32_t v = v0 + lane;
+            int32_t e0 = 0, e1 = 0, nch = 0;
+            if (v < sg.r1) {
+                e0 = off[v];
+                e1 = off[v + 1];
+                nch = max(1, (e1 - e0 + CH - 1) / CH);
             }
-            if (kWrite)
+            const int32_t lg = nch > 1 ? 1 : 0, sl = nch > 1 ? nch : 0;
+            int32_t a_t = nch, a_l = lg, a_s = sl;   // inclusive prefix sums over the lanes
+            for (int m = 1; m < 32; m <<= 1) {
+                const int32_t x_t = __shfl_up_sync(0xffffffffu, a_t, m);
+                const int32_t x_l = __shfl_up_sync(0xffffffffu, a_l, m);
+                const int32_t x_s = __shfl_up_sync(0xffffffffu, a_s, m);
+                if (lane >= m) {
+                    a_t += x_t;
+                    a_l += x_l;
+                    a_s += x_s;
+                }
+            }
+            if (kWrite && v < sg.r1) {
+                int32_t slot = -1;
+                if (lg) {
+                    slot = (int32_t)(l0 + nl + a_l - 1);
+                    slot_base[slot] = (int32_t)(s0 + ns + a_s - sl);
+                }
+                const int64_t at = t0 + nt + a_t - nch;
                 for (int32_t k = 0; k < nch; k++) {
                     const int32_t a = e0 + k * CH;
-                    tiles[t0 + nt + k] = Tile{v, v + 1, a, min(e1, a + CH), -1, slot, k, nch};
+                    tiles[at + k] = Tile{v, v + 1, a, min(e1, a + CH), -1, slot, k, nch};
                 }
-            nt += nch;
+            }
+            nt += __shfl_sync(0xffffffffu, a_t, 31);
+            nl += __shfl_sync(0xffffffffu, a_l, 31);
+            ns += __shfl_sync(0xffffffffu, a_s, 31);
         }
     } else {
         int32_t r = sg.r0;
         while (r < sg.r1) {
             const int32_t e0 = off[r];
             int32_t r1 = r;
-            // extend the tile row by row; the next four row ends are loaded together
-            for (bool more = true; more;) {
-                int32_t nx[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) nx[u] = r1 + u < sg.r1 ? off[r1 + u + 1] : 0;
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    if (more && r1 < sg.r1 && r1 - r < TR && nx[u] - e0 <= TE) r1++;
-                    else more = false;
-                }
+            for (;;) {
+                const int32_t row = r1 + lane;
+                const bool ok = row < sg.r1 && row - r < TR && off[row + 1] - e0 <= TE;
+                const unsigned int m = __ballot_sync(0xffffffffu, ok);
+                const int run = m == 0xffffffffu ? 32 : __ffs(~m) - 1;   // the conditions only turn false
+                r1 += run;
+                if (run < 32) break;
             }
             if (r1 == r) r1 = r + 1;   // cannot happen (in-degree <= TE), kept for safety
-            if (kWrite) tiles[t0 + nt] = Tile{r, r1, e0, off[r1], sg.glog, -1, 0, 0};
+            if (kWrite && lane == 0) tiles[t0 + nt] = Tile{r, r1, e0, off[r1], sg.glog, -1, 0, 0};
             nt++;
             r = r1;
         }
     }
-    if (!kWrite) {
-        cnt[3 * (int64_t)i] = (int32_t)nt;
-        cnt[3 * (int64_t)i + 1] = (int32_t)ns;
-        cnt[3 * (int64_t)i + 2] = (int32_t)nl;
+    if (!kWrite && lane == 0) {
+        cnt[3 * i] = (int32_t)nt;
+        cnt[3 * i + 1] = (int32_t)ns;
+        cnt[3 * i + 2] = (int32_t)nl;
     }
 }
-
 
 }  // namespace
 
@@ -212,7 +231,7 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     if (e == cudaSuccess) e = d_base.alloc(sizeof(int64_t) * base.size());
     if (e == cudaSuccess && nseg > 0)
         e = cudaMemcpy(d_segs.p, segs.data(), sizeof(TileSeg) * (size_t)nseg, cudaMemcpyHostToDevice);
-    const int blocks = std::max(1, (nseg + 127) / 128);
+    const int blocks = std::max(1, (int)(((int64_t)nseg * 32 + 127) / 128));   // a warp per segment
     if (e == cudaSuccess && nseg > 0) {
         tile_segments_kernel<false><<<blocks, 128>>>(static_cast<const TileSeg *>(d_segs.p), nseg, g->d_off, TE, TR, CH,
                                                      static_cast<int32_t *>(d_cnt.p), nullptr, nullptr, nullptr);
