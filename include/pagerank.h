@@ -271,6 +271,9 @@ pr_status pr_solve_batch(pr_instance *inst, int32_t count, const pr_options *opt
  *    in-neighbours u, alpha]
  * predicts log(N * r); the start is exp(prediction) renormalised to sum 1.
  * Weights are held in FP32 (master) and BF16 (inference/training operands).
+ * Training differentiates the exact (erf) GELU; inference evaluates GELU by
+ * its tanh approximation (Hendrycks and Gimpel) on the hardware tanh, within
+ * 5e-4 of the exact form (below the BF16 rounding of the hidden layer).
  * params layout (host, 4609 floats): W1[64][5], b1[64], W2[64][64], b2[64],
  * W3[1][64], b3[1].
  */
@@ -278,10 +281,14 @@ pr_status pr_mlp_create(const float *params, pr_mlp **out);
 pr_status pr_mlp_destroy(pr_mlp *m);
 pr_status pr_mlp_get_params(const pr_mlp *m, float *params_out);
 
-/* Features (n x 5 floats, caller order, device pointer) of graph g at alpha. */
+/* Features (n x 5 floats, caller order, device pointer) of graph g at alpha.
+ * Returns after the features are written (the stream is synchronised). */
 pr_status pr_features(const pr_graph *g, double alpha, float *d_feat_out, void *stream);
 
-/* Warm-start vector (n doubles, caller order; device pointer) for (g, alpha). */
+/* Warm-start vector (n doubles, caller order; device pointer) for (g, alpha).
+ * Returns after the vector is written (the stream is synchronised). Errors:
+ * PR_ESTATE for a stale handle, PR_EINVAL for a NULL output or alpha outside
+ * [0, 1]. */
 pr_status pr_mlp_warm_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_r0_out,
                             void *stream);
 
