@@ -346,6 +346,20 @@ pr_status pr_plan_columns(int32_t count, const double *iters, const double *us_p
                           int32_t *width_of, double *cost_out);
 
 /*
+ * The same grouping when jobs of one width share each launch and with it the
+ * launch's latency (latency_us, measured by pr_graph_tune with four
+ * single-column jobs in one launch). Candidates: the pr_plan_columns
+ * partition, the partition for the launch times less the latency, and one job
+ * per column; kept: the cheapest under
+ *     sum over widths used  latency_us x max(iters)
+ *   + sum over jobs         max(iters in the job) x max(t(W) - latency_us, 0.05 t(W)).
+ * cost_out (optional) receives that cost. Errors as pr_plan_columns, and
+ * PR_EINVAL for a negative or non-finite latency. Host only.
+ */
+pr_status pr_plan_columns_shared(int32_t count, const double *iters, const double *us_per_launch, double latency_us,
+                                 int32_t *job_of, int32_t *width_of, double *cost_out);
+
+/*
  * Resident CTAs per SM of the iteration kernel for `precision` (PR_PREC_DF64,
  * PR_PREC_FP64 or PR_PREC_FP32) and column width `width` (1, 2, 4, .., 32) on
  * the current device, as the CUDA occupancy calculator reports it for the

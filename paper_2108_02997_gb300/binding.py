@@ -81,6 +81,7 @@ SIGNATURES = {
     "pr_graph_tune": ([_vp, _i32, _i32, _vp, _vp], _i32),
     "pr_kernel_occupancy": ([_i32, _i32, _vp], _i32),
     "pr_plan_columns": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
+    "pr_plan_columns_shared": ([_i32, _vp, _vp, _d, _vp, _vp, _vp], _i32),
     "pr_solve_noalloc": ([_vp, _d, _d, _i32, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "pr_last_error": ([], C.c_char_p),
     "pr_status_string": ([_i32], C.c_char_p),
@@ -330,6 +331,21 @@ def plan_columns(iters, us_per_launch):
     cost = C.c_double()
     _check(lib().pr_plan_columns(it.size, it.ctypes.data, us.ctypes.data, job.ctypes.data, wid.ctypes.data,
                                  C.byref(cost)), "pr_plan_columns")
+    return job, wid, cost.value
+
+
+def plan_columns_shared(iters, us_per_launch, latency_us):
+    """The planner with the launch latency that jobs of one width share:
+    (job_of, width_of, cost under the shared-latency model)."""
+    it = np.ascontiguousarray(iters, np.float64)
+    us = np.ascontiguousarray(us_per_launch, np.float64)
+    if us.size != 6:
+        raise ValueError("need 6 launch times (W = 1 .. 32)")
+    job = np.empty(it.size, np.int32)
+    wid = np.empty(it.size, np.int32)
+    cost = C.c_double()
+    _check(lib().pr_plan_columns_shared(it.size, it.ctypes.data, us.ctypes.data, float(latency_us), job.ctypes.data,
+                                        wid.ctypes.data, C.byref(cost)), "pr_plan_columns_shared")
     return job, wid, cost.value
 
 

@@ -168,6 +168,65 @@ bool plan_partition(const std::vector<std::array<double, 2>> &it, const double *
     return true;
 }
 
+// Cost of a grouping when jobs of one width share each launch, and with it
+// the launch's latency lat: sum over widths lat x max(iterations) plus sum
+// over jobs max(iterations in the job) x (t(W) - lat), per phase.
+double shared_cost(const std::vector<std::array<double, 2>> &it, const double *const *t, int nphase,
+                   const double *lat, const std::vector<int> &job_of, const std::vector<int> &width_of) {
+    std::map<int, std::array<double, 2>> job_it;
+    std::map<int, int> job_w;
+    for (size_t k = 0; k < job_of.size(); k++) {
+        auto &m = job_it[job_of[k]];
+        for (int p = 0; p < nphase; p++) m[p] = std::max(m[p], it[k][p]);
+        job_w[job_of[k]] = width_of[k];
+    }
+    std::map<int, std::array<double, 2>> width_it;
+    double cost = 0.0;
+    for (auto &kv : job_it) {
+        int wi = 0;
+        while ((1 << wi) < job_w[kv.first]) wi++;
+        auto &m = width_it[wi];
+        for (int p = 0; p < nphase; p++) {
+            m[p] = std::max(m[p], kv.second[p]);
+            cost += kv.second[p] * std::max(t[p][wi] - lat[p], 0.05 * t[p][wi]);
+        }
+    }
+    for (auto &kv : width_it)
+        for (int p = 0; p < nphase; p++) cost += kv.second[p] * lat[p];
+    return cost;
+}
+
+// Given the partition for whole launch times in job_of / width_of, keeps the
+// cheapest under shared_cost of: that partition, the partition for the
+// launch times less the latency, and one job per column. Returns its cost.
+double choose_shared_plan(const std::vector<std::array<double, 2>> &it, const double *const *t, int nphase,
+                          const double *lat, std::vector<int> &job_of, std::vector<int> &width_of) {
+    double best = shared_cost(it, t, nphase, lat, job_of, width_of);
+    if (!(lat[0] > 0.0)) return best;
+    Table vt[2];
+    for (int p = 0; p < nphase; p++)
+        for (int w = 0; w < kWidths; w++) vt[p][w] = t[p][w] > 0.0 ? std::max(t[p][w] - lat[p], 0.05 * t[p][w]) : t[p][w];
+    const double *vp[2] = {vt[0].data(), vt[1].data()};
+    std::vector<int> jo2, wo2;
+    if (plan_partition(it, vp, nphase, jo2, wo2, nullptr)) {
+        const double c2 = shared_cost(it, t, nphase, lat, jo2, wo2);
+        if (c2 < best) {
+            best = c2;
+            job_of = jo2;
+            width_of = wo2;
+        }
+    }
+    std::vector<int> jo3(it.size()), wo3(it.size(), 1);
+    for (size_t k = 0; k < it.size(); k++) jo3[k] = (int)k;
+    const double c3 = shared_cost(it, t, nphase, lat, jo3, wo3);
+    if (c3 < best) {
+        best = c3;
+        job_of = jo3;
+        width_of = wo3;
+    }
+    return best;
+}
+
 // Bytes of device workspace a W-column timing solve needs (two rank and two
 // contribution buffers of 8-byte slots, plus the staged answers), with slack.
 double tune_bytes(const pr_graph *g, int W) { return 48.0 * (double)g->n * W + (64 << 20); }
@@ -362,59 +421,8 @@ pr_status pr_plan_request(const SolveRequest &req, int group, std::vector<SubSol
         std::vector<int> job_of, width_of;
         if (!plan_partition(it, tp, np, job_of, width_of, nullptr))
             return pr_fail(PR_ECUDA, "internal: no column plan (width 1 untimed)");
-        // Jobs of one width share each launch, and with it the launch's
-        // latency. Candidates: the plan above (each job pays a whole launch
-        // time), the plan for the marginal times t(W) - latency, and one job
-        // per column; kept: the cheapest under
-        //     sum over widths  latency x max(iterations)
-        //   + sum over jobs    max(iterations in the job) x (t(W) - latency)
         const double lat[2] = {std::max(0.0, t0.lat), std::max(0.0, mixed ? t1.lat : 0.0)};
-        Table vt[2];
-        for (int p = 0; p < np; p++)
-            for (int w = 0; w < kWidths; w++)
-                vt[p][w] = tp[p][w] > 0.0 ? std::max(tp[p][w] - lat[p], 0.05 * tp[p][w]) : tp[p][w];
-        auto model = [&](const std::vector<int> &jo, const std::vector<int> &wo) {
-            std::map<int, std::array<double, 2>> job_it;   // job -> per-phase max iterations
-            std::map<int, int> job_w;
-            for (size_t k = 0; k < jo.size(); k++) {
-                auto &m = job_it[jo[k]];
-                for (int p = 0; p < np; p++) m[p] = std::max(m[p], it[k][p]);
-                job_w[jo[k]] = wo[k];
-            }
-            std::map<int, std::array<double, 2>> width_it;
-            double cost = 0.0;
-            for (auto &kv : job_it) {
-                int wi = 0;
-                while ((1 << wi) < job_w[kv.first]) wi++;
-                auto &m = width_it[wi];
-                for (int p = 0; p < np; p++) {
-                    m[p] = std::max(m[p], kv.second[p]);
-                    cost += kv.second[p] * vt[p][wi];
-                }
-            }
-            for (auto &kv : width_it)
-                for (int p = 0; p < np; p++) cost += kv.second[p] * lat[p];
-            return cost;
-        };
-        if (lat[0] > 0.0) {
-            double best = model(job_of, width_of);
-            const double *vp[2] = {vt[0].data(), vt[1].data()};
-            std::vector<int> jo2, wo2;
-            if (plan_partition(it, vp, np, jo2, wo2, nullptr)) {
-                const double c2 = model(jo2, wo2);
-                if (c2 < best) {
-                    best = c2;
-                    job_of = jo2;
-                    width_of = wo2;
-                }
-            }
-            std::vector<int> jo3(v.size()), wo3(v.size(), 1);
-            for (size_t k = 0; k < v.size(); k++) jo3[k] = (int)k;
-            if (model(jo3, wo3) < best) {
-                job_of = jo3;
-                width_of = wo3;
-            }
-        }
+        choose_shared_plan(it, tp, np, lat, job_of, width_of);
         std::map<int, std::pair<int, std::vector<int>>> jobs;   // job index -> (width, request columns)
         for (size_t k = 0; k < v.size(); k++) {
             jobs[job_of[k]].first = width_of[k];
@@ -473,6 +481,31 @@ extern "C" pr_status pr_plan_columns(int32_t count, const double *iters, const d
         job_of[c] = jo[c];
         width_of[c] = wo[c];
     }
+    return PR_OK;
+}
+
+extern "C" pr_status pr_plan_columns_shared(int32_t count, const double *iters, const double *us_per_launch,
+                                            double latency_us, int32_t *job_of, int32_t *width_of,
+                                            double *cost_out) {
+    pr_clear_error();
+    if (!(latency_us >= 0.0) || !std::isfinite(latency_us)) return pr_fail(PR_EINVAL, "latency must be >= 0 and finite");
+    double base_cost = 0.0;
+    pr_status s = pr_plan_columns(count, iters, us_per_launch, job_of, width_of, &base_cost);
+    if (s != PR_OK || count == 0) {
+        if (s == PR_OK && cost_out) *cost_out = 0.0;
+        return s;
+    }
+    std::vector<std::array<double, 2>> it(count);
+    for (int32_t c = 0; c < count; c++) it[c] = {iters[c], 0.0};
+    std::vector<int> jo(job_of, job_of + count), wo(width_of, width_of + count);
+    const double *tp[1] = {us_per_launch};
+    const double lat[2] = {latency_us, 0.0};
+    const double cost = choose_shared_plan(it, tp, 1, lat, jo, wo);
+    for (int32_t c = 0; c < count; c++) {
+        job_of[c] = jo[c];
+        width_of[c] = wo[c];
+    }
+    if (cost_out) *cost_out = cost;
     return PR_OK;
 }
 

@@ -116,3 +116,72 @@ def test_rejects_bad_arguments(B):
         B.plan_columns([float("nan")], [1.0] * 6)
     job, wid, cost = B.plan_columns([], [1.0] * 6)
     assert job.size == 0 and cost == 0.0
+
+
+# ---- shared launch latency (jobs of one width share each launch)
+
+def _shared_cost(iters, us, lat, job, wid):
+    """Independent restatement of the model: every width used pays the latency
+    once for its longest job; every job pays its iterations times its width's
+    launch time less the latency (at least 5 % of the launch time)."""
+    by_job = {}
+    for c, j in enumerate(job.tolist()):
+        by_job.setdefault(j, []).append(c)
+    width_max = {}
+    cost = 0.0
+    for j, members in by_job.items():
+        w = int(wid[members[0]])
+        k = int(math.log2(w))
+        m = max(iters[c] for c in members)
+        cost += m * max(us[k] - lat, 0.05 * us[k])
+        width_max[k] = max(width_max.get(k, 0.0), m)
+    return cost + lat * sum(width_max.values())
+
+
+def _singles(n):
+    return np.arange(n, dtype=np.int32), np.ones(n, np.int32)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_shared_plan_is_cheapest_candidate(B, seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 12))
+    iters = rng.integers(5, 80, size=n).astype(np.float64)
+    base = float(rng.uniform(10, 300))
+    us = np.array([base * (1 + g) for g in np.cumsum(rng.uniform(0.05, 1.0, size=6)) - rng.uniform(0.05, 1.0)])
+    us = np.maximum(us, base)
+    lat = float(rng.uniform(0.0, 0.9)) * us[0]
+    job, wid, cost = B.plan_columns_shared(iters, us, lat)
+    assert math.isclose(cost, _shared_cost(iters, us, lat, job, wid), rel_tol=1e-12)
+    # never worse than the whole-launch-time plan or one job per column
+    j0, w0, _ = B.plan_columns(iters, us)
+    assert cost <= _shared_cost(iters, us, lat, j0, w0) * (1 + 1e-12)
+    js, ws = _singles(n)
+    assert cost <= _shared_cost(iters, us, lat, js, ws) * (1 + 1e-12)
+    # every job fits its width
+    for j in set(job.tolist()):
+        members = [c for c in range(n) if job[c] == j]
+        assert len(members) <= int(wid[members[0]]) <= 32
+
+
+def test_shared_plan_latency_bound_small_graph(B):
+    """Eleven equal columns on a small graph: a launch is almost all latency,
+    so eleven single-column jobs sharing one launch beat packing them."""
+    iters = np.full(11, 20.0)
+    us = np.array([30.0, 45.0, 70.0, 120.0, 220.0, 420.0])
+    job, wid, cost = B.plan_columns_shared(iters, us, 28.0)
+    assert (wid == 1).all() and len(set(job.tolist())) == 11
+    assert math.isclose(cost, 20.0 * 28.0 + 11 * 20.0 * 2.0)
+    # the whole-launch-time plan packs them
+    j0, w0, _ = B.plan_columns(iters, us)
+    assert (w0 > 1).any()
+
+
+def test_shared_plan_without_latency_is_the_plain_plan(B):
+    iters = np.array([40.0, 39.0, 12.0, 11.0, 10.0])
+    us = np.array([100.0, 150.0, 260.0, 500.0, 990.0, 1990.0])
+    j1, w1, _ = B.plan_columns_shared(iters, us, 0.0)
+    j0, w0, _ = B.plan_columns(iters, us)
+    assert (j1 == j0).all() and (w1 == w0).all()
+    with pytest.raises(Exception):
+        B.plan_columns_shared(iters, us, -1.0)
