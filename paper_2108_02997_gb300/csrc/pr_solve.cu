@@ -208,20 +208,21 @@ int tile_ctas(int32_t ntiles) {
 pr_status setup_split(int prec, int W, int *occ_gather, int *occ_update) {
     static std::mutex mu;
     static bool done[4][6] = {};
+    static int occ_g[4][6] = {}, occ_u[4][6] = {};   // residencies, queried once
     void *kg = gather_kernel_for(prec, W);
     const size_t smem = gather_smem_bytes(prec, W);
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        const int pi = prec & 3, wi = w_index(W);
-        if (!done[pi][wi]) {
-            PR_CUDA(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            pr_status s = set_carveout(kg, smem, W == 1);
-            if (s != PR_OK) return s;
-            done[pi][wi] = true;
-        }
+    std::lock_guard<std::mutex> lk(mu);
+    const int pi = prec & 3, wi = w_index(W);
+    if (!done[pi][wi]) {
+        PR_CUDA(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        pr_status s = set_carveout(kg, smem, W == 1);
+        if (s != PR_OK) return s;
+        occ_g[pi][wi] = resident_ctas(kg, smem);
+        occ_u[pi][wi] = resident_ctas(update_kernel_for(prec, W), 0);
+        done[pi][wi] = true;
     }
-    *occ_gather = resident_ctas(kg, smem);
-    *occ_update = resident_ctas(update_kernel_for(prec, W), 0);
+    *occ_gather = occ_g[pi][wi];
+    *occ_update = occ_u[pi][wi];
     return PR_OK;
 }
 
@@ -307,21 +308,21 @@ size_t gather_smem_bytes(int prec, int W) {
 pr_status pr_kernel_setup(int prec, int W, int *blocks_per_sm) {
     static std::mutex mu;
     static bool done[4][6] = {};
+    static int occ_k[4][6] = {};   // residency, queried once
     void *k = pr_iter_kernel_for(prec, W);
     const size_t smem = pr_tile_smem_bytes(prec, W);
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        int pi = prec & 3, wi = w_index(W);
-        if (!done[pi][wi]) {
-            PR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            pr_status s = set_carveout(k, smem, false);
-            if (s != PR_OK) return s;
-            done[pi][wi] = true;
-        }
+    std::lock_guard<std::mutex> lk(mu);
+    const int pi = prec & 3, wi = w_index(W);
+    if (!done[pi][wi]) {
+        PR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        pr_status s = set_carveout(k, smem, false);
+        if (s != PR_OK) return s;
+        int occ = 0;
+        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBlock, smem));
+        occ_k[pi][wi] = std::max(occ, 1);
+        done[pi][wi] = true;
     }
-    int occ = 0;
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBlock, smem));
-    *blocks_per_sm = std::max(occ, 1);
+    *blocks_per_sm = occ_k[pi][wi];
     return PR_OK;
 }
 
