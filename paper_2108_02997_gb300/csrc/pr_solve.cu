@@ -258,12 +258,12 @@ int pow2_at_least(int k) {
 }
 
 struct HostJob {
-    const pr_graph *g;
+    const pr_graph *g = nullptr;
     std::vector<int> cols;           // request column indices
     const TileTable *tt = nullptr;
     int cta_count = 0;
     int gcta_count = 0;              // split passes: CTAs of the gather kernel
-    size_t off_r[2], off_c[2], off_cp, off_part, off_hist, off_rowsum = 0;
+    size_t off_r[2] = {0, 0}, off_c[2] = {0, 0}, off_cp = 0, off_part = 0, off_hist = 0, off_rowsum = 0;
     int ntaps = 0;
     int hist_total = 0;
 };
