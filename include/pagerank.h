@@ -100,11 +100,17 @@ typedef enum pr_loop {
  * Grouping changes only the order of floating-point additions: every
  * grouping meets the same accuracy bounds. */
 typedef enum pr_group {
-    PR_GROUP_AUTO = 0,    /* default: per graph, columns sorted by the estimated
-                             iteration count log(tau)/log(alpha) (Section 1) are
-                             cut into the contiguous jobs that minimise the sum
-                             over jobs of (iterations x launch time at the job's
-                             width); launch times come from pr_graph_tune, run
+    PR_GROUP_AUTO = 0,    /* default: per graph, columns sorted by their
+                             estimated iteration counts (the error decay that
+                             pr_graph_tune measures, scaled to each alpha; else
+                             log(tau)/log(alpha), Section 1) are cut into the
+                             contiguous jobs that minimise the sum over jobs of
+                             (iterations x launch time at the job's width); as
+                             jobs of one width share each launch and its
+                             latency, the cheapest of that partition, the one
+                             for launch times less the latency, and one job per
+                             column is kept (pr_plan_columns_shared). Launch
+                             times and latency come from pr_graph_tune, run
                              automatically the first time a graph with two or
                              more columns meets this mode (cached per process by
                              graph signature: vertices, edges and in-degree
