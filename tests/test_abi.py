@@ -107,3 +107,25 @@ def test_options_defaults(L):
     assert o.precision == binding.PR_PREC_DF64 and o.switch_tol == 1e-6 and o.share_trajectories == 1
     assert o.loop == binding.PR_LOOP_GRAPH and o.init == binding.PR_INIT_UNIFORM
     assert o.group == binding.PR_GROUP_AUTO and o.max_passes == 0
+
+
+def test_learned_start_calls_reject_bad_arguments_before_device_work(L):
+    """The warm-start entry points check handles and arguments first (no GPU
+    is touched on these paths)."""
+    h = C.c_void_p()
+    assert L.pr_mlp_create(None, C.byref(h)) == 1
+    bad = np.zeros(4609, np.float32)
+    bad[17] = np.nan
+    assert L.pr_mlp_create(bad.ctypes.data, C.byref(h)) == 1 and b"finite" in L.pr_last_error()
+    assert not h.value
+    bogus = C.c_void_p(0x1234)
+    out = np.empty(8)
+    assert L.pr_mlp_warm_start(bogus, bogus, 0.85, out.ctypes.data, None) == 5
+    assert L.pr_mlp_warm_start(bogus, bogus, 0.85, None, None) == 1
+    assert L.pr_mlp_warm_start(bogus, bogus, 1.5, out.ctypes.data, None) == 1
+    feat = np.empty(40, np.float32)
+    assert L.pr_features(bogus, 0.85, feat.ctypes.data, None) == 5
+    assert L.pr_mlp_loss_grad(bogus, bogus, 0.85, out.ctypes.data, None, None, None) == 5
+    assert L.pr_mlp_train(bogus, None, None, None, 1, 1, C.c_float(1e-3), None, None) == 5
+    assert L.pr_mlp_destroy(None) == 0
+    assert L.pr_mlp_destroy(bogus) == 5
