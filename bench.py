@@ -1,23 +1,36 @@
 #!/usr/bin/env python3
 """Benchmark of the PageRank hot path on GB300 (one JSON line on stdout).
 
-Workloads (synthetic, seeded; stand-ins for the paper's SuiteSparse graphs):
+Default (``--workload headline``): the paper's sweeps as batched solves
+against the plain per-instance GPU solver, the composite of three workloads
+(synthetic, seeded; stand-ins for the paper's SuiteSparse graphs):
 
-* ``rmat22`` (default) — R-MAT scale 22 (N = 4,194,304; 67,108,864 sampled
-  edges; a/b/c/d = .57/.19/.19/.05; ids permuted; self-loops and duplicates
-  removed), alpha = 0.85, tau in {1e-6, 1e-10} x {L1, L2, Linf}: 6 instances
-  solved as one batch (one shared iterate sequence, six stopping rules).
-* ``sweep330`` — the 10k-vertex Erdos-Renyi graph, alpha 0.50..1.00 step .05
-  x tau 1e-1..1e-10 x {L1, L2, Linf} = 330 instances, max 500 iterations.
+* ``sweep330`` — the 10k-vertex Erdos-Renyi graph (100,000 unique edges, 5 %
+  dangling), alpha 0.50..1.00 step .05 x tau 1e-1..1e-10 x {L1, L2, Linf} =
+  330 instances, max 500 iterations; learned start, precision chosen by the
+  planner (Sections 2-4: the alpha sweep, the tau sweep, the norm comparison).
 * ``multi64`` — 64 R-MAT graphs of scale 12 + (i mod 9), edge factor 16,
   alpha 0.85, tau 1e-10, L1, one batch.
-* ``rmat24mixed`` — R-MAT scale 24, alpha in {0.85, 0.95}, Linf, tau 1e-10,
-  FP32 phase to 1e-6 then DF64 refinement.
+* ``evalsweep`` — the learned start's evaluation graphs, unseen in training:
+  R-MAT scale 22 (seed 3022) and 24 (seed 3024) and a directed configuration
+  model with N = 8,000,000 (Zipf 2.1 in/out degrees, mean 12; seed 3008), each
+  swept over alpha 0.50..0.95 x tau 1e-1..1e-10 x {L1, L2, Linf} (300
+  instances per graph), learned start, planner-chosen precision.
 
-A step is one solve of the whole workload with the graph resident in HBM
-(``value``); ``e2e`` repeats it through the public C ABI from pinned host
-arrays (graph creation, solve, ranks back to the host) every step.
-``--impl reference`` times the CPU oracle on the host cores instead.
+A step solves the three workloads once each as batches (``pr_solve_batch``)
+with the graphs resident in HBM; ``value`` is their instances per second. The
+plain per-instance solver (every instance alone through ``pr_solve``, one
+launch per iteration and a host read of the stop flag) is timed on the same
+resident graphs; the per-workload ratios and their geometric mean (GM-RATIO,
+Section 1) are reported with and without trajectory sharing. ``roofline`` is
+the one-column gather kernel on R-MAT scale 22 (seed 22; alpha 0.85, tau
+{1e-6, 1e-10} x {L1, L2, Linf}), measured in the same run. ``e2e`` repeats the
+composite through the C ABI from pinned host arrays (graph creation, solve,
+results to the host). ``cpu_baseline`` is the CPU oracle on a bounded sample,
+on all host cores and on one.
+
+Single workloads (``--workload rmat22`` and others below) keep the same line
+for one workload. ``--impl reference`` times the CPU oracle instead.
 """
 from __future__ import annotations
 
@@ -30,21 +43,27 @@ import subprocess
 import sys
 import threading
 import time
+from dataclasses import dataclass, field
 from pathlib import Path
 
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "sweep solves/s and GTEPS (%HBM roofline), batched+warm vs plain, ≤10τ/(1−α) L1 err"
+HEADLINE = ("sweep330", "multi64", "evalsweep")
+SINGLE = ("rmat22", "rmat21", "sweep330", "sweep330warm", "multi64", "rmat24mixed", "learned", "road24", "evalsweep")
+ALPHAS_SWEEP = [round(0.5 + 0.05 * i, 2) for i in range(11)]      # 0.50 .. 1.00
+ALPHAS_TRAIN = [round(0.5 + 0.05 * i, 2) for i in range(10)]      # 0.50 .. 0.95
+TAUS_SWEEP = [10.0 ** -k for k in range(1, 11)]                    # 1e-1 .. 1e-10
 
 
 def kernel_traffic_ratio():
-    """DRAM traffic / algorithmic bytes of the iteration kernel from the ncu
+    """DRAM traffic / algorithmic bytes of the gather kernel from the ncu
     capture summarised in profiles/, valid only while the kernel sources hash
     to the value recorded there (else None)."""
     import hashlib
     import re
-    prof = ROOT / "profiles" / "pr_iter_kernel-gather_rmat-s21.md"
+    prof = ROOT / "profiles" / "pr_gather_hub_kernel_rmat-s21.md"
     if not prof.exists():
         return None, None
     text = prof.read_text()
@@ -54,7 +73,9 @@ def kernel_traffic_ratio():
     h = hashlib.sha256(b"".join((csrc / f).read_bytes() for f in ("pr_kernels.cuh", "pr_internal.cuh", "df64.cuh")))
     if not (m_hash and m_ratio) or h.hexdigest()[:16] != m_hash.group(1):
         return None, None
-    return float(m_ratio.group(1)), "ncu capture at rmat-s21 (profiles/pr_iter_kernel-gather_rmat-s21.md), scaled by algorithmic bytes"
+    return float(m_ratio.group(1)), ("scaled: one ncu capture at R-MAT scale 21 "
+                                     "(profiles/pr_gather_hub_kernel_rmat-s21.md), traffic/algorithmic bytes "
+                                     "times this launch's algorithmic bytes")
 
 
 def peaks():
@@ -67,55 +88,76 @@ def peaks():
 
 # --------------------------------------------------------------------------- workloads
 
-def make_workload(name, gg, rank=0):
-    """(graphs, instance specs [(graph index, alpha, tau, norm, max_iter)], precision, description).
-    Rank r > 0 of a multi-GPU run gets graphs of the same shape from its own
-    seeds (weak scaling: every rank solves a full batch of its own)."""
+@dataclass
+class Workload:
+    name: str
+    graphs: list
+    specs: list                 # (graph index, alpha, tau, norm, max_iter)
+    desc: str
+    precision: str = "df64"     # batched arm
+    learned: bool = False       # batched arm starts from the learned warm start
+    dgs: list = field(default_factory=list)
+    outs: list = field(default_factory=list)
+
+
+def sweep_specs(gis, alphas):
+    return [(gi, a, t, nm, 500) for gi in gis for a in alphas for t in TAUS_SWEEP for nm in (1, 2, 3)]
+
+
+def make_workload(name, gg, rank=0) -> Workload:
+    """Graphs and instances of one workload. Rank r > 0 of a multi-GPU run gets
+    graphs of the same shape from its own seeds (weak scaling: every rank
+    solves a full batch of its own)."""
     from paper_2108_02997_gb300.dist import rank_seed
     s = lambda seed: rank_seed(seed, rank)
     if name in ("rmat22", "rmat21"):
         scale = int(name[4:])
         g = gg.rmat(scale, 16, seed=s(scale))
         specs = [(0, 0.85, t, nm, 500) for t in (1e-6, 1e-10) for nm in (1, 2, 3)]
-        return [g], specs, "df64", f"rmat-s{scale} ef16 seed{scale}, alpha .85, tau {{1e-6,1e-10}} x {{L1,L2,Linf}}"
+        return Workload(name, [g], specs, f"rmat-s{scale} ef16 seed{scale}, alpha .85, tau {{1e-6,1e-10}} x {{L1,L2,Linf}}")
     if name == "sweep330":
         g = gg.erdos_renyi_10k(seed=s(1))
-        alphas = [round(0.5 + 0.05 * i, 2) for i in range(11)]
-        specs = [(0, a, 10.0 ** -k, nm, 500) for a in alphas for k in range(1, 11) for nm in (1, 2, 3)]
-        return [g], specs, "df64", "er-10k (100k edges, 5% dangling), 11 alpha x 10 tau x 3 norms"
+        return Workload(name, [g], sweep_specs([0], ALPHAS_SWEEP),
+                        "er-10k (100k edges, 5% dangling), 11 alpha x 10 tau x 3 norms; learned start, auto precision",
+                        precision="auto", learned=True)
+    if name == "sweep330warm":
+        g = gg.erdos_renyi_10k(seed=s(1))
+        return Workload(name, [g], sweep_specs([0], ALPHAS_SWEEP),
+                        "er-10k, 11 alpha x 10 tau x 3 norms; learned start, fp32->df64", precision="mixed",
+                        learned=True)
     if name == "multi64":
         gs = [gg.rmat(12 + (i % 9), 16, seed=s(1000 + i)) for i in range(64)]
         specs = [(i, 0.85, 1e-10, 1, 500) for i in range(64)]
-        return gs, specs, "df64", "64 rmat graphs scale 12..20 ef16, alpha .85, tau 1e-10, L1"
+        return Workload(name, gs, specs, "64 rmat graphs scale 12..20 ef16, alpha .85, tau 1e-10, L1",
+                        precision="auto")
+    if name == "evalsweep":
+        gs = [gg.rmat(22, 16, seed=s(3022)), gg.rmat(24, 16, seed=s(3024)), gg.config_model(8_000_000, seed=s(3008))]
+        return Workload(name, gs, sweep_specs(range(3), ALPHAS_TRAIN),
+                        ("unseen rmat-s22 (seed 3022), rmat-s24 (seed 3024), config model N=8M (seed 3008); "
+                         "10 alpha x 10 tau x 3 norms each; learned start, auto precision"),
+                        precision="auto", learned=True)
     if name == "rmat24mixed":
         g = gg.rmat(24, 16, seed=s(24))
         specs = [(0, a, 1e-10, 3, 500) for a in (0.85, 0.95)]
-        return [g], specs, "mixed", "rmat-s24 ef16 seed24, alpha {.85,.95}, Linf, tau 1e-10, fp32->df64"
-    if name == "sweep330warm":
-        g = gg.erdos_renyi_10k(seed=s(1))
-        alphas = [round(0.5 + 0.05 * i, 2) for i in range(11)]
-        specs = [(0, a, 10.0 ** -k, nm, 500) for a in alphas for k in range(1, 11) for nm in (1, 2, 3)]
-        return [g], specs, "mixed", ("er-10k, 11 alpha x 10 tau x 3 norms; learned start, fp32->df64 "
-                                     "(the batched mixed-precision warm-started sweep)")
+        return Workload(name, [g], specs, "rmat-s24 ef16 seed24, alpha {.85,.95}, Linf, tau 1e-10, fp32->df64",
+                        precision="mixed")
     if name == "road24":
         g = gg.road_grid(4096, 4096, seed=s(7))
         specs = [(0, 0.85, t, nm, 500) for t in (1e-6, 1e-10) for nm in (1, 2, 3)]
-        return [g], specs, "df64", ("road-like lattice 4096 x 4096 (links kept .8, one-way .2), alpha .85, "
-                                    "tau {1e-6,1e-10} x {L1,L2,Linf}")
+        return Workload(name, [g], specs, ("road-like lattice 4096 x 4096 (links kept .8, one-way .2), alpha .85, "
+                                           "tau {1e-6,1e-10} x {L1,L2,Linf}"))
     if name == "learned":
         gs = [gg.rmat(22, 16, seed=s(3022)), gg.rmat(24, 16, seed=s(3024)), gg.config_model(8_000_000, seed=s(3008))]
-        alphas = (0.5, 0.6, 0.7, 0.8, 0.85, 0.9, 0.95)
-        specs = [(i, a, 1e-10, 1, 500) for i in range(len(gs)) for a in alphas]
-        return gs, specs, "mixed", ("unseen rmat-s22 (seed 3022), rmat-s24 (seed 3024), config model N=8M "
-                                    "(seed 3008); 7 alpha x tau 1e-10 L1; learned start, fp32->df64")
+        specs = [(i, a, 1e-10, 1, 500) for i in range(len(gs)) for a in (0.5, 0.6, 0.7, 0.8, 0.85, 0.9, 0.95)]
+        return Workload(name, gs, specs, ("unseen rmat-s22, rmat-s24, config model N=8M; 7 alpha x tau 1e-10 L1; "
+                                          "learned start, fp32->df64"), precision="mixed", learned=True)
     raise SystemExit(f"unknown workload {name}")
 
 
 def train_warm_start(B, gg, torch, sptr, epochs=30, lr=3e-3):
     """Training of the learned warm start: 32 seeded R-MAT graphs of
     scale 16 + (i mod 5), alpha 0.50..0.95; targets are this library's own
-    solves at tau 1e-12. Returns (mlp, report)."""
-    alphas = [round(0.5 + 0.05 * i, 2) for i in range(10)]
+    solves at tau 1e-12. Returns (mlp, graphs to keep alive, report)."""
     t0 = time.perf_counter()
     sets, keep = [], []
     for i in range(32):
@@ -123,7 +165,7 @@ def train_warm_start(B, gg, torch, sptr, epochs=30, lr=3e-3):
         dg = B.Graph.from_csr(g)
         keep.append(dg)
         xs = [B.Instance(dg, a, 1e-12, 1, 2000, out=torch.empty(g.n, dtype=torch.float64, device="cuda"))
-              for a in alphas]
+              for a in ALPHAS_TRAIN]
         B.pr_solve_batch(xs, outputs_on_device=True, stream=sptr)
         sets += [(dg, x.alpha, x.out) for x in xs]
     t1 = time.perf_counter()
@@ -133,7 +175,7 @@ def train_warm_start(B, gg, torch, sptr, epochs=30, lr=3e-3):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     return mlp, keep, {"train_sets": len(sets), "epochs": epochs, "lr": lr, "loss_first_set_initial": loss0,
-                       "loss_final_mean": loss, "target_solves_s": t1 - t0, "train_s": t2 - t1}
+                       "loss_final_mean": loss, "target_solves_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2)}
 
 
 # --------------------------------------------------------------------------- clocks
@@ -197,50 +239,6 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- distributed
 
-def sweep_report(B, torch, dgs, specs, last, outs, sptr):
-    """Outputs of the alpha x tau x norm sweep beyond its timing (untimed):
-    per alpha, the L1 distance of its ranks (tau 1e-10, L1) to the alpha = 0.85
-    ranks and its iteration count relative to alpha = 0.85 (the comparisons of
-    Section 2); and the same 330 instances solved in FP32 throughout, giving per
-    norm the largest tau at which an alpha < 1 instance ran into the 500 cap
-    (the stalls Section 4 describes)."""
-    ref_k = [k for k, (gi, a, t, nm, mi) in enumerate(specs) if a == 0.85 and t == 1e-10 and nm == 1][0]
-    alphas, l1, ratio = [], [], []
-    for k, (gi, a, t, nm, mi) in enumerate(specs):
-        if t == 1e-10 and nm == 1:
-            alphas.append(a)
-            l1.append(float((outs[k] - outs[ref_k]).abs().sum()))
-            ratio.append(last[k].iters / last[ref_k].iters)
-    xs = [B.Instance(dgs[gi], a, t, nm, mi) for gi, a, t, nm, mi in specs]
-    B.pr_solve_batch(xs, precision="fp32", stream=sptr)
-    stall = {}
-    for nm, name in ((1, "L1"), (2, "L2"), (3, "Linf")):
-        hit = [t for (gi, a, t, n2, mi), x in zip(specs, xs) if n2 == nm and a < 1.0 and not x.converged]
-        stall[name] = max(hit) if hit else None
-    # alpha continuation (tau 1e-10, L1, df64): each alpha starts from the
-    # previous alpha's ranks instead of 1/N
-    uni, cont, prev = [], [], None
-    for a in alphas:
-        r_u = B.pr_solve(dgs[0], a, 1e-10, 1, 500, out=torch.empty(dgs[0].n, dtype=torch.float64, device="cuda"))
-        uni.append(r_u.iters)
-        out = torch.empty(dgs[0].n, dtype=torch.float64, device="cuda")
-        r_c = B.pr_solve(dgs[0], a, 1e-10, 1, 500, out=out, init=prev) if prev is not None else r_u
-        cont.append(r_c.iters)
-        prev = out if prev is not None else r_u.ranks
-    # the paper's norm comparison over the tau sweep at alpha 0.85: geometric
-    # mean over tau of iterations, each norm relative to L1 (Section 4)
-    def gm(v):
-        v = [float(x) for x in v]
-        return math.exp(sum(math.log(x) for x in v) / len(v))
-    its = {nm: [x.iters for (gi, a, t, n2, mi), x in zip(specs, last) if a == 0.85 and n2 == nm] for nm in (1, 2, 3)}
-    norm_gm = {name: gm(its[nm]) / gm(its[1]) for nm, name in ((1, "L1"), (2, "L2"), (3, "Linf"))}
-    return {"alpha": alphas, "l1_vs_alpha_085": l1, "iterations_vs_alpha_085": ratio,
-            "tau_sweep_iteration_gm_ratio_alpha_085": norm_gm,
-            "fp32_largest_tau_hitting_cap": stall,
-            "continuation": {"iterations_uniform": uni, "iterations_from_previous_alpha": cont,
-                             "saved": sum(uni) - sum(cont)}}
-
-
 def dist_init(n_gpus):
     from paper_2108_02997_gb300 import dist
     return dist.init("cuda")
@@ -256,6 +254,66 @@ def max_over_ranks(x, world):
     return dist.max_over_ranks(x, world, "cuda")
 
 
+# --------------------------------------------------------------------------- helpers of our arm
+
+def gm(v):
+    v = [float(x) for x in v]
+    return math.exp(sum(math.log(x) for x in v) / len(v))
+
+
+def trajectories(w):
+    """(graph, alpha) -> instance indices: the iterate sequences the instances share."""
+    out = {}
+    for k, (gi, a, t, nm, mi) in enumerate(w.specs):
+        out.setdefault((gi, a), []).append(k)
+    return out
+
+
+def sweep_report(B, torch, w, last, mlp, sptr):
+    """Outputs of an alpha x tau x norm sweep on one graph beyond its timing
+    (untimed): per alpha, the L1 distance of its ranks (tau 1e-10, L1) to the
+    alpha = 0.85 ranks and its iteration count relative to alpha = 0.85 (the
+    comparisons of Section 2); the same instances solved in FP32 throughout,
+    giving per norm the largest tau at which an alpha < 1 instance ran into the
+    500 cap (the stalls Section 4 describes); and the tau 1e-10 L1 column of
+    every alpha started from the uniform vector, from the learned start, and
+    from the previous alpha's answer (alpha continuation), in one batch each."""
+    dg = w.dgs[0]
+    ks = {a: [k for k, (gi, a2, t, nm, mi) in enumerate(w.specs) if a2 == a and t == 1e-10 and nm == 1][0]
+          for a in ALPHAS_SWEEP}
+    ref = w.outs[ks[0.85]]
+    l1 = [float((w.outs[ks[a]] - ref).abs().sum()) for a in ALPHAS_SWEEP]
+    ratio = [last[ks[a]].iters / last[ks[0.85]].iters for a in ALPHAS_SWEEP]
+    xs = [B.Instance(w.dgs[gi], a, t, nm, mi) for gi, a, t, nm, mi in w.specs]
+    B.pr_solve_batch(xs, precision="fp32", stream=sptr)
+    stall = {}
+    for nm, name in ((1, "L1"), (2, "L2"), (3, "Linf")):
+        hit = [t for (gi, a, t, n2, mi), x in zip(w.specs, xs) if n2 == nm and a < 1.0 and not x.converged]
+        stall[name] = max(hit) if hit else None
+    starts = {}
+    for mode, kw in (("uniform", {}), ("learned", {"init": "learned", "mlp": mlp}), ("continuation", {"init": "chain"})):
+        ys = [B.Instance(dg, a, 1e-10, 1, 500) for a in ALPHAS_SWEEP]
+        B.pr_solve_batch(ys, stream=sptr, **kw)
+        starts[mode] = [y.iters for y in ys]
+    its = {nm: [x.iters for (gi, a, t, n2, mi), x in zip(w.specs, last) if a == 0.85 and n2 == nm] for nm in (1, 2, 3)}
+    norm_gm = {name: gm(its[nm]) / gm(its[1]) for nm, name in ((1, "L1"), (2, "L2"), (3, "Linf"))}
+    return {"alpha": ALPHAS_SWEEP, "l1_vs_alpha_085": l1, "iterations_vs_alpha_085": ratio,
+            "tau_sweep_iteration_gm_ratio_alpha_085": norm_gm,
+            "fp32_largest_tau_hitting_cap": stall,
+            "start_iterations_tau_1e-10_L1": starts,
+            "start_iterations_total": {k: sum(v) for k, v in starts.items()}}
+
+
+def cuda_ms(torch, stream, fn):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), r
+
+
 # --------------------------------------------------------------------------- our arm
 
 def run_ours(args, world, rank, local):
@@ -267,174 +325,115 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     B.lib()
-    graphs, specs, precision, desc = make_workload(args.workload, gg, rank)
-    dgs = [B.Graph.from_csr(g) for g in graphs]
-    outs = [torch.empty(graphs[gi].n, dtype=torch.float64, device="cuda") for gi, *_ in specs]
     stream = torch.cuda.current_stream()
     sptr = int(stream.cuda_stream)
-    mlp, learned = None, None
-    if args.workload in ("learned", "sweep330warm"):
-        mlp, _train_keep, learned = train_warm_start(B, gg, torch, sptr)
-    init_kw = {"init": "learned", "mlp": mlp} if mlp is not None else {}
-    total_edges = sum(g.nnz for g in graphs)
-    l2_bytes = sum(4 * (g.n + 1) + 4 * g.nnz + 24 * g.n for g in graphs)
-    inputs_large = l2_bytes > 2 * 129e6
-    flush = None if inputs_large else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    names = HEADLINE if args.workload == "headline" else (args.workload,)
+    wls = [make_workload(n, gg, rank) for n in names]
+    for w in wls:
+        w.dgs = [B.Graph.from_csr(g) for g in w.graphs]
+        w.outs = [torch.empty(w.graphs[gi].n, dtype=torch.float64, device="cuda") for gi, *_ in w.specs]
+    mlp, train = None, None
+    if any(w.learned for w in wls):
+        mlp, _train_keep, train = train_warm_start(B, gg, torch, sptr)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def insts():
-        return [B.Instance(dgs[gi], a, t, nm, mi, out=outs[k]) for k, (gi, a, t, nm, mi) in enumerate(specs)]
-
-    def step():
-        xs = insts()
-        B.pr_solve_batch(xs, precision=precision, outputs_on_device=True, stream=sptr, loop=args.loop, **init_kw)
+    def solve(w, share=True, init=None, precision=None, loop=None):
+        xs = [B.Instance(w.dgs[gi], a, t, nm, mi, out=w.outs[k]) for k, (gi, a, t, nm, mi) in enumerate(w.specs)]
+        kw = {}
+        if init == "learned":
+            kw = {"init": "learned", "mlp": mlp}
+        B.pr_solve_batch(xs, precision=precision or w.precision, outputs_on_device=True, stream=sptr, share=share,
+                         loop=loop or args.loop, **kw)
         return xs
 
+    def batched(w):
+        return solve(w, init="learned" if w.learned else None)
+
     for _ in range(args.warmup):
-        if flush is not None:
-            flush.zero_()
-        last = step()
+        flush.zero_()
+        for w in wls:
+            batched(w)
     torch.cuda.synchronize()
+    per_w = {w.name: [] for w in wls}
     launches = 0
-    times = []
+    last = {}
     barrier(world)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         for _ in range(args.steps):
-            if flush is not None:
-                flush.zero_()
-            ev0.record(stream)
-            last = step()
-            ev1.record(stream)
-            ev1.synchronize()
-            times.append(ev0.elapsed_time(ev1))
-            launches += B.pr_last_solve_stats()["launches"]
+            flush.zero_()                      # L2 flushed between steps (outside the timed regions)
+            for w in wls:
+                ms, xs = cuda_ms(torch, stream, lambda w=w: batched(w))
+                per_w[w.name].append(ms)
+                last[w.name] = xs
+                launches += B.pr_last_solve_stats()["launches"]
         torch.cuda.synchronize()
     barrier(world)
-    ms_step = sum(times) / len(times)
+    clocks = clk.summary()
+    ms_w = {n: sum(v) / len(v) for n, v in per_w.items()}
+    ms_step = sum(ms_w.values())
     ms_step_max = max_over_ranks(ms_step, world)
-    solves = len(specs)
+    solves = sum(len(w.specs) for w in wls)
     value = world * solves * 1000.0 / ms_step_max
-    inst_iters = [x.iters for x in last]
-    edges_inst = sum(graphs[gi].nnz * x.iters for (gi, *_), x in zip(specs, last))
-    # ---- roofline pass: the same solves with one launch per iteration, each
-    # launch bracketed by CUDA events on the launching stream
-    hbm, peak_kind = peaks()
-    k_ms, k_launches, bytes_per_launch = 0.0, 0, 0.0
-    g_ms, g_bytes = 0.0, 0.0
-    for gi, g in enumerate(graphs):
-        sel = [k for k, s in enumerate(specs) if s[0] == gi]
-        xs = [B.Instance(dgs[gi], specs[k][1], specs[k][2], specs[k][3], specs[k][4], out=outs[k]) for k in sel]
-        B.pr_solve_batch(xs, precision=precision, outputs_on_device=True, stream=sptr, loop="host", **init_kw)
-        st = B.pr_last_solve_stats()
-        n_src = int((g.outdeg > 0).sum())
-        # one pass, one column: offsets, indices, gathered contributions (each
-        # source once), previous ranks, new ranks, out-degrees
-        b = 4.0 * (g.n + 1) + 4.0 * g.nnz + 8.0 * n_src + 8.0 * g.n + 8.0 * g.n + 4.0 * g.n
-        # its gather kernel: offsets, indices, gathered contributions, row sums written
-        bg = 4.0 * (g.n + 1) + 4.0 * g.nnz + 8.0 * n_src + 8.0 * g.n
-        passes = st["passes"]
-        k_ms += st["kernel_ms"]
-        k_launches += passes
-        bytes_per_launch += b * passes
-        if st["gather_ms"] > 0:
-            g_ms += st["gather_ms"]
-            g_bytes += bg * passes
-    avg_launch_ms = k_ms / max(k_launches, 1)
-    bytes_avg = bytes_per_launch / max(k_launches, 1)
-    achieved = bytes_avg / (avg_launch_ms * 1e-3) / 1e9
-    pass_roofline = {"achieved": achieved, "frac": achieved / hbm, "avg_pass_us": avg_launch_ms * 1e3,
-                     "algorithmic_bytes_per_pass": bytes_avg, "unit": "GB/s"}
-    if g_ms > 0:
-        # the dominant kernel is the gather kernel of the split passes
-        kernel_name = "pr_iter_kernel (gather half of a one-column pass)"
-        avg_kernel_ms = g_ms / max(k_launches, 1)
-        kernel_bytes = g_bytes / max(k_launches, 1)
-    else:
-        kernel_name = "pr_iter_kernel (whole pass)"
-        avg_kernel_ms = avg_launch_ms
-        kernel_bytes = bytes_avg
-    kernel_achieved = kernel_bytes / (avg_kernel_ms * 1e-3) / 1e9
-    gteps_device = total_edges * (k_launches / max(len(graphs), 1)) / (ms_step * 1e-3) / 1e9
-    if learned is not None:
-        # iterations from the uniform start, same batched mixed-precision sweep
-        xs_u = [B.Instance(dgs[gi], a, t, nm, mi, out=outs[k]) for k, (gi, a, t, nm, mi) in enumerate(specs)]
-        B.pr_solve_batch(xs_u, precision=precision, outputs_on_device=True, stream=sptr)
-        learned["iterations_uniform"] = [x.iters for x in xs_u]
-        learned["iterations_learned"] = inst_iters
-        learned["iterations_saved_total"] = sum(x.iters for x in xs_u) - sum(inst_iters)
-        # cost of the start itself: features + MLP + softmax, per graph (CUDA events)
-        ws = []
-        for gi, dg in enumerate(dgs):
-            buf = torch.empty(dg.n, dtype=torch.float64, device="cuda")
-            mlp.warm_start(dg, 0.85, out=buf, stream=sptr)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            mlp.warm_start(dg, 0.85, out=buf, stream=sptr)
-            e1.record(stream)
-            e1.synchronize()
-            ws.append({"n": dg.n, "ms": e0.elapsed_time(e1)})
-        learned["warm_start_ms"] = ws
-        if precision != "df64":
-            # the same comparison with df64 throughout (no FP32 phase)
-            its = {}
-            for mode, kw in (("uniform", {}), ("learned", init_kw)):
-                xs_d = [B.Instance(dgs[gi], a, t, nm, mi, out=outs[k]) for k, (gi, a, t, nm, mi) in enumerate(specs)]
-                B.pr_solve_batch(xs_d, precision="df64", outputs_on_device=True, stream=sptr, **kw)
-                its[mode] = [x.iters for x in xs_d]
-            learned["df64"] = {"iterations_uniform": its["uniform"], "iterations_learned": its["learned"],
-                               "iterations_saved_total": sum(its["uniform"]) - sum(its["learned"])}
-    sweep = sweep_report(B, torch, dgs, specs, last, outs, sptr) if args.workload.startswith("sweep330") else None
-    # ---- plain per-instance GPU solver on the same resident graphs: every
-    # instance alone through pr_solve, one launch per iteration and a host read
-    # of the stop flag after each (the baseline the batched path is measured against)
-    plain = None
+    # ---- per workload: the plain per-instance solver, the batch without
+    # trajectory sharing, the learned start's net effect
+    records = {}
+    for w in wls:
+        xs = last[w.name]
+        rec = {"instances": len(w.specs), "graphs": len(w.graphs), "edges": sum(g.nnz for g in w.graphs),
+               "trajectories": len(trajectories(w)), "batched_ms": ms_w[w.name],
+               "batched": {"precision": w.precision, "start": "learned" if w.learned else "uniform"},
+               "iterations_total": sum(x.iters for x in xs),
+               "converged": sum(1 for x in xs if x.converged)}
+        # edges traversed: each trajectory's graph times its last tap's iterations
+        tr = trajectories(w)
+        rec["gteps_trajectories"] = sum(w.graphs[gi].nnz * max(xs[k].iters for k in ks)
+                                        for (gi, a), ks in tr.items()) / (ms_w[w.name] * 1e-3) / 1e9
+        if not args.no_plain:
+            t_plain = 0.0
+            for k, (gi, a, t, nm, mi) in enumerate(w.specs):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                B.pr_solve(w.dgs[gi], a, t, nm, mi, out=w.outs[k], loop="host", stream=sptr, precision="df64")
+                torch.cuda.synchronize()
+                t_plain += time.perf_counter() - t0
+            rec["plain_ms"] = t_plain * 1000.0
+            rec["ratio"] = rec["plain_ms"] / rec["batched_ms"]
+            ms_ns, _ = cuda_ms(torch, stream, lambda w=w: solve(w, share=False, init="learned" if w.learned else None))
+            rec["batched_no_share_ms"] = ms_ns
+            rec["ratio_no_share"] = rec["plain_ms"] / ms_ns
+        if w.learned:
+            ms_u, xu = cuda_ms(torch, stream, lambda w=w: solve(w))
+            rec["uniform_start"] = {"batched_ms": ms_u, "iterations_total": sum(x.iters for x in xu),
+                                    "learned_saves_iterations": sum(x.iters for x in xu) - rec["iterations_total"],
+                                    "learned_net_ms": ms_u - ms_w[w.name]}
+            # the start's own cost: features once per graph, network and softmax per alpha
+            ws = []
+            for dg in w.dgs:
+                buf = torch.empty(dg.n, dtype=torch.float64, device="cuda")
+                mlp.warm_start(dg, 0.85, out=buf, stream=sptr)
+                ms1, _ = cuda_ms(torch, stream, lambda dg=dg, buf=buf: mlp.warm_start(dg, 0.85, out=buf, stream=sptr))
+                ws.append({"n": dg.n, "ms": ms1})
+            rec["warm_start_ms_per_call"] = ws
+        if w.name.startswith("sweep330"):
+            rec["sweep_report"] = sweep_report(B, torch, w, xs, mlp, sptr)
+        records[w.name] = rec
+    gm_ratio = gm_ratio_ns = None
     if not args.no_plain:
-        t_plain = 0.0
-        for k, (gi, a, t, nm, mi) in enumerate(specs):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            B.pr_solve(dgs[gi], a, t, nm, mi, out=outs[k], loop="host", stream=sptr,
-                       precision="df64" if precision == "mixed" else precision)
-            torch.cuda.synchronize()
-            t_plain += time.perf_counter() - t0
-        plain = {"solves_per_s": solves / t_plain, "ms_per_step": t_plain * 1000.0,
-                 "what": "each instance alone, pr_solve with one launch per iteration and a host read of the stop flag",
-                 "speedup_of_value": (solves * 1000.0 / ms_step) / (solves / t_plain)}
-    # ---- e2e: graph creation from pinned host arrays + solve + ranks to host, every step
-    e2e = None
-    if not args.no_e2e:
-        pinned = []
-        for g in graphs:
-            off = torch.from_numpy(g.offsets).pin_memory().numpy()
-            src = torch.from_numpy(g.sources).pin_memory().numpy()
-            od = torch.from_numpy(g.outdeg).pin_memory().numpy()
-            pinned.append((off, src, od))
-        host_outs = [torch.empty(graphs[gi].n, dtype=torch.float64).pin_memory().numpy() for gi, *_ in specs]
-        h2d = sum(a.nbytes + b.nbytes + c.nbytes for a, b, c in pinned)
-        d2h = sum(o.nbytes for o in host_outs)
-        et = []
-        for i in range(args.warmup + args.steps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            hg = [B.Graph(*p) for p in pinned]
-            xs = [B.Instance(hg[gi], a, t, nm, mi, out=host_outs[k]) for k, (gi, a, t, nm, mi) in enumerate(specs)]
-            B.pr_solve_batch(xs, precision=precision, stream=sptr)
-            for h in hg:
-                h.close()
-            t1 = time.perf_counter()
-            if i >= args.warmup:
-                et.append((t1 - t0) * 1000.0)
-        e2e_ms = max_over_ranks(sum(et) / len(et), world)
-        e2e = {"value": world * solves * 1000.0 / e2e_ms, "unit": "solves/s", "ms_per_step": e2e_ms,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-    # ---- CPU baseline: the oracle on the host cores, bounded sample
+        gm_ratio = gm([records[n]["ratio"] for n in records])
+        gm_ratio_ns = gm([records[n]["ratio_no_share"] for n in records])
+    # ---- roofline: the one-column gather kernel at R-MAT scale 22, one launch
+    # per iteration, each launch bracketed by CUDA events on the solve's stream
+    roofline = roofline_s22(B, gg, torch, sptr, rank, wls if args.workload == "rmat22" else None)
+    # ---- e2e: through the C ABI from pinned host arrays, every step: graph
+    # creation (host CSR to the device), the batched solves, per-instance
+    # results and each trajectory's answer (its last stopping rule) to the host
+    e2e = None if args.no_e2e else run_e2e(B, torch, wls, mlp, sptr, args, world)
+    # ---- CPU baseline: the oracle on the host cores, bounded samples
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(graphs, specs, inst_iters, args.cpu_seconds)
-    clocks = clk.summary()
-    ratio, tsrc = kernel_traffic_ratio()
+        cpu = cpu_baseline(wls, args.cpu_seconds)
+    precisions = sorted({w.precision for w in wls})
     line = {
         "metric": METRIC,
         "value": value,
@@ -446,49 +445,128 @@ def run_ours(args, world, rank, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"df64": "df64 (f32x2)", "mixed": "f32 -> df64", "fp64": "f64", "fp32": "f32"}[precision],
+        "dtype": "df64 (f32x2); f32 -> df64 where the planner picks mixed precision"
+        if "auto" in precisions or "mixed" in precisions else "df64 (f32x2)",
         "data": "synthetic (seeded generators; paper's SuiteSparse graphs unavailable)",
-        "config": {"workload": desc, "instances": solves, "graphs": len(graphs),
-                   "edges": total_edges, "parallelism": f"instance batches x{world} (one per rank, no collective)",
-                   "l2": "inputs larger than L2" if inputs_large else "L2 flushed (256 MB write) between steps"},
-        "iterations": inst_iters,
-        "gteps_instances": edges_inst / (ms_step * 1e-3) / 1e9,
-        "gteps_device": gteps_device,
-        "roofline": {"bound": "hbm", "achieved": kernel_achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": kernel_achieved / hbm,
-                     "traffic": (ratio * kernel_bytes) if ratio and precision == "df64" else None,
-                     "traffic_source": tsrc if ratio and precision == "df64" else None,
-                     "kernel": kernel_name, "avg_launch_us": avg_kernel_ms * 1e3,
-                     "algorithmic_bytes_per_launch": kernel_bytes, "peak_source": peak_kind,
-                     "pass": pass_roofline},
+        "config": {"workload": " + ".join(w.name for w in wls) if len(wls) > 1 else wls[0].desc,
+                   "workloads": {w.name: w.desc for w in wls},
+                   "instances": solves, "graphs": sum(len(w.graphs) for w in wls),
+                   "edges": sum(sum(g.nnz for g in w.graphs) for w in wls),
+                   "parallelism": f"instance batches x{world} (one per rank, no collective)",
+                   "l2": "L2 flushed (256 MB write) before every step"},
+        "workloads": records,
+        "gm_ratio": gm_ratio,
+        "gm_ratio_no_share": gm_ratio_ns,
+        "gm_ratio_what": ("geometric mean over the workloads of (plain per-instance time) / (batched time); "
+                          "plain = every instance alone through pr_solve, df64, uniform start, one launch per "
+                          "iteration and a host read of the stop flag"),
+        "learned_training": train,
+        "roofline": roofline,
         "e2e": e2e,
-        "plain_gpu": plain,
-        "learned_start": learned,
-        "sweep_report": sweep,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": launches,
     }
     if rank == 0:
         print(json.dumps(line))
-    for d in dgs:
-        d.close()
+    for w in wls:
+        for d in w.dgs:
+            d.close()
+
+
+def roofline_s22(B, gg, torch, sptr, rank, have):
+    """The gather kernel's and the whole pass's achieved bandwidth on R-MAT
+    scale 22 against the measured copy bandwidth. Algorithmic bytes per
+    one-column pass (the method's data): offsets 4(N+1), in-edge indices 4E,
+    each source's contribution once 8 N_src, previous ranks 8N, new ranks 8N,
+    out-degrees 4N; of these the gather kernel moves the first three."""
+    if have is not None:
+        w = have[0]
+    else:
+        w = make_workload("rmat22", gg, rank)
+        w.dgs = [B.Graph.from_csr(w.graphs[0])]
+        w.outs = [torch.empty(w.graphs[0].n, dtype=torch.float64, device="cuda") for _ in w.specs]
+    g, dg = w.graphs[0], w.dgs[0]
+    hbm, peak_kind = peaks()
+    xs = [B.Instance(dg, a, t, nm, mi, out=w.outs[k]) for k, (gi, a, t, nm, mi) in enumerate(w.specs)]
+    B.pr_solve_batch(xs, outputs_on_device=True, stream=sptr, loop="host")
+    st = B.pr_last_solve_stats()
+    n_src = int((g.outdeg > 0).sum())
+    b_pass = 4.0 * (g.n + 1) + 4.0 * g.nnz + 8.0 * n_src + 8.0 * g.n + 8.0 * g.n + 4.0 * g.n
+    b_gather = 4.0 * (g.n + 1) + 4.0 * g.nnz + 8.0 * n_src
+    passes = max(st["passes"], 1)
+    pass_us = st["kernel_ms"] / passes * 1e3
+    gather_us = st["gather_ms"] / passes * 1e3
+    ach = b_gather / (gather_us * 1e-6) / 1e9
+    ratio, tsrc = kernel_traffic_ratio()
+    if have is None:
+        dg.close()
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": ratio * b_gather if ratio else None, "traffic_source": tsrc,
+            "kernel": "pr_gather_hub_kernel<df64> (gather half of a one-column pass)",
+            "workload": "rmat-s22 ef16 seed22 (N 4,194,304, E %d), alpha .85, tau {1e-6,1e-10} x {L1,L2,Linf}, df64"
+                        % g.nnz,
+            "avg_launch_us": gather_us, "algorithmic_bytes_per_launch": b_gather, "launches": passes,
+            "peak_source": peak_kind, "frac_of": "measured copy bandwidth" if peak_kind == "measured" else "fallback",
+            "pass": {"avg_pass_us": pass_us, "algorithmic_bytes_per_pass": b_pass,
+                     "achieved": b_pass / (pass_us * 1e-6) / 1e9, "frac": b_pass / (pass_us * 1e-6) / 1e9 / hbm,
+                     "update_kernel_us": st["update_ms"] / passes * 1e3}}
+
+
+def run_e2e(B, torch, wls, mlp, sptr, args, world):
+    import numpy as np
+    pinned = []
+    for w in wls:
+        pinned.append([(torch.from_numpy(g.offsets).pin_memory().numpy(), torch.from_numpy(g.sources).pin_memory().numpy(),
+                        torch.from_numpy(g.outdeg).pin_memory().numpy()) for g in w.graphs])
+    # each trajectory's answer at its last stopping rule (the last instance of the trajectory)
+    picks = []
+    for w in wls:
+        picks.append([ks[-1] for ks in trajectories(w).values()])
+    host = [[torch.empty(w.graphs[w.specs[k][0]].n, dtype=torch.float64).pin_memory() for k in pk]
+            for w, pk in zip(wls, picks)]
+    h2d = sum(a.nbytes + b.nbytes + c.nbytes for pw in pinned for a, b, c in pw)
+    d2h = sum(h.numel() * 8 for hw in host for h in hw) + sum(len(w.specs) * 24 for w in wls)
+    reps = min(args.steps, 5)
+    et = []
+    for i in range(1 + reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for w, pw, pk, hw in zip(wls, pinned, picks, host):
+            hg = [B.Graph(*p) for p in pw]
+            xs = [B.Instance(hg[gi], a, t, nm, mi, out=w.outs[k]) for k, (gi, a, t, nm, mi) in enumerate(w.specs)]
+            kw = {"init": "learned", "mlp": mlp} if w.learned else {}
+            B.pr_solve_batch(xs, precision=w.precision, outputs_on_device=True, stream=sptr, **kw)
+            for k, h in zip(pk, hw):
+                h.copy_(w.outs[k], non_blocking=True)
+            torch.cuda.synchronize()
+            for h in hg:
+                h.close()
+        t1 = time.perf_counter()
+        if i >= 1:
+            et.append((t1 - t0) * 1000.0)
+    e2e_ms = max_over_ranks(sum(et) / len(et), world)
+    solves = sum(len(w.specs) for w in wls)
+    return {"value": world * solves * 1000.0 / e2e_ms, "unit": "solves/s", "ms_per_step": e2e_ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": reps,
+            "what": ("graph creation from pinned host CSR arrays, pr_solve_batch, every instance's iterations/"
+                     "error and each trajectory's final ranks to pinned host memory")}
 
 
 def oracle_sample(graphs, specs, budget_s, cores):
-    """Time the CPU oracle on the workload within about budget_s seconds.
+    """Time the CPU oracle on a workload within about budget_s seconds.
 
     Instances sharing (graph, alpha) are one trajectory read at several stopping
     rules (oracle.pagerank_taps). Trajectories are solved in workload order for
     real while the estimated cost fits the budget; the rest are costed as
     (iterations) x (measured time of one oracle update on that graph), with
-    iterations from the first solved trajectory of the same graph when there
-    is one, else Section 1's estimate round(log10 tau / log10 alpha)."""
+    iterations from Section 1's estimate round(log10 tau / log10 alpha)."""
     import numpy as np
 
     from oracle import oracle as orc
     t_upd = {}
-    for gi, g in enumerate(graphs):
+    for gi in sorted({s[0] for s in specs}):
+        g = graphs[gi]
         r = np.full(g.n, 1.0 / g.n)
         t0 = time.perf_counter()
         r, _ = orc.step(g, 0.85, r, threads=cores)
@@ -498,31 +576,40 @@ def oracle_sample(graphs, specs, budget_s, cores):
     for k, (gi, a, t, nm, mi) in enumerate(specs):
         groups.setdefault((gi, a), []).append(k)
     spent, solved, modeled = 0.0, 0, 0.0
-    iters_seen = {}
     for (gi, a), ks in groups.items():
         taps = [(specs[k][2], specs[k][3], specs[k][4]) for k in ks]
         est = max(min(mi, orc.estimate_iterations(t, a) if 0 < a < 1 else mi) for t, nm, mi in taps)
         if spent + t_upd[gi] * est <= budget_s:
             t0 = time.perf_counter()
-            res = orc.pagerank_taps(graphs[gi], a, taps, threads=cores)
+            orc.pagerank_taps(graphs[gi], a, taps, threads=cores)
             spent += time.perf_counter() - t0
             solved += len(ks)
-            iters_seen[(gi, a)] = [x.iters for x in res]
         else:
             for t, nm, mi in taps:
                 it = min(mi, orc.estimate_iterations(t, a)) if 0 < a < 1 else mi
                 modeled += t_upd[gi] * max(it, 1)
     total_time = spent + modeled
-    value = len(specs) / total_time
     kind = "measured" if modeled == 0 else ("mixed" if solved else "extrapolated")
-    sample = (f"{solved} of {len(specs)} instances solved by the oracle ({spent:.1f}s); "
-              f"{len(specs) - solved} costed as estimated iterations x measured update time ({kind})")
-    return {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
+    return {"time_s": total_time, "solved": solved, "spent_s": spent, "kind": kind}
 
 
-def cpu_baseline(graphs, specs, inst_iters, seconds):
+def cpu_baseline(wls, seconds):
+    """The oracle as it stands on a bounded sample of every workload, on all
+    host cores and on one (the paper's program is single-threaded)."""
     from oracle import oracle as orc
-    return oracle_sample(graphs, specs, seconds, orc.default_threads())
+    out = {}
+    for cores in (orc.default_threads(), 1):
+        t_all, parts = 0.0, []
+        for w in wls:
+            r = oracle_sample(w.graphs, w.specs, seconds / len(wls), cores)
+            t_all += r["time_s"]
+            parts.append(f"{w.name}: {r['solved']} of {len(w.specs)} solved ({r['spent_s']:.1f}s), rest {r['kind']}")
+        out[cores] = (sum(len(w.specs) for w in wls) / t_all, "; ".join(parts))
+    allc = orc.default_threads()
+    return {"value": out[allc][0], "unit": "solves/s", "cores": allc, "kind": "oracle",
+            "sample": out[allc][1] + " (unsolved instances costed as Section 1's estimated iterations x measured "
+                                     "update time)",
+            "single_thread": {"value": out[1][0], "unit": "solves/s", "cores": 1, "sample": out[1][1]}}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -534,20 +621,33 @@ def run_reference(args, world, rank):
     from oracle import oracle as orc
     from paper_2108_02997_gb300 import graphgen as gg
     orc.build()
-    graphs, specs, precision, desc = make_workload(args.workload, gg)
+    names = HEADLINE if args.workload == "headline" else (args.workload,)
+    wls = [make_workload(n, gg) for n in names]
     cores = orc.default_threads()
-    budget = max(5.0, args.cpu_seconds)
+    budget = max(1.0, args.ref_seconds)
+    w0 = wls[0]
     for _ in range(args.warmup):
-        oracle_sample(graphs, specs[:1], 1.0, cores)
-    vals = [oracle_sample(graphs, specs, budget, cores) for _ in range(args.steps)]
-    v = statistics.mean(x["value"] for x in vals)
+        oracle_sample(w0.graphs, w0.specs[:1], 0.2, cores)
+    vals, samples = [], []
+    for _ in range(args.steps):
+        t, parts = 0.0, []
+        for w in wls:
+            r = oracle_sample(w.graphs, w.specs, budget / len(wls), cores)
+            t += r["time_s"]
+            parts.append(f"{w.name}: {r['solved']} of {len(w.specs)} solved, rest {r['kind']}")
+        vals.append(sum(len(w.specs) for w in wls) / t)
+        samples.append("; ".join(parts))
+    v = statistics.mean(vals)
+    solves = sum(len(w.specs) for w in wls)
     line = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": len(specs) / v * 1000.0, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": solves / v * 1000.0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "instances": len(specs), "graphs": len(graphs)},
+            "config": {"workload": " + ".join(w.name for w in wls) if len(wls) > 1 else wls[0].desc,
+                       "instances": solves, "graphs": sum(len(w.graphs) for w in wls)},
             "impl": "reference",
             "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v, "unit": "solves/s",
-                             "sample": vals[-1]["sample"]},
+                             "sample": samples[-1] + " (unsolved instances costed as Section 1's estimated "
+                                                     "iterations x measured update time)"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -558,15 +658,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22",
-                    choices=["rmat22", "rmat21", "sweep330", "sweep330warm", "multi64", "rmat24mixed", "learned",
-                             "road24"])
+    ap.add_argument("--workload", default="headline", choices=("headline",) + SINGLE)
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="device loop of the timed solves (host: one launch per iteration)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-instance GPU solver comparison")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle budget of the cpu_baseline sample")
+    ap.add_argument("--ref-seconds", type=float, default=6.0, help="oracle budget per step of --impl reference")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -22,8 +22,19 @@
  *   - Host pointers are plain CPU memory. Device pointers are CUDA global
  *     memory of the current device. Which one an argument is, is stated per
  *     argument.
- *   - The library allocates device memory with cudaMalloc and releases it
- *     before returning (solves) or in pr_graph_destroy (graphs).
+ *   - Device memory. A graph's arrays are allocated by pr_graph_create and
+ *     freed by pr_graph_destroy. Everything else (solve and training
+ *     workspaces, graph-creation scratch) comes from one stream-ordered
+ *     memory pool per device (cudaMallocFromPoolAsync on the call's stream,
+ *     cudaFreeAsync before the call returns; cudaMalloc only if the pool
+ *     cannot serve a request). The pool keeps up to 4 GiB of freed memory
+ *     reserved between calls so that repeated calls do not pay the
+ *     synchronising cudaMalloc/cudaFree; pr_workspace_info reports what it
+ *     holds and pr_workspace_release returns the unused part to the device.
+ *     pr_solve_noalloc allocates nothing (see there).
+ *   - Per-device set-up (kernel attributes, residencies, the tuning table,
+ *     the no-alloc array's address) is done once per device and process; the
+ *     library does not survive a cudaDeviceReset of a device it has used.
  *   - A graph handle may be used by one solve at a time.
  *   - Calls are synchronous with respect to the host unless stated otherwise;
  *     device work is issued on the stream given in pr_options (NULL: the
@@ -65,19 +76,37 @@ typedef enum pr_norm { PR_NORM_L1 = 1, PR_NORM_L2 = 2, PR_NORM_LINF = 3 } pr_nor
  *                 or below switch_tol, then DF64 refinement to tau. The
  *                 dangling sum, c0 and the norms stay FP64-class throughout.
  *  PR_PREC_FP32 : FP32 ranks/gathers/accumulation throughout (norms FP64-class).
+ *  PR_PREC_AUTO : per graph of a pr_solve_batch call, PR_PREC_MIXED where the
+ *                 grouping planner's cost model (the launch times pr_graph_tune
+ *                 measures for FP32 and DF64, and each column's estimated
+ *                 iterations in both phases, the refinement phase damping the
+ *                 FP32 iterate's rounding noise at the rate alpha) predicts it
+ *                 cheaper than DF64 throughout, else PR_PREC_DF64. Graphs with a
+ *                 single column, and every graph under PR_GROUP_PACK or
+ *                 PR_GROUP_SINGLE, run DF64. The accuracy is that of the
+ *                 precision chosen.
  */
 typedef enum pr_precision {
     PR_PREC_DF64 = 0,
     PR_PREC_FP64 = 1,
     PR_PREC_MIXED = 2,
-    PR_PREC_FP32 = 3
+    PR_PREC_FP32 = 3,
+    PR_PREC_AUTO = 4
 } pr_precision;
 
 /* Start vector r^0. */
 typedef enum pr_init {
     PR_INIT_UNIFORM = 0,  /* 1/N everywhere */
     PR_INIT_USER = 1,     /* caller's vector, used as given (not renormalised) */
-    PR_INIT_LEARNED = 2   /* MLP warm start (pr_mlp), renormalised to sum 1 */
+    PR_INIT_LEARNED = 2,  /* MLP warm start (pr_mlp), renormalised to sum 1 */
+    PR_INIT_CHAIN = 3     /* alpha continuation (pr_solve_batch): on each graph
+                             the columns (iterate sequences) are taken in
+                             increasing alpha; the first starts from 1/N and each
+                             later one from the final iterate of the one before
+                             it (its answer at its last stopping rule). The
+                             columns of one graph then run one after another
+                             (those of different graphs side by side); the
+                             alpha sweep of Section 2 in the order it is swept */
 } pr_init;
 
 /* Device-side loop control. */
@@ -230,9 +259,15 @@ pr_status pr_solve(const pr_graph *g, double alpha, double tol, int32_t norm, in
  *   - the working set is about 32 bytes per vertex plus small tables; a graph
  *     that does not fit (about n > 1.2 million) is rejected with PR_EINVAL
  *     and a message stating the bytes needed;
+ *   - the graph must live on the current device, and d_ranks_out must be
+ *     device memory of that device (checked with cudaPointerGetAttributes;
+ *     PR_EINVAL otherwise);
  *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture;
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     life of the process;
+ *   - the call reads the device's stop flag back after every pass and
+ *     synchronises the stream each time, so it must not be called on a stream
+ *     that is being captured into a CUDA graph;
  *   - every call shares the one array and overwrites what the previous call
  *     left there: calls that overlap on the GPU (other streams, other host
  *     threads) race and corrupt each other; serialise them.
@@ -397,6 +432,21 @@ pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel
  * loop was PR_LOOP_GRAPH. Host pointers, each may be NULL.
  */
 pr_status pr_last_solve_kernel_ms(double *gather_ms, double *update_ms);
+
+/*
+ * The workspace pool of the current device (no counterpart in the paper):
+ * bytes it has reserved from the device, bytes lent out to calls in flight
+ * now, and the most ever lent out at once (host pointers, each may be NULL).
+ * All zero before the first call that used the pool on this device.
+ */
+pr_status pr_workspace_info(int64_t *reserved_bytes, int64_t *used_bytes, int64_t *used_high_bytes);
+
+/*
+ * Return the pool's reserved but unused memory on the current device to the
+ * device (after synchronising the device); later calls reserve again as
+ * needed. PR_ECUDA on failure.
+ */
+pr_status pr_workspace_release(void);
 
 /* Message for the last error on this thread ("" if none). */
 const char *pr_last_error(void);

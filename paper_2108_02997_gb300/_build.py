@@ -3,7 +3,9 @@
 * ``libprgraphgen.so`` — the seeded graph generators (plain C, gcc).
 * ``libpagerank.so``  — the C-ABI PageRank library (CUDA, nvcc, sm_103a only).
 
-Each library is rebuilt when a source file is newer than it. The CUDA
+Each library is rebuilt when a source file is newer than it, or when the
+extra compiler definitions in the environment variable PR_NVCC_FLAGS (tuning
+constants such as -DPR_HUB_BYTES=...) differ from the last build's. The CUDA
 translation units compile in parallel to keep the build within a minute.
 """
 from __future__ import annotations
@@ -64,11 +66,16 @@ def build_graphgen(force: bool = False) -> Path:
 def build_pagerank(force: bool = False, verbose_ptxas: bool = False) -> Path:
     srcs = [CSRC / s for s in CU_SOURCES]
     hdrs = [CSRC / h for h in CU_HEADERS] + sorted(INCLUDE.glob("*.h"))
+    extra = os.environ.get("PR_NVCC_FLAGS", "").split()
+    stamp = BUILD / "flags.txt"
+    flags_changed = (stamp.read_text() if stamp.exists() else "") != " ".join(extra)
+    if flags_changed:
+        force = True
     if not (force or _stale(PAGERANK_SO, srcs + hdrs + [Path(__file__)])):
         return PAGERANK_SO
     nvcc = _nvcc()
     BUILD.mkdir(exist_ok=True)
-    flags = ARCH + NVCC_FLAGS + ["-I", str(INCLUDE), "-I", str(CSRC)]
+    flags = ARCH + NVCC_FLAGS + extra + ["-I", str(INCLUDE), "-I", str(CSRC)]
     if verbose_ptxas:
         flags += ["-Xptxas", "-v"]
 
@@ -85,6 +92,7 @@ def build_pagerank(force: bool = False, verbose_ptxas: bool = False) -> Path:
     tmp = PAGERANK_SO.with_suffix(".so.tmp")
     _run([nvcc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lcudart", "-lcuda"])
     os.replace(tmp, PAGERANK_SO)
+    stamp.write_text(" ".join(extra))
     return PAGERANK_SO
 
 

@@ -23,14 +23,15 @@ from . import _build
 
 PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT, PR_ESTATE, PR_ENOTSUP = range(7)
 PR_NORM_L1, PR_NORM_L2, PR_NORM_LINF = 1, 2, 3
-PR_PREC_DF64, PR_PREC_FP64, PR_PREC_MIXED, PR_PREC_FP32 = 0, 1, 2, 3
-PR_INIT_UNIFORM, PR_INIT_USER, PR_INIT_LEARNED = 0, 1, 2
+PR_PREC_DF64, PR_PREC_FP64, PR_PREC_MIXED, PR_PREC_FP32, PR_PREC_AUTO = 0, 1, 2, 3, 4
+PR_INIT_UNIFORM, PR_INIT_USER, PR_INIT_LEARNED, PR_INIT_CHAIN = 0, 1, 2, 3
 PR_LOOP_GRAPH, PR_LOOP_HOST = 0, 1
 PR_GROUP_AUTO, PR_GROUP_PACK, PR_GROUP_SINGLE = 0, 1, 2
 GROUPS = {"auto": PR_GROUP_AUTO, "pack": PR_GROUP_PACK, "single": PR_GROUP_SINGLE}
 PR_KERNELS_AUTO, PR_KERNELS_FUSED, PR_KERNELS_SPLIT = 0, 1, 2
 KERNELS = {"auto": PR_KERNELS_AUTO, "fused": PR_KERNELS_FUSED, "split": PR_KERNELS_SPLIT}
-PRECISIONS = {"df64": PR_PREC_DF64, "fp64": PR_PREC_FP64, "mixed": PR_PREC_MIXED, "fp32": PR_PREC_FP32}
+PRECISIONS = {"df64": PR_PREC_DF64, "fp64": PR_PREC_FP64, "mixed": PR_PREC_MIXED, "fp32": PR_PREC_FP32,
+              "auto": PR_PREC_AUTO}
 NORMS = {"L1": 1, "L2": 2, "Linf": 3, 1: 1, 2: 2, 3: 3}
 MLP_PARAMS = 64 * 5 + 64 + 64 * 64 + 64 + 64 + 1
 
@@ -83,6 +84,8 @@ SIGNATURES = {
     "pr_plan_columns": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "pr_plan_columns_shared": ([_i32, _vp, _vp, _d, _vp, _vp, _vp], _i32),
     "pr_solve_noalloc": ([_vp, _d, _d, _i32, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
+    "pr_workspace_info": ([_vp, _vp, _vp], _i32),
+    "pr_workspace_release": ([], _i32),
     "pr_last_error": ([], C.c_char_p),
     "pr_status_string": ([_i32], C.c_char_p),
     "pr_version": ([], _i32),
@@ -212,6 +215,10 @@ def _make_options(precision="df64", init=None, loop="graph", stream=None, share=
     elif init == "learned":
         o.init = PR_INIT_LEARNED
         o.mlp = mlp.handle if mlp is not None else None
+    elif init == "chain":
+        o.init = PR_INIT_CHAIN
+    elif init is not None:
+        raise ValueError(f"unknown start {init!r}")
     return o, keep
 
 
@@ -347,6 +354,18 @@ def plan_columns_shared(iters, us_per_launch, latency_us):
     _check(lib().pr_plan_columns_shared(it.size, it.ctypes.data, us.ctypes.data, float(latency_us), job.ctypes.data,
                                         wid.ctypes.data, C.byref(cost)), "pr_plan_columns_shared")
     return job, wid, cost.value
+
+
+def workspace_info():
+    """(reserved, used, used_high) bytes of the current device's workspace pool."""
+    r, u, h = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().pr_workspace_info(C.byref(r), C.byref(u), C.byref(h)), "pr_workspace_info")
+    return r.value, u.value, h.value
+
+
+def workspace_release():
+    """Return the workspace pool's unused reserved memory to the device."""
+    _check(lib().pr_workspace_release(), "pr_workspace_release")
 
 
 def pr_last_solve_stats():

@@ -1,4 +1,5 @@
 // pr_api.cu — C-ABI entry points: argument checks, batching, error reporting.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -77,13 +78,13 @@ extern "C" void pr_options_default(pr_options *opt) {
 namespace {
 
 pr_status check_options(const pr_options &o) {
-    if (o.precision < PR_PREC_DF64 || o.precision > PR_PREC_FP32) return pr_fail(PR_EINVAL, "unknown precision");
-    if (o.init < PR_INIT_UNIFORM || o.init > PR_INIT_LEARNED) return pr_fail(PR_EINVAL, "unknown init mode");
+    if (o.precision < PR_PREC_DF64 || o.precision > PR_PREC_AUTO) return pr_fail(PR_EINVAL, "unknown precision");
+    if (o.init < PR_INIT_UNIFORM || o.init > PR_INIT_CHAIN) return pr_fail(PR_EINVAL, "unknown init mode");
     if (o.loop != PR_LOOP_GRAPH && o.loop != PR_LOOP_HOST) return pr_fail(PR_EINVAL, "unknown loop mode");
     if (o.group < PR_GROUP_AUTO || o.group > PR_GROUP_SINGLE) return pr_fail(PR_EINVAL, "unknown group mode");
     if (o.max_passes < 0) return pr_fail(PR_EINVAL, "max_passes must be >= 0");
     if (o.kernels < PR_KERNELS_AUTO || o.kernels > PR_KERNELS_SPLIT) return pr_fail(PR_EINVAL, "unknown kernels mode");
-    if (o.precision == PR_PREC_MIXED && !(o.switch_tol > 0.0 && std::isfinite(o.switch_tol)))
+    if ((o.precision == PR_PREC_MIXED || o.precision == PR_PREC_AUTO) && !(o.switch_tol > 0.0 && std::isfinite(o.switch_tol)))
         return pr_fail(PR_EINVAL, "switch_tol must be positive and finite");
     if (o.init == PR_INIT_LEARNED && !pr_mlp_valid(o.mlp)) return pr_fail(PR_EINVAL, "PR_INIT_LEARNED needs a live pr_mlp");
     return PR_OK;
@@ -91,6 +92,11 @@ pr_status check_options(const pr_options &o) {
 
 pr_status check_instance(const pr_instance &in) {
     if (!pr_graph_valid(in.g)) return pr_fail(PR_ESTATE, "not a live graph handle");
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    if (in.g->device != dev)
+        return pr_fail(PR_EINVAL, "the graph lives on device " + std::to_string(in.g->device) + " but device " +
+                                      std::to_string(dev) + " is current");
     if (!(in.alpha >= 0.0 && in.alpha <= 1.0)) return pr_fail(PR_EINVAL, "alpha must be in [0, 1]");
     if (!(in.tol > 0.0) || !std::isfinite(in.tol)) return pr_fail(PR_EINVAL, "tol must be positive and finite");
     if (in.norm < PR_NORM_L1 || in.norm > PR_NORM_LINF) return pr_fail(PR_EINVAL, "norm must be 1 (L1), 2 (L2) or 3 (Linf)");
@@ -134,7 +140,7 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
     std::map<const pr_graph *, const void *> learned_feat;
     auto start_for = [&](const pr_instance &in, const double **out) -> pr_status {
         *out = nullptr;
-        if (opt.init == PR_INIT_UNIFORM) return PR_OK;
+        if (opt.init == PR_INIT_UNIFORM || opt.init == PR_INIT_CHAIN) return PR_OK;   // chain: set per level below
         size_t bytes = (size_t)in.g->n * sizeof(double);
         if (opt.init == PR_INIT_USER) {
             const double *src = in.init_vec ? in.init_vec : opt.init_vec;
@@ -224,40 +230,96 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
         req.cols[0].hist_host = hist_host;
         req.cols[0].hist_cap = hist_cap;
     }
-    // ---- jobs: the grouping plan, one sub-solve per job width
+    // ---- jobs: the grouping plan, one sub-solve per job precision and width
     std::vector<std::vector<Tap>> taps(req.cols.size());
-    {
-        auto fail_all = [&](pr_status fs) {
-            std::string msg = pr_last_error();
-            for (auto &c : req.cols)
-                for (int i : c.inst) inst[i].status = fs;
-            return pr_fail(fs, msg);
-        };
+    auto fail_all = [&](pr_status fs) {
+        std::string msg = pr_last_error();
+        for (auto &c : req.cols)
+            for (int i : c.inst) inst[i].status = fs;
+        return pr_fail(fs, msg);
+    };
+    // solves the columns `cols` of req (the whole request, or one level of an
+    // alpha continuation) and adds the launch accounting to `total`
+    auto run_columns = [&](const std::vector<int> &cols, SolveStats &total) -> pr_status {
+        SolveRequest part;
+        part.precision = req.precision;
+        part.loop = req.loop;
+        part.switch_tol = req.switch_tol;
+        part.stream = req.stream;
+        part.max_passes = req.max_passes;
+        part.kernels = req.kernels;
+        for (int c : cols) part.cols.push_back(req.cols[c]);
         std::vector<SubSolve> plan;
-        if (!req.cols.empty() && (s = pr_plan_request(req, opt.group, plan)) != PR_OK) return fail_all(s);
-        SolveStats total;
+        pr_status ps = pr_plan_request(part, opt.group, plan);
+        if (ps != PR_OK) return ps;
         for (const SubSolve &sp : plan) {
             SolveRequest sub;
-            sub.precision = req.precision;
-            sub.loop = req.loop;
-            sub.switch_tol = req.switch_tol;
-            sub.stream = req.stream;
-            sub.max_passes = req.max_passes;
-            sub.kernels = req.kernels;
+            sub.precision = sp.precision;
+            sub.loop = part.loop;
+            sub.switch_tol = part.switch_tol;
+            sub.stream = part.stream;
+            sub.max_passes = part.max_passes;
+            sub.kernels = part.kernels;
             std::vector<int> cmap;   // sub-request column -> request column
             for (const auto &jc : sp.jobs) {
                 std::vector<int> local;
                 for (int c : jc) {
                     local.push_back((int)sub.cols.size());
-                    cmap.push_back(c);
-                    sub.cols.push_back(req.cols[c]);
+                    cmap.push_back(cols[c]);
+                    sub.cols.push_back(part.cols[c]);
                 }
                 sub.jobs.push_back(local);
             }
             std::vector<std::vector<Tap>> sub_taps;
-            if ((s = pr_run_solve(sub, sub_taps)) != PR_OK) return fail_all(s);
+            if ((ps = pr_run_solve(sub, sub_taps)) != PR_OK) return ps;
             for (size_t k = 0; k < cmap.size(); k++) taps[cmap[k]] = sub_taps[k];
             total.add(sub.stats);
+        }
+        return PR_OK;
+    };
+    if (!req.cols.empty()) {
+        SolveStats total;
+        if (opt.init != PR_INIT_CHAIN) {
+            std::vector<int> all(req.cols.size());
+            for (size_t c = 0; c < all.size(); c++) all[c] = (int)c;
+            if ((s = run_columns(all, total)) != PR_OK) return fail_all(s);
+        } else {
+            // alpha continuation: per graph, columns in increasing alpha; level L
+            // holds every graph's L-th column and starts it from the final
+            // iterate of the graph's column at level L - 1
+            std::vector<const pr_graph *> gorder;
+            std::map<const pr_graph *, std::vector<int>> per_g;
+            for (size_t c = 0; c < req.cols.size(); c++) {
+                if (!per_g.count(req.cols[c].g)) gorder.push_back(req.cols[c].g);
+                per_g[req.cols[c].g].push_back((int)c);
+            }
+            size_t levels = 0;
+            for (auto &kv : per_g) {
+                std::stable_sort(kv.second.begin(), kv.second.end(),
+                                 [&](int a, int b) { return req.cols[a].alpha < req.cols[b].alpha; });
+                levels = std::max(levels, kv.second.size());
+            }
+            std::vector<std::unique_ptr<PoolBuf>> finals(req.cols.size());
+            for (size_t L = 0; L < levels; L++) {
+                std::vector<int> lvl;
+                for (const pr_graph *g : gorder) {
+                    const auto &v = per_g[g];
+                    if (L >= v.size()) continue;
+                    const int c = v[L];
+                    SolveColumn &sc = req.cols[c];
+                    if (L > 0) {
+                        sc.init_dev = static_cast<const double *>(finals[v[L - 1]]->p);
+                        sc.init_relabelled = false;
+                    }
+                    if (L + 1 < v.size()) {
+                        finals[c].reset(new PoolBuf());
+                        if ((s = finals[c]->alloc((size_t)g->n * sizeof(double), st)) != PR_OK) return fail_all(s);
+                        sc.final_dev = static_cast<double *>(finals[c]->p);
+                    }
+                    lvl.push_back(c);
+                }
+                if ((s = run_columns(lvl, total)) != PR_OK) return fail_all(s);
+            }
         }
         pr_record_last_stats(total);
     }

@@ -43,6 +43,9 @@ void free_tables(pr_graph *g) {
         cudaFree(t.d_slot_base);
         t = TileTable();
     }
+    cudaFree(g->hub_table.d_tiles);
+    cudaFree(g->hub_table.d_slot_base);
+    g->hub_table = TileTable();
 }
 
 void free_graph(pr_graph *g) {
@@ -196,15 +199,9 @@ __global__ void tile_segments_kernel(const TileSeg *__restrict__ segs, int32_t n
 // tile_edges(W) in-edges each), lanes per row the smallest power of two
 // (at most 32) with four in-edges per lane for the class's longest row; the
 // other classes get chunks of chunk_edges(W) in-edges per row.
-pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
-    int wi = w_index(W);
-    if (wi < 0) return pr_fail(PR_EINVAL, "unsupported column width");
-    TileTable &t = g->tables[wi];
-    if (t.d_tiles) {
-        *out = &t;
-        return PR_OK;
-    }
-    const int TE = tile_edges(W), TR = tile_rows(W), CH = chunk_edges(W);
+namespace {
+
+pr_status build_tile_table(pr_graph *g, int W, int TE, int TR, int CH, TileTable &t) {
     const int max_es = 32;
     std::vector<TileSeg> segs;
     try {
@@ -271,6 +268,31 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
         return pr_cuda_fail(e, "tile table (write)");
     }
     t = nt;
+    return PR_OK;
+}
+
+}  // namespace
+
+pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
+    int wi = w_index(W);
+    if (wi < 0) return pr_fail(PR_EINVAL, "unsupported column width");
+    TileTable &t = g->tables[wi];
+    if (!t.d_tiles) {
+        pr_status s = build_tile_table(g, W, tile_edges(W), tile_rows(W), chunk_edges(W), t);
+        if (s != PR_OK) return s;
+    }
+    *out = &t;
+    return PR_OK;
+}
+
+// The one-column gather kernel with a shared-memory hub table stages fewer
+// values per warp (kHubTile), so its rows tiles are smaller.
+pr_status pr_graph_hub_tiles(pr_graph *g, const TileTable **out) {
+    TileTable &t = g->hub_table;
+    if (!t.d_tiles) {
+        pr_status s = build_tile_table(g, 1, kHubTile, tile_rows(1), chunk_edges(1), t);
+        if (s != PR_OK) return s;
+    }
     *out = &t;
     return PR_OK;
 }

@@ -25,6 +25,7 @@ struct pr_graph {
     int32_t *d_inv = nullptr;        // caller -> relabelled
     std::vector<ClassRange> classes; // in-degree classes in relabelled order
     TileTable tables[6];             // W = 1, 2, 4, 8, 16, 32
+    TileTable hub_table;             // W = 1, tiles of the hub gather kernel
     uint64_t signature = 0;          // hash of n, nnz and the in-degree class layout
 };
 constexpr uint32_t kGraphMagic = 0x50524731u;   // "PRG1"
@@ -49,6 +50,7 @@ pr_status pr_cuda_fail(cudaError_t e, const char *what);
 // ------------------------------------------------------------------ internals
 int w_index(int W);   // 1,2,4,..,32 -> 0..5
 pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out);
+pr_status pr_graph_hub_tiles(pr_graph *g, const TileTable **out);
 bool pr_graph_valid(const pr_graph *g);
 
 // Solve driver (pr_solve.cu)
@@ -62,6 +64,8 @@ struct SolveColumn {
     bool init_relabelled = false;       // init_dev in relabelled order (else caller order)
     double *hist_host = nullptr;
     int32_t hist_cap = 0;
+    double *final_dev = nullptr;        // optional: device, n doubles (caller order) receiving the
+                                        // column's final iterate (its last stopping rule's answer)
 };
 
 // Launch accounting of one solve (or the sum over a request's sub-solves).
@@ -99,6 +103,7 @@ void pr_record_last_stats(const SolveStats &s);
 // width W, given as lists of request column indices.
 struct SubSolve {
     int W = 1;
+    int precision = PR_PREC_DF64;   // never PR_PREC_AUTO
     std::vector<std::vector<int>> jobs;
 };
 pr_status pr_plan_request(const SolveRequest &req, int group, std::vector<SubSolve> &plan);
@@ -108,6 +113,9 @@ void *pr_iter_kernel_for(int precision, int W);
 void *pr_init_kernel_for(int precision, int W);
 size_t pr_tile_smem_bytes(int precision, int W);
 pr_status pr_kernel_setup(int precision, int W, int *blocks_per_sm);
+// CTAs a job of ntiles warp tiles is given in a fused pass (at most one per
+// kMinTilesPerWarp tiles of each warp).
+int tile_ctas(int32_t ntiles);
 
 // Stream-ordered device buffer from the per-device workspace pool
 // (pr_solve.cu): released with cudaFreeAsync on the stream it was taken on,

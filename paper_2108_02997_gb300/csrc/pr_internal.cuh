@@ -96,6 +96,30 @@ constexpr int kVecGatherBatch = PR_VEC_GATHER_BATCH;  // vector gathers per lane
 #endif
 constexpr int kMinTilesPerWarp = PR_MIN_TILES_PER_WARP;
 constexpr int kChunkValues = PR_CHUNK_VALUES;
+// One column, split passes: the gather kernel runs one CTA of kHubBlock
+// threads per SM and keeps the contributions of the first vertices in the
+// relabelled order (the highest in-/out-degree classes, the most gathered
+// sources) in shared memory, up to kHubBytes; their gathers read shared memory
+// instead of L1/L2. Its warps stage kHubTile gathered values each.
+#ifndef PR_HUB_GATHER
+#define PR_HUB_GATHER 1
+#endif
+#ifndef PR_HUB_TILE_VALUES
+#define PR_HUB_TILE_VALUES 224
+#endif
+#ifndef PR_HUB_BYTES
+#define PR_HUB_BYTES (96 * 1024)
+#endif
+#ifndef PR_HUB_CHUNK_PER
+#define PR_HUB_CHUNK_PER 8
+#endif
+constexpr bool kHubGather = PR_HUB_GATHER != 0;
+constexpr int kHubBlock = 1024;
+constexpr int kHubWarps = kHubBlock / 32;
+constexpr int kHubTile = PR_HUB_TILE_VALUES;
+constexpr int kHubBytes = PR_HUB_BYTES;
+constexpr int kHubChunkPer = PR_HUB_CHUNK_PER;   // chunk tiles: gathers in flight per lane
+static_assert(kHubTile % 32 == 0 && kHubTile <= 256, "hub tiles hold 32..256 values");
 constexpr int kMinBlocks = PR_MIN_BLOCKS;
 constexpr int kVecTileEdges = 256;
 __host__ __device__ constexpr int tile_edges(int W) { return W == 1 ? kTileValues : kVecTileEdges; }
@@ -211,6 +235,8 @@ struct JobDev {
     int32_t cur;              // buffer parity shared by the job's active columns
     void *rowsum;             // one column, split passes: the n row sums of the pass
     int32_t gcta_begin, gcta_count;   // CTAs of the gather pass (split passes)
+    int32_t hub_n;            // hub gather kernel: contributions of ids [0, hub_n) held in shared memory
+    int32_t pad_hub;
 };
 
 struct GlobalDev {

@@ -18,7 +18,9 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
 #include <vector>
 
 #include "pr_internal.cuh"
@@ -718,11 +720,17 @@ int grid_for(long long work, int threads) {
     return (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * 8));
 }
 
+// The training kernel's dynamic shared-memory opt-in, once per device (an
+// attribute of the device context).
 pr_status mlp_setup_smem() {
-    static bool done = false;
-    if (!done) {
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count(dev)) {
         PR_CUDA(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpShared)));
-        done = true;
+        done.insert(dev);
     }
     return PR_OK;
 }

@@ -14,7 +14,9 @@
 // stand-in for the device variable, so its device address is obtained with
 // cudaGetSymbolAddress once per device (with that device current) and passed
 // to the kernels. Every GPU that loads this library holds the array until the
-// process exits.
+// process exits. The address is kept for the life of the process: after a
+// cudaDeviceReset of a device the library has used, it is stale (the kernel
+// setup records of the other entry points have the same limit).
 #include <cstring>
 #include <mutex>
 
@@ -61,18 +63,35 @@ extern "C" pr_status pr_solve_noalloc(const pr_graph *g, double alpha, double to
     if (norm < PR_NORM_L1 || norm > PR_NORM_LINF) return pr_fail(PR_EINVAL, "norm must be 1 (L1), 2 (L2) or 3 (Linf)");
     if (max_iter < 1) return pr_fail(PR_EINVAL, "max_iter must be >= 1");
     if (!d_ranks_out) return pr_fail(PR_EINVAL, "d_ranks_out is NULL");
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    if (dev != g->device)
+        return pr_fail(PR_EINVAL, "the graph lives on device " + std::to_string(g->device) + " but device " +
+                                      std::to_string(dev) + " is current");
+    {
+        // the kernels write d_ranks_out: it must be device memory of this GPU
+        // (cudaPointerGetAttributes allocates nothing)
+        cudaPointerAttributes pa;
+        cudaError_t e = cudaPointerGetAttributes(&pa, d_ranks_out);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return pr_fail(PR_EINVAL, "d_ranks_out is not a device pointer");
+        }
+        if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != dev)
+            return pr_fail(PR_EINVAL, "d_ranks_out must be device memory of the current device");
+    }
     const TileTable &ut = g->tables[0];
     if (!ut.d_tiles) return pr_fail(PR_ESTATE, "graph has no single-column work table");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     void *kiter = pr_iter_kernel_for(PR_PREC_DF64, 1);
     void *kinit = pr_init_kernel_for(PR_PREC_DF64, 1);
     const size_t smem = pr_tile_smem_bytes(PR_PREC_DF64, 1);
-    int dev = 0, sms = 0, occ = 1;
-    PR_CUDA(cudaGetDevice(&dev));
+    int sms = 0, occ = 1;
     PR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     pr_status s = pr_kernel_setup(PR_PREC_DF64, 1, &occ);
     if (s != PR_OK) return s;
-    const int ctas = std::max(1, std::min(sms * occ, std::max(ut.ntiles, 1)));
+    // the grid of pr_solve's one-column fused pass
+    const int ctas = std::max(1, std::min(sms * occ, tile_ctas(ut.ntiles)));
     // ---- layout inside the scratch array
     const size_t n = (size_t)g->n;
     size_t at = 0;

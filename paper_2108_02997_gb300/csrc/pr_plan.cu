@@ -390,6 +390,7 @@ pr_status pr_plan_request(const SolveRequest &req, int group, std::vector<SubSol
     }
     if (group == PR_GROUP_PACK) {
         SubSolve sp;
+        sp.precision = req.precision == PR_PREC_AUTO ? PR_PREC_DF64 : req.precision;
         for (const pr_graph *g : order) {
             const auto &v = by_graph[g];
             for (size_t i = 0; i < v.size(); i += 32) {
@@ -400,58 +401,83 @@ pr_status pr_plan_request(const SolveRequest &req, int group, std::vector<SubSol
         if (!sp.jobs.empty()) plan.push_back(sp);
         return PR_OK;
     }
-    // ---- jobs per graph: (width, request columns)
-    std::vector<std::pair<int, std::vector<int>>> jobs_all;
+    // ---- jobs per graph: (precision, width, request columns). PR_PREC_AUTO
+    // takes, per graph, mixed precision when the cost model (measured launch
+    // times of both value types, estimated iterations of both phases) predicts
+    // it cheaper than DF64 throughout, else DF64; single-column graphs, which
+    // are not tuned, run DF64.
+    struct JobSpec {
+        int precision, W;
+        std::vector<int> cols;
+    };
+    std::vector<JobSpec> jobs_all;
+    const bool auto_prec = req.precision == PR_PREC_AUTO;
     for (const pr_graph *g : order) {
         const auto &v = by_graph[g];
         if (group == PR_GROUP_SINGLE || v.size() == 1) {
-            for (int c : v) jobs_all.push_back({1, {c}});
+            const int pg = auto_prec ? PR_PREC_DF64 : req.precision;
+            for (int c : v) jobs_all.push_back({pg, 1, {c}});
             continue;
         }
         const int maxw = pow2_ceil(std::min<int>((int)v.size(), 32));
-        const bool mixed = req.precision == PR_PREC_MIXED;
-        TuneEntry t0, t1;
-        pr_status s = tune(g, mixed ? PR_PREC_FP32 : req.precision, maxw, req.stream, t0);
-        if (s != PR_OK) return s;
-        if (mixed && (s = tune(g, PR_PREC_DF64, maxw, req.stream, t1)) != PR_OK) return s;
-        std::vector<std::array<double, 2>> it;
-        for (int c : v) it.push_back(column_iterations(req.cols[c], req.precision, req.switch_tol, &t0.decay));
-        const int np = mixed ? 2 : 1;
-        const double *tp[2] = {t0.us.data(), t1.us.data()};
-        std::vector<int> job_of, width_of;
-        if (!plan_partition(it, tp, np, job_of, width_of, nullptr))
-            return pr_fail(PR_ECUDA, "internal: no column plan (width 1 untimed)");
-        const double lat[2] = {std::max(0.0, t0.lat), std::max(0.0, mixed ? t1.lat : 0.0)};
-        choose_shared_plan(it, tp, np, lat, job_of, width_of);
+        // candidate precisions for this graph, each with its plan and cost
+        std::vector<int> cands;
+        if (auto_prec) cands = {PR_PREC_DF64, PR_PREC_MIXED};
+        else cands = {req.precision};
+        double best_cost = std::numeric_limits<double>::infinity();
+        int best_prec = cands[0];
+        std::vector<int> best_job, best_width;
+        for (int prec : cands) {
+            const bool mixed = prec == PR_PREC_MIXED;
+            TuneEntry t0, t1;
+            pr_status s = tune(g, mixed ? PR_PREC_FP32 : prec, maxw, req.stream, t0);
+            if (s != PR_OK) return s;
+            if (mixed && (s = tune(g, PR_PREC_DF64, maxw, req.stream, t1)) != PR_OK) return s;
+            std::vector<std::array<double, 2>> it;
+            for (int c : v) it.push_back(column_iterations(req.cols[c], prec, req.switch_tol, &t0.decay));
+            const int np = mixed ? 2 : 1;
+            const double *tp[2] = {t0.us.data(), t1.us.data()};
+            std::vector<int> job_of, width_of;
+            if (!plan_partition(it, tp, np, job_of, width_of, nullptr))
+                return pr_fail(PR_ECUDA, "internal: no column plan (width 1 untimed)");
+            const double lat[2] = {std::max(0.0, t0.lat), std::max(0.0, mixed ? t1.lat : 0.0)};
+            const double cost = choose_shared_plan(it, tp, np, lat, job_of, width_of);
+            if (cost < best_cost) {
+                best_cost = cost;
+                best_prec = prec;
+                best_job = job_of;
+                best_width = width_of;
+            }
+        }
         std::map<int, std::pair<int, std::vector<int>>> jobs;   // job index -> (width, request columns)
         for (size_t k = 0; k < v.size(); k++) {
-            jobs[job_of[k]].first = width_of[k];
-            jobs[job_of[k]].second.push_back(v[k]);
+            jobs[best_job[k]].first = best_width[k];
+            jobs[best_job[k]].second.push_back(v[k]);
         }
-        for (auto &kv : jobs) jobs_all.push_back(kv.second);
+        for (auto &kv : jobs) jobs_all.push_back({best_prec, kv.second.first, kv.second.second});
     }
-    // ---- sub-solves: jobs of one width together while their gathered
-    // vectors fit in half of L2; a job larger than that alone
+    // ---- sub-solves: jobs of one precision and width together while their
+    // gathered vectors fit in half of L2; a job larger than that alone
     int dev = 0, l2 = 0;
     PR_CUDA(cudaGetDevice(&dev));
     PR_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
     const double budget = 0.5 * (double)std::max(l2, 1 << 20);
-    const int vprec = req.precision == PR_PREC_MIXED ? PR_PREC_DF64 : req.precision;
-    std::stable_sort(jobs_all.begin(), jobs_all.end(),
-                     [](const std::pair<int, std::vector<int>> &a, const std::pair<int, std::vector<int>> &b) {
-                         return a.first < b.first;
-                     });
+    std::stable_sort(jobs_all.begin(), jobs_all.end(), [](const JobSpec &a, const JobSpec &b) {
+        return a.precision != b.precision ? a.precision < b.precision : a.W < b.W;
+    });
     SubSolve cur;
     double cur_bytes = 0.0;
     for (auto &jb : jobs_all) {
-        const double b = gather_bytes(req.cols[jb.second[0]].g, jb.first, vprec);
-        if (!cur.jobs.empty() && (cur.W != jb.first || cur_bytes + b > budget)) {
+        const int vprec = jb.precision == PR_PREC_MIXED ? PR_PREC_DF64 : jb.precision;
+        const double b = gather_bytes(req.cols[jb.cols[0]].g, jb.W, vprec);
+        if (!cur.jobs.empty() && (cur.W != jb.W || cur.precision != jb.precision || cur_bytes + b > budget)) {
             plan.push_back(cur);
             cur = SubSolve();
             cur_bytes = 0.0;
         }
-        cur.W = jb.first;
-        cur.jobs.push_back(jb.second);
+        cur.W = jb.W;
+        cur.precision = jb.precision;
+        cur.jobs.push_back(jb.cols);
         cur_bytes += b;
     }
     if (!cur.jobs.empty()) plan.push_back(cur);

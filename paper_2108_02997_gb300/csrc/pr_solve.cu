@@ -27,10 +27,19 @@ namespace {
 // kPoolKeepBytes stay reserved between solves; the rest goes back to the device.
 constexpr unsigned long long kPoolKeepBytes = 4ull << 30;
 
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+// The device's pool if one has been created (no creation).
+cudaMemPool_t existing_pool(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    return it == g_pools.end() ? nullptr : it->second;
+}
+
 cudaMemPool_t workspace_pool(int dev) {
-    static std::mutex mu;
-    static std::map<int, cudaMemPool_t> pools;
-    std::lock_guard<std::mutex> lk(mu);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto &pools = g_pools;
     auto it = pools.find(dev);
     if (it != pools.end()) return it->second;
     cudaMemPoolProps props{};
@@ -94,6 +103,33 @@ pr_status PoolBuf::alloc(size_t bytes, cudaStream_t st) {
     return PR_OK;
 }
 
+extern "C" pr_status pr_workspace_info(int64_t *reserved_bytes, int64_t *used_bytes, int64_t *used_high_bytes) {
+    pr_clear_error();
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    unsigned long long res = 0, used = 0, high = 0;   // the attributes are 64-bit counts
+    if (cudaMemPool_t pool = existing_pool(dev)) {
+        PR_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &res));
+        PR_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+        PR_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
+    }
+    if (reserved_bytes) *reserved_bytes = (int64_t)res;
+    if (used_bytes) *used_bytes = (int64_t)used;
+    if (used_high_bytes) *used_high_bytes = (int64_t)high;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_workspace_release(void) {
+    pr_clear_error();
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    if (cudaMemPool_t pool = existing_pool(dev)) {
+        PR_CUDA(cudaDeviceSynchronize());   // frees issued on any stream have completed
+        PR_CUDA(cudaMemPoolTrimTo(pool, 0));
+    }
+    return PR_OK;
+}
+
 void PoolBuf::release() {
     if (!p) return;
     if (pooled) cudaFreeAsync(p, stream);
@@ -138,7 +174,18 @@ void *update_ptr(int W) {
         default: return (void *)pr_update_kernel<V, 32>;
     }
 }
+// The one-column gather kernel with the shared-memory hub table (split passes).
+bool hub_gather(int W) { return kHubGather && W == 1; }
+void *hub_gather_kernel_for(int prec) {
+    switch (prec) {
+        case PR_PREC_FP64: return (void *)pr_gather_hub_kernel<double>;
+        case PR_PREC_FP32: return (void *)pr_gather_hub_kernel<float>;
+        default: return (void *)pr_gather_hub_kernel<df64>;
+    }
+}
+int gather_block(int W) { return hub_gather(W) ? kHubBlock : kBlock; }
 void *gather_kernel_for(int prec, int W) {
+    if (hub_gather(W)) return hub_gather_kernel_for(prec);
     switch (prec) {
         case PR_PREC_FP64: return gather_ptr<double>(W);
         case PR_PREC_FP32: return gather_ptr<float>(W);
@@ -152,9 +199,9 @@ void *update_kernel_for(int prec, int W) {
         default: return update_ptr<df64>(W);
     }
 }
-int resident_ctas(void *k, size_t smem) {
+int resident_ctas(void *k, size_t smem, int block = kBlock) {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBlock, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -169,7 +216,7 @@ int resident_ctas(void *k, size_t smem) {
 // launch at scale 22, 981 -> 949 us at scale 24, 361 -> 339 us on the 8M-vertex
 // configuration-model graph (FP32: 6-8 % faster). The fused and multi-column
 // kernels keep the driver's choice (no gain measured; W = 4 df64 lost 15 %).
-pr_status set_carveout(void *k, size_t smem, bool minimal) {
+pr_status set_carveout(void *k, size_t smem, bool minimal, int block = kBlock) {
     if (kSmemCarveout == -2) return PR_OK;
     if (kSmemCarveout >= 0) {
         PR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, kSmemCarveout));
@@ -182,47 +229,52 @@ pr_status set_carveout(void *k, size_t smem, bool minimal) {
     PR_CUDA(cudaGetDevice(&dev));
     PR_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     PR_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBlock, smem));   // largest carveout
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, smem));   // largest carveout
     if (occ < 1 || per_sm <= 0) return PR_OK;
     const double need = (double)occ * ((double)fa.sharedSizeBytes + (double)smem + (double)reserved);
     for (int pct = std::max(1, (int)std::ceil(100.0 * need / per_sm)); pct <= 100; pct++) {
         PR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
         int got = 0;
-        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, k, kBlock, smem));
+        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, k, block, smem));
         if (got >= occ) return PR_OK;
     }
     PR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, -1));
     return PR_OK;
 }
 
-// CTAs worth giving a job of ntiles warp tiles: at least kMinTilesPerWarp
-// tiles per warp, so that small graphs do not spread over idle CTAs whose
-// partials the job's finalizer must then reduce.
-int tile_ctas(int32_t ntiles) {
-    const int64_t per_cta = kMinTilesPerWarp > 0 ? (int64_t)kWarps * kMinTilesPerWarp : 1;
-    return (int)std::max<int64_t>(1, ((int64_t)std::max(ntiles, 1) + per_cta - 1) / per_cta);
-}
+// Kernel attributes (dynamic shared memory, carveout) are set per device
+// context, so the setup and the residencies it measures are kept per device
+// ordinal, precision and width. A cudaDeviceReset discards the attributes but
+// not this record: the library does not survive a reset of a device it used.
+struct SetupKey {
+    int dev, prec, wi;
+    bool operator<(const SetupKey &o) const {
+        return dev != o.dev ? dev < o.dev : (prec != o.prec ? prec < o.prec : wi < o.wi);
+    }
+};
 
 // Split passes: opt the gather kernel into its dynamic shared memory (once per
-// process, precision and width) and report both kernels' residency.
+// device, precision and width) and report both kernels' residency.
 pr_status setup_split(int prec, int W, int *occ_gather, int *occ_update) {
     static std::mutex mu;
-    static bool done[4][6] = {};
-    static int occ_g[4][6] = {}, occ_u[4][6] = {};   // residencies, queried once
+    static std::map<SetupKey, std::pair<int, int>> done;   // residencies (gather, update), queried once
     void *kg = gather_kernel_for(prec, W);
     const size_t smem = gather_smem_bytes(prec, W);
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    const SetupKey key{dev, prec & 3, w_index(W)};
     std::lock_guard<std::mutex> lk(mu);
-    const int pi = prec & 3, wi = w_index(W);
-    if (!done[pi][wi]) {
+    auto it = done.find(key);
+    if (it == done.end()) {
         PR_CUDA(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        pr_status s = set_carveout(kg, smem, W == 1);
+        pr_status s = set_carveout(kg, smem, W == 1, gather_block(W));
         if (s != PR_OK) return s;
-        occ_g[pi][wi] = resident_ctas(kg, smem);
-        occ_u[pi][wi] = resident_ctas(update_kernel_for(prec, W), 0);
-        done[pi][wi] = true;
+        const std::pair<int, int> occ{resident_ctas(kg, smem, gather_block(W)),
+                                      resident_ctas(update_kernel_for(prec, W), 0)};
+        it = done.emplace(key, occ).first;
     }
-    *occ_gather = occ_g[pi][wi];
-    *occ_update = occ_u[pi][wi];
+    *occ_gather = it->second.first;
+    *occ_update = it->second.second;
     return PR_OK;
 }
 
@@ -275,6 +327,14 @@ SolveStats g_last_stats;
 
 }  // namespace
 
+// CTAs worth giving a job of ntiles warp tiles: at least kMinTilesPerWarp
+// tiles per warp, so that small graphs do not spread over idle CTAs whose
+// partials the job's finalizer must then reduce.
+int tile_ctas(int32_t ntiles) {
+    const int64_t per_cta = kMinTilesPerWarp > 0 ? (int64_t)kWarps * kMinTilesPerWarp : 1;
+    return (int)std::max<int64_t>(1, ((int64_t)std::max(ntiles, 1) + per_cta - 1) / per_cta);
+}
+
 void *pr_iter_kernel_for(int prec, int W) {
     switch (prec) {
         case PR_PREC_FP64: return iter_ptr<double>(W);
@@ -296,33 +356,38 @@ size_t pr_tile_smem_bytes(int prec, int W) {
     if (W == 1) return 0;
     return (size_t)kWarps * vec_warp_bytes(vbytes, W, false);
 }
-// The gather-only kernel's: no previous ranks or out-degrees staged.
+// The hub gather kernel's contributions held in shared memory (values), at most.
+int hub_capacity(int prec) { return kHubBytes / (prec == PR_PREC_FP32 ? 4 : 8); }
+// The gather-only kernel's: no previous ranks or out-degrees staged; the hub
+// gather kernel's: every warp's staged values, then the hub table.
 size_t gather_smem_bytes(int prec, int W) {
     const int vbytes = prec == PR_PREC_FP32 ? 4 : 8;
+    if (hub_gather(W)) return (size_t)kHubWarps * kHubTile * vbytes + (size_t)hub_capacity(prec) * vbytes;
     if (W == 1) return 0;
     return (size_t)kWarps * vec_warp_bytes(vbytes, W, true);
 }
 
-// Opt the iteration kernel into its dynamic shared memory (once per process
-// and instantiation) and report its resident CTAs per SM.
+// Opt the iteration kernel into its dynamic shared memory (once per device,
+// precision and width) and report its resident CTAs per SM.
 pr_status pr_kernel_setup(int prec, int W, int *blocks_per_sm) {
     static std::mutex mu;
-    static bool done[4][6] = {};
-    static int occ_k[4][6] = {};   // residency, queried once
+    static std::map<SetupKey, int> done;   // residency, queried once
     void *k = pr_iter_kernel_for(prec, W);
     const size_t smem = pr_tile_smem_bytes(prec, W);
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    const SetupKey key{dev, prec & 3, w_index(W)};
     std::lock_guard<std::mutex> lk(mu);
-    const int pi = prec & 3, wi = w_index(W);
-    if (!done[pi][wi]) {
+    auto it = done.find(key);
+    if (it == done.end()) {
         PR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         pr_status s = set_carveout(k, smem, false);
         if (s != PR_OK) return s;
         int occ = 0;
         PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBlock, smem));
-        occ_k[pi][wi] = std::max(occ, 1);
-        done[pi][wi] = true;
+        it = done.emplace(key, std::max(occ, 1)).first;
     }
-    *blocks_per_sm = occ_k[pi][wi];
+    *blocks_per_sm = it->second;
     return PR_OK;
 }
 
@@ -391,7 +456,7 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
     struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{ev0, ev1};
     void *args[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_ctajob};
     void *gargs[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_gctajob};
-    dim3 grid(total_ctas), ggrid(split ? total_gctas : 1), block(kBlock);
+    dim3 grid(total_ctas), ggrid(split ? total_gctas : 1), block(kBlock), gblock(gather_block(W));
     const size_t iter_smem = split ? 0 : smem, gather_smem = split ? gather_smem_bytes(prec, W) : 0;
     PR_CUDA(cudaEventRecord(ev0, st));
     if (loop == PR_LOOP_HOST) {
@@ -412,7 +477,7 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
         for (int p = 0; p < pass_cap + 1; p++) {
             PR_CUDA(cudaEventRecord(k0, st));
             if (split) {
-                PR_CUDA(cudaLaunchKernel(kgather, ggrid, block, gargs, gather_smem, st));
+                PR_CUDA(cudaLaunchKernel(kgather, ggrid, gblock, gargs, gather_smem, st));
                 PR_CUDA(cudaEventRecord(km, st));
                 stats.launches++;
             }
@@ -466,6 +531,7 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
             cudaKernelNodeParams gp = kp;
             gp.func = kgather;
             gp.gridDim = ggrid;
+            gp.blockDim = gblock;
             gp.sharedMemBytes = (unsigned int)gather_smem;
             gp.kernelParams = gargs;
             PR_CUDA(cudaGraphAddKernelNode(&n_gather, body, nullptr, 0, &gp));
@@ -582,9 +648,12 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         }
     }
     const int budget = sms * occ, gbudget = sms * occ_gather;
+    // split one-column passes gather with the hub kernel, which has tiles of its own
+    const bool hub = split && hub_gather(W);
     double total_work = 0.0;
     for (auto &j : jobs) {
-        s = pr_graph_tiles(const_cast<pr_graph *>(j.g), W, &j.tt);
+        s = hub ? pr_graph_hub_tiles(const_cast<pr_graph *>(j.g), &j.tt)
+                : pr_graph_tiles(const_cast<pr_graph *>(j.g), W, &j.tt);
         if (s != PR_OK) return s;
         total_work += std::max(j.tt->work, 1.0);
     }
@@ -596,7 +665,9 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             // update kernel: rows grid-stride
             j.cta_count = std::max(1, std::min<int>(want, (int)(((int64_t)j.g->n * W + kBlock - 1) / kBlock)));
             int gwant = (int)std::lround(gbudget * share);
-            j.gcta_count = std::max(1, std::min(gwant, tile_ctas(j.tt->ntiles)));
+            const int gcap = hub ? (int)std::max<int64_t>(1, ((int64_t)j.tt->ntiles + kHubWarps - 1) / kHubWarps)
+                                 : tile_ctas(j.tt->ntiles);
+            j.gcta_count = std::max(1, std::min(gwant, gcap));
             total_gctas += j.gcta_count;
         } else {
             j.cta_count = std::max(1, std::min(want, tile_ctas(j.tt->ntiles)));
@@ -690,6 +761,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             for (int q = 0; q < j.gcta_count; q++) gctajob[gcta_at + q] = (int32_t)ji;
             gcta_at += j.gcta_count;
             d.rowsum = ar.at<void>(j.off_rowsum);
+            d.hub_n = hub ? j.g->n : 0;   // the kernel clamps to its value type's capacity
         }
         d.ncols = (int32_t)j.cols.size();
         d.alive = 1;
@@ -838,6 +910,14 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
                     PR_CUDA(cudaMemcpyAsync(sc.host_dst[q], mine[q].out, (size_t)j.g->n * sizeof(double),
                                             cudaMemcpyDeviceToHost, st));
             tap_out[j.cols[k]] = mine;
+            if (sc.final_dev && !mine.empty()) {
+                // the tap that fired last holds the column's final iterate (after the alias copies above)
+                size_t last = 0;
+                for (size_t q = 1; q < mine.size(); q++)
+                    if (mine[q].iters > mine[last].iters) last = q;
+                PR_CUDA(cudaMemcpyAsync(sc.final_dev, mine[last].out, (size_t)j.g->n * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
+            }
             if (sc.hist_host && cs.hist) {
                 int nh = std::min(cs.iters, sc.hist_cap);
                 if (nh > 0)

@@ -4,7 +4,7 @@ mixed precision and FP32 against the error bound of the L1 contraction."""
 import numpy as np
 import pytest
 
-from tests.parity import assert_fp64_parity, bound_l1, rel_l1
+from tests.parity import assert_bound_parity, assert_fp64_parity, previous_iterates, rel_l1
 
 pytestmark = pytest.mark.gpu
 
@@ -112,24 +112,41 @@ def test_mixed_precision_error_bound(B, orc, gg, alpha):
     g = gg.rmat(16, 16, seed=24)
     ref = orc.pagerank(g, alpha, 1e-13, 1, 10000, threads=orc.default_threads())
     with B.Graph.from_csr(g) as dg:
-        insts = [B.Instance(dg, alpha, t, nm, 500) for t in (1e-4, 1e-8, 1e-10) for nm in (1, 2, 3)]
-        B.pr_solve_batch(insts, precision="mixed")
-        for x in insts:
+        specs = [(t, nm) for t in (1e-4, 1e-8, 1e-10) for nm in (1, 2, 3)]
+
+        def solve(caps):
+            xs = [B.Instance(dg, alpha, t, nm, c) for (t, nm), c in zip(specs, caps)]
+            B.pr_solve_batch(xs, precision="mixed")
+            return xs
+        insts = solve([500] * len(specs))
+        prev = previous_iterates(solve, insts)
+        for x, rp in zip(insts, prev):
             assert x.converged
-            err = np.abs(x.out - ref.ranks).sum()
-            assert err <= bound_l1(alpha, x.tol, x.norm, x.err_l1), (x.tol, x.norm, err)
+            assert_bound_parity(orc, g, alpha, x.tol, x.norm, 500, x.out, x.iters, x.converged, ref.ranks,
+                                r_prev=rp, err=x.err, err_l1=x.err_l1, what=f"tau {x.tol} norm {x.norm}")
         # a tight tau is reached by the refinement phase: close to the FP64 answer
         tight = [x for x in insts if x.tol == 1e-10 and x.norm == 1][0]
         assert rel_l1(tight.out, ref.ranks) < 1e-8
 
 
 def test_fp32_error_bound(B, orc, er):
+    """FP32 throughout: an L1 stop (bound from tau alone) and an Linf stop
+    (bound from the host-recomputed last step)."""
     ref = orc.pagerank(er, 0.85, 1e-13, 1, 10000)
     with B.Graph.from_csr(er) as dg:
         x = B.Instance(dg, 0.85, 1e-5, 1, 500)
         B.pr_solve_batch([x], precision="fp32")
         assert x.converged
-        assert np.abs(x.out - ref.ranks).sum() <= bound_l1(0.85, 1e-5, 1, x.err_l1)
+        assert_bound_parity(orc, er, 0.85, 1e-5, 1, 500, x.out, x.iters, x.converged, ref.ranks, what="fp32 L1")
+
+        def solve(caps):
+            xs = [B.Instance(dg, 0.85, 1e-8, 3, caps[0])]
+            B.pr_solve_batch(xs, precision="fp32")
+            return xs
+        y = solve([500])
+        rp = previous_iterates(solve, y)
+        assert_bound_parity(orc, er, 0.85, 1e-8, 3, 500, y[0].out, y[0].iters, y[0].converged, ref.ranks,
+                            r_prev=rp[0], err=y[0].err, err_l1=y[0].err_l1, what="fp32 Linf")
 
 
 def test_invalid_instance_reports_its_status(B, er):
@@ -170,7 +187,8 @@ def test_grouping_modes_mixed_precision(B, orc, gg, group):
         B.pr_solve_batch(insts, precision="mixed", group=group)
         for a, x in zip(alphas, insts):
             assert x.converged
-            assert np.abs(x.out - refs[a].ranks).sum() <= bound_l1(a, 1e-10, 1, x.err_l1)
+            assert_bound_parity(orc, g, a, 1e-10, 1, 500, x.out, x.iters, x.converged, refs[a].ranks,
+                                what=f"{group} alpha {a}")
 
 
 def test_graph_tune_measures_and_caches(B, gg):
@@ -200,3 +218,53 @@ def test_multi_column_kernels_match_oracle(B, orc, gg, kernels, width):
             B.pr_solve_batch(insts, group="pack", kernels=kernels, precision=prec)
             for a, x in zip(alphas, insts):
                 assert_fp64_parity(x.out, x.iters, x.err, refs[a], 1e-10, 1, f"W {width} {kernels} {prec} alpha {a}")
+
+
+def test_alpha_continuation_matches_oracle_from_the_same_starts(B, orc, gg):
+    """PR_INIT_CHAIN (the alpha sweep of Section 2 in its order): on each
+    graph the first alpha starts from 1/N and every later one from the
+    previous alpha's final answer. Each column is compared with the oracle run
+    from the start the chain gave it (the previous column's answer as returned),
+    and two graphs run their chains side by side."""
+    g1 = gg.rmat(14, 16, seed=61)
+    g2 = gg.erdos_renyi(5000, 40000, 200, 62)
+    alphas = [0.95, 0.5, 0.7, 0.85, 0.6]          # given out of order: the chain sorts them
+    graphs = [g1, g2]
+    dgs = [B.Graph.from_csr(g) for g in graphs]
+    # two taps on every (graph, alpha): the chain continues from the later one
+    specs = [(gi, a, t, 1) for gi in (0, 1) for a in alphas for t in (1e-6, 1e-10)]
+    insts = [B.Instance(dgs[gi], a, t, nm, 500) for gi, a, t, nm in specs]
+    B.pr_solve_batch(insts, init="chain")
+    for gi, g in enumerate(graphs):
+        prev = None
+        for a in sorted(alphas):
+            xs = [(t, x) for (gj, a2, t, nm), x in zip(specs, insts) if gj == gi and a2 == a]
+            taps = [(t, 1, 500) for t, _ in xs]
+            refs = orc.pagerank_taps(g, a, taps, init=prev, threads=orc.default_threads())
+            for (t, x), r in zip(xs, refs):
+                assert_fp64_parity(x.out, x.iters, x.err, r, t, 1, f"graph {gi} alpha {a} tau {t}")
+            prev = [x for t, x in xs if t == 1e-10][0].out
+    # the chain saves updates over the uniform start on the later alphas
+    uni = [B.Instance(dgs[gi], a, t, nm, 500) for gi, a, t, nm in specs]
+    B.pr_solve_batch(uni)
+    assert sum(x.iters for x in insts) < sum(x.iters for x in uni)
+    for d in dgs:
+        d.close()
+
+
+def test_sweep_outputs_match_oracle(B, orc, er):
+    """The alpha sweep's outputs (Section 2): per alpha, the L1 distance of its
+    ranks to the alpha = 0.85 ranks and its iterations relative to alpha = 0.85,
+    from the batched sweep and from the oracle."""
+    alphas = [0.5, 0.6, 0.7, 0.8, 0.85, 0.9, 0.95]
+    with B.Graph.from_csr(er) as dg:
+        xs = [B.Instance(dg, a, 1e-10, 1, 500) for a in alphas]
+        B.pr_solve_batch(xs)
+    refs = [orc.pagerank(er, a, 1e-10, 1, 500, history=True) for a in alphas]
+    k85 = alphas.index(0.85)
+    for a, x, r in zip(alphas, xs, refs):
+        d_gpu = float(np.abs(x.out - xs[k85].out).sum())
+        d_orc = float(np.abs(r.ranks - refs[k85].ranks).sum())
+        # each answer is within 1e-12 (relative L1) of the oracle's
+        assert abs(d_gpu - d_orc) <= 4e-12, (a, d_gpu, d_orc)
+        assert x.iters * refs[k85].iters == r.iters * xs[k85].iters, (a, x.iters, r.iters)

@@ -5,7 +5,7 @@ saves over the uniform start while converging to the same fixed point."""
 import numpy as np
 import pytest
 
-from tests.parity import bound_l1
+from tests.parity import assert_bound_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -169,6 +169,7 @@ def test_training_lowers_loss_and_warm_start_saves_iterations(B, orc, gg):
         uni = B.pr_solve(dgt, a, 1e-10, 1, 500)
         lrn = B.pr_solve(dgt, a, 1e-10, 1, 500, init="learned", mlp=m)
         assert lrn.converged
-        assert np.abs(lrn.ranks - ref.ranks).sum() <= bound_l1(a, 1e-10, 1, lrn.err)
+        assert_bound_parity(orc, test_g, a, 1e-10, 1, 500, lrn.ranks, lrn.iters, lrn.converged, ref.ranks,
+                            what=f"learned alpha {a}")
         assert lrn.iters < uni.iters, (a, lrn.iters, uni.iters)
     m.close()

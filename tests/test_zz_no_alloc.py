@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 
 def _noalloc(B, dg, alpha, tau, norm, max_iter, out, stream):
     it, err, conv = C.c_int32(), C.c_double(), C.c_int32()
-    st = B.lib().pr_solve_noalloc(dg.handle, alpha, tau, norm, max_iter, out.data_ptr(), stream,
+    addr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    st = B.lib().pr_solve_noalloc(dg.handle, alpha, tau, norm, max_iter, addr, stream,
                                   C.byref(it), C.byref(err), C.byref(conv))
     return st, it.value, err.value, bool(conv.value)
 
@@ -61,3 +62,42 @@ def test_noalloc_rejects_graphs_beyond_its_scratch(gg):
         st, *_ = _noalloc(B, dg, 0.85, 1e-6, 1, 10, out, int(torch.cuda.current_stream().cuda_stream))
         assert st == B.PR_EINVAL
         assert b"no-alloc scratch" in B.lib().pr_last_error()
+
+
+def test_noalloc_rejects_a_host_output_buffer(gg):
+    """The kernels write the output: a host buffer is refused before any work."""
+    import torch
+
+    from paper_2108_02997_gb300 import binding as B
+    g = gg.rmat(10, 8, seed=3)
+    with B.Graph.from_csr(g) as dg:
+        host = np.full(g.n, -1.0)
+        st, *_ = _noalloc(B, dg, 0.85, 1e-8, 1, 100, host, int(torch.cuda.current_stream().cuda_stream))
+        assert st == B.PR_EINVAL
+        assert b"device memory" in B.lib().pr_last_error()
+        assert (host == -1.0).all()
+
+
+def test_noalloc_allocates_no_device_memory(gg):
+    """After a first call (which looks up the array's address), further calls
+    leave the device's free memory and the library's workspace pool as they
+    were."""
+    import torch
+
+    from paper_2108_02997_gb300 import binding as B
+    g = gg.rmat(15, 16, seed=15)
+    sptr = int(torch.cuda.current_stream().cuda_stream)
+    with B.Graph.from_csr(g) as dg:
+        outs = [torch.empty(g.n, dtype=torch.float64, device="cuda") for _ in range(3)]
+        st, *_ = _noalloc(B, dg, 0.85, 1e-9, 1, 500, outs[0], sptr)
+        assert st == 0, B.lib().pr_last_error()
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        pool0 = B.workspace_info()
+        for o in outs[1:]:
+            st, *_ = _noalloc(B, dg, 0.85, 1e-9, 1, 500, o, sptr)
+            assert st == 0, B.lib().pr_last_error()
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert B.workspace_info() == pool0
+        assert torch.equal(outs[1], outs[2]) and torch.equal(outs[0], outs[1])
