@@ -300,8 +300,27 @@ def sweep_report(B, torch, w, last, mlp, sptr):
     return {"alpha": ALPHAS_SWEEP, "l1_vs_alpha_085": l1, "iterations_vs_alpha_085": ratio,
             "tau_sweep_iteration_gm_ratio_alpha_085": norm_gm,
             "fp32_largest_tau_hitting_cap": stall,
+            "fp32_stalls_road_lattice": fp32_stalls(B, sptr),
             "start_iterations_tau_1e-10_L1": starts,
             "start_iterations_total": {k: sum(v) for k, v in starts.items()}}
+
+
+def fp32_stalls(B, sptr):
+    """The sensitivity stalls of Section 4 on a slow-mixing input: a road-like
+    lattice of 300 x 400 vertices (seed 7), alpha 0.85, tau 1e-4 .. 1e-12 x
+    {L1, L2, Linf}, in FP32 and in DF64; per norm the largest tau at which the
+    solve ran into the 500 cap (None: none did)."""
+    from paper_2108_02997_gb300 import graphgen as gg
+    g = gg.road_grid(300, 400, seed=7)
+    taus = [10.0 ** -k for k in range(4, 13)]
+    out = {"graph": "road-like lattice 300 x 400 (seed 7), alpha .85"}
+    with B.Graph.from_csr(g) as dg:
+        for prec in ("fp32", "df64"):
+            xs = [B.Instance(dg, 0.85, t, nm, 500) for t in taus for nm in (1, 2, 3)]
+            B.pr_solve_batch(xs, precision=prec, stream=sptr)
+            out[prec] = {name: max([x.tol for x in xs if x.norm == nm and x.iters >= 500], default=None)
+                         for nm, name in ((1, "L1"), (2, "L2"), (3, "Linf"))}
+    return out
 
 
 def cuda_ms(torch, stream, fn):

@@ -448,6 +448,13 @@ pr_status pr_workspace_info(int64_t *reserved_bytes, int64_t *used_bytes, int64_
  */
 pr_status pr_workspace_release(void);
 
+/*
+ * Columns (iterate sequences) of the last pr_solve / pr_solve_batch and, of
+ * those, the ones solved in mixed precision (FP32 then DF64): with
+ * PR_PREC_AUTO, what the planner chose. Host pointers, each may be NULL.
+ */
+pr_status pr_last_solve_columns(int32_t *columns, int32_t *mixed_columns);
+
 /* Message for the last error on this thread ("" if none). */
 const char *pr_last_error(void);
 

@@ -79,6 +79,7 @@ SIGNATURES = {
     "pr_mlp_loss_grad": ([_vp, _vp, _d, _vp, _vp, _vp, _vp], _i32),
     "pr_last_solve_stats": ([_vp, _vp, _vp, _vp], _i32),
     "pr_last_solve_kernel_ms": ([_vp, _vp], _i32),
+    "pr_last_solve_columns": ([_vp, _vp], _i32),
     "pr_graph_tune": ([_vp, _i32, _i32, _vp, _vp], _i32),
     "pr_kernel_occupancy": ([_i32, _i32, _vp], _i32),
     "pr_plan_columns": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
@@ -373,8 +374,10 @@ def pr_last_solve_stats():
     lib().pr_last_solve_stats(C.byref(la), C.byref(pa), C.byref(km), C.byref(tm))
     gm, um = C.c_double(), C.c_double()
     lib().pr_last_solve_kernel_ms(C.byref(gm), C.byref(um))
+    co, mc = C.c_int32(), C.c_int32()
+    lib().pr_last_solve_columns(C.byref(co), C.byref(mc))
     return {"launches": la.value, "passes": pa.value, "kernel_ms": km.value, "total_ms": tm.value,
-            "gather_ms": gm.value, "update_ms": um.value}
+            "gather_ms": gm.value, "update_ms": um.value, "columns": co.value, "mixed_columns": mc.value}
 
 
 class MLP:

@@ -76,9 +76,12 @@ struct SolveStats {
     double total_ms = 0.0;  // device time of the whole solve
     double gather_ms = 0.0; // PR_LOOP_HOST, split passes: the gather kernels' share of kernel_ms
     double update_ms = 0.0; //   and the update kernels' share
+    int columns = 0;        // columns (iterate sequences) solved
+    int mixed_columns = 0;  //   of which in mixed precision
     void add(const SolveStats &o) {
         launches += o.launches; passes += o.passes; kernel_ms += o.kernel_ms; total_ms += o.total_ms;
-        gather_ms += o.gather_ms; update_ms += o.update_ms;
+        gather_ms += o.gather_ms; update_ms += o.update_ms; columns += o.columns;
+        mixed_columns += o.mixed_columns;
     }
 };
 

@@ -38,6 +38,10 @@ constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, 
 #ifndef PR_UPDATE_MIN_BLOCKS
 #define PR_UPDATE_MIN_BLOCKS 3
 #endif
+// One-column update kernel: pairs of rows (vector loads) in flight per thread.
+#ifndef PR_UPDATE_PAIRS
+#define PR_UPDATE_PAIRS 2
+#endif
 #ifndef PR_TILE_UPDATE
 #define PR_TILE_UPDATE 1
 #endif

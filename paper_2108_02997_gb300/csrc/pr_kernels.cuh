@@ -844,6 +844,46 @@ __global__ void __launch_bounds__(kBlock, kUpdateMinBlocks) pr_update_kernel(Job
         const long long total = (long long)job.n * W;
         const long long stride = (long long)job.cta_count * kBlock;
         long long i = (long long)local * kBlock + tid;
+        if constexpr (W == 1) {
+            // one column: pairs of consecutive rows, their row sums and previous
+            // ranks read with one vector load each and their out-degrees with one
+            // 8-byte load; kPairs pairs per step, all loads issued before any update
+            using V2 = VecV<V, 2>;
+            const long long npairs = total >> 1;
+            const V2 *__restrict__ rs2 = reinterpret_cast<const V2 *>(rowsum);
+            const V2 *__restrict__ rp2 = reinterpret_cast<const V2 *>(r_prev);
+            const int2 *__restrict__ od2 = reinterpret_cast<const int2 *>(outdeg);
+            constexpr int kPairs = PR_UPDATE_PAIRS;
+            long long q = i;
+            for (; q + (kPairs - 1) * stride < npairs; q += kPairs * stride) {
+                V2 sv[kPairs], pv[kPairs];
+                int2 dv[kPairs];
+#pragma unroll
+                for (int k = 0; k < kPairs; k++) {
+                    const long long j = q + k * stride;
+                    if (cv.active) sv[k] = load_vec<V, 2>(reinterpret_cast<const V *>(rs2 + j));
+                    else sv[k].v[0] = sv[k].v[1] = N::zero();
+                    pv[k] = load_vec<V, 2>(reinterpret_cast<const V *>(rp2 + j));
+                    dv[k] = od2[j];
+                }
+#pragma unroll
+                for (int k = 0; k < kPairs; k++) {
+                    const int32_t v = (int32_t)(2 * (q + k * stride));
+                    row_update_pd<V, 1>(perm, cv, acc, v, 0, sv[k].v[0], pv[k].v[0], dv[k].x);
+                    row_update_pd<V, 1>(perm, cv, acc, v + 1, 0, sv[k].v[1], pv[k].v[1], dv[k].y);
+                }
+            }
+            for (; q < npairs; q += stride) {
+                row_update<V, 1>(outdeg, perm, cv, acc, (int32_t)(2 * q), 0, cv.active ? rowsum[2 * q] : N::zero());
+                row_update<V, 1>(outdeg, perm, cv, acc, (int32_t)(2 * q + 1), 0,
+                                 cv.active ? rowsum[2 * q + 1] : N::zero());
+            }
+            // an odd last row
+            if ((total & 1) && local == 0 && tid == 0)
+                row_update<V, 1>(outdeg, perm, cv, acc, (int32_t)(total - 1), 0,
+                                 cv.active ? rowsum[total - 1] : N::zero());
+            i = total;   // nothing left for the general loops below
+        }
         // four rows per step, their loads issued before any update
         for (; i + 3 * stride < total; i += 4 * stride) {
             V sv[4], pv[4];

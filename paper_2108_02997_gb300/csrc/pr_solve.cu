@@ -419,6 +419,13 @@ extern "C" pr_status pr_last_solve_kernel_ms(double *gather_ms, double *update_m
     return PR_OK;
 }
 
+extern "C" pr_status pr_last_solve_columns(int32_t *columns, int32_t *mixed_columns) {
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    if (columns) *columns = g_last_stats.columns;
+    if (mixed_columns) *mixed_columns = g_last_stats.mixed_columns;
+    return PR_OK;
+}
+
 extern "C" pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms) {
     std::lock_guard<std::mutex> lk(g_stats_mu);
     if (launches) *launches = g_last_stats.launches;
@@ -926,6 +933,8 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         }
     }
     PR_CUDA(cudaStreamSynchronize(st));
+    stats.columns = ncols;
+    stats.mixed_columns = mixed ? ncols : 0;
     req.stats = stats;
     return PR_OK;
 }

@@ -26,7 +26,8 @@ def _rank_main(rank, world, port, out_dir):
     assert (w, r) == (world, rank)
     dist.barrier(w, "cpu")
     mx = dist.max_over_ranks(1.5 * (rank + 1), w, "cpu")
-    graphs, specs, prec, _ = bench.make_workload("sweep330", gg, rank)
+    wl = bench.make_workload("sweep330", gg, rank)
+    graphs, specs = wl.graphs, wl.specs
     shapes = [None] * world
     tdist.all_gather_object(shapes, (graphs[0].n, len(specs), int(graphs[0].sources[:64].sum())))
     dist.barrier(w, "cpu")

@@ -268,3 +268,79 @@ def test_sweep_outputs_match_oracle(B, orc, er):
         # each answer is within 1e-12 (relative L1) of the oracle's
         assert abs(d_gpu - d_orc) <= 4e-12, (a, d_gpu, d_orc)
         assert x.iters * refs[k85].iters == r.iters * xs[k85].iters, (a, x.iters, r.iters)
+
+
+def test_fp32_stalls_in_the_papers_order(B, gg):
+    """The sensitivity stalls of Section 4 reproduced with FP32 arithmetic on a
+    slow-mixing road-like lattice (300 x 400, seed 7), alpha 0.85: below some
+    tau the FP32 iteration cannot reduce its step and runs into the 500 cap,
+    first for L1, then L2, then Linf (the paper: L1 from 1e-8, L2/Linf from
+    1e-9 on web-BerkStan), while DF64 converges at every tau."""
+    g = gg.road_grid(300, 400, seed=7)
+    taus = [10.0 ** -k for k in range(4, 13)]
+    onset = {}
+    with B.Graph.from_csr(g) as dg:
+        for prec in ("fp32", "df64"):
+            xs = [B.Instance(dg, 0.85, t, nm, 500) for t in taus for nm in (1, 2, 3)]
+            B.pr_solve_batch(xs, precision=prec)
+            for nm in (1, 2, 3):
+                hit = [x.tol for x in xs if x.norm == nm and x.iters >= 500]
+                # once a norm stalls, every smaller tau stalls too
+                assert all(not x.converged for x in xs if x.norm == nm and hit and x.tol <= max(hit))
+                onset[(prec, nm)] = max(hit) if hit else 0.0
+    assert onset[("df64", 1)] == onset[("df64", 2)] == onset[("df64", 3)] == 0.0
+    assert onset[("fp32", 1)] > 0.0
+    assert onset[("fp32", 1)] > onset[("fp32", 2)] > onset[("fp32", 3)] > 0.0
+
+
+def test_planner_precision_choice(B, orc, gg):
+    """PR_PREC_AUTO: per graph the planner runs DF64 or mixed precision,
+    whichever its cost model predicts cheaper; every answer meets the bound of
+    the precision used (FP64 parity when no column ran mixed)."""
+    g = gg.rmat(15, 16, seed=71)
+    alphas = (0.5, 0.7, 0.85, 0.9, 0.95)
+    with B.Graph.from_csr(g) as dg:
+        xs = [B.Instance(dg, a, 1e-10, 1, 500) for a in alphas]
+        B.pr_solve_batch(xs, precision="auto")
+        st = B.pr_last_solve_stats()
+        assert st["columns"] == len(alphas) and 0 <= st["mixed_columns"] <= len(alphas)
+        for a, x in zip(alphas, xs):
+            if st["mixed_columns"] == 0:
+                ref = orc.pagerank(g, a, 1e-10, 1, 500, history=True, threads=orc.default_threads())
+                assert_fp64_parity(x.out, x.iters, x.err, ref, 1e-10, 1, f"auto alpha {a}")
+            else:
+                star = orc.pagerank(g, a, 1e-13, 1, 10000, threads=orc.default_threads())
+                assert_bound_parity(orc, g, a, 1e-10, 1, 500, x.out, x.iters, x.converged, star.ranks,
+                                    what=f"auto alpha {a}")
+        # mixed requested: every column mixed
+        B.pr_solve_batch([B.Instance(dg, a, 1e-10, 1, 500) for a in alphas], precision="mixed")
+        assert B.pr_last_solve_stats()["mixed_columns"] == len(alphas)
+
+
+def test_fp32_split_passes_beyond_the_hub_table(B, orc, gg):
+    """FP32 split passes on a graph larger than the gather kernel's shared
+    hub table (R-MAT scale 17: 131,072 vertices), against the oracle's fixed
+    point (tau-only bound of an L1 stop)."""
+    g = gg.rmat(17, 16, seed=73)
+    star = orc.pagerank(g, 0.85, 1e-13, 1, 10000, threads=orc.default_threads())
+    with B.Graph.from_csr(g) as dg:
+        x = B.Instance(dg, 0.85, 1e-5, 1, 500)
+        B.pr_solve_batch([x], precision="fp32", kernels="split")
+        assert x.converged
+        assert_bound_parity(orc, g, 0.85, 1e-5, 1, 500, x.out, x.iters, x.converged, star.ranks, what="fp32 split")
+
+
+def test_workspace_pool_info_and_release(B, er):
+    """The workspace pool lends memory only during calls and keeps it reserved
+    between them; pr_workspace_release returns the reserve to the device."""
+    import torch
+    with B.Graph.from_csr(er) as dg:
+        B.pr_solve(dg, 0.85, 1e-10, 1, 500)
+        torch.cuda.synchronize()
+        reserved, used, high = B.workspace_info()
+        assert used == 0 and high > 0 and reserved >= high
+        B.workspace_release()
+        reserved2, used2, _ = B.workspace_info()
+        assert used2 == 0 and reserved2 == 0
+        B.pr_solve(dg, 0.85, 1e-10, 1, 500)          # reserves again as needed
+        assert B.workspace_info()[0] > 0
