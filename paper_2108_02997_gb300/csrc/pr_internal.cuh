@@ -180,6 +180,8 @@ struct ClassRange {
 struct ColState {
     double alpha;
     double c0;            // teleport term of the next update (FP64)
+    double c0_base;       // (1 - alpha)/N and alpha/N: c0 = c0_base + c0_coef * (dangling sum),
+    double c0_coef;       //   the two divisions of Section 2's c0 done once on the host
     double v_alpha[2];    // alpha in the job's value type (raw bits: 4 or 8 bytes used)
     double v_c0[2];       // c0 in the job's value type (init pass: the uniform start 1/N)
     int32_t active;       // 1 while the column still updates

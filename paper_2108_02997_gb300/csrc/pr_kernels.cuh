@@ -188,14 +188,13 @@ __device__ __forceinline__ void row_update(const int32_t *__restrict__ outdeg, c
 // CTA partials of the thread accumulators, then the job finalizer (last CTA of
 // the job) and the global decision (last job). Shared by both kernels.
 template <typename V, int W>
-__device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V> &acc, int local, int mode) {
+__device__ __noinline__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V> &acc, int local, int mode) {
     using N = Num<V>;
     using Acc = typename N::Acc;
     const int tid = threadIdx.x;
     const int col = tid % W;
     __shared__ Acc s_red[kWarps][W][kPartials];
     __shared__ int s_flag;
-    __shared__ double s_tot[kBlock];
     __shared__ double s_fin[W * kPartials];
     {
         Acc a[kPartials] = {acc.l1, acc.l2, acc.linf, acc.dsum, acc.rsum};
@@ -246,33 +245,31 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
     ColState *const cols = job.cols;
     Tap *const taps = job.taps;
     const double *const cta_part = job.cta_part;
-    // fixed-order FP64 reduction over the job's CTAs, four loads in flight per thread
+    // fixed-order FP64 reduction over the job's CTAs: partial p by warp
+    // p mod kWarps, lane l adding CTAs l, l + 32, ... (four loads in flight),
+    // then a fixed butterfly over the lanes; short dependent chains, since
+    // every FP64 operation on this GPU has a long latency
     {
         constexpr int P = W * kPartials;
-        constexpr int S = kBlock / P;
-        const int p = tid % P, sl = tid / P;
-        const int k = p % kPartials;
-        double t = 0.0;
-        if (sl < S) {
-            for (int c = sl; c < cta_count; c += 4 * S) {
+        const int rl = tid & 31, rw = tid >> 5;
+        for (int p = rw; p < P; p += kWarps) {
+            const bool is_max = (p % kPartials) == 2;
+            double t = 0.0;
+            for (int c = rl; c < cta_count; c += 4 * 32) {
                 double x[4];
 #pragma unroll
                 for (int u = 0; u < 4; u++)
-                    x[u] = c + u * S < cta_count ? ld_cg(cta_part + (size_t)(c + u * S) * P + p) : 0.0;
+                    x[u] = c + 32 * u < cta_count ? ld_cg(cta_part + (size_t)(c + 32 * u) * P + p) : 0.0;
 #pragma unroll
                 for (int u = 0; u < 4; u++)
-                    if (c + u * S < cta_count) t = (k == 2) ? fmax(t, x[u]) : t + x[u];
+                    if (c + 32 * u < cta_count) t = is_max ? fmax(t, x[u]) : t + x[u];
             }
-        }
-        s_tot[tid] = t;
-        __syncthreads();
-        if (tid < P) {
-            double r = s_tot[tid];
-            for (int q = 1; q < S; q++) {
-                double x = s_tot[q * P + tid];
-                r = (k == 2) ? fmax(r, x) : r + x;
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) {
+                const double o = __shfl_xor_sync(0xffffffffu, t, m);
+                t = is_max ? fmax(t, o) : t + o;
             }
-            s_fin[tid] = r;
+            if (rl == 0) s_fin[p] = t;
         }
         __syncthreads();
     }
@@ -296,13 +293,12 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
         const double li = s_fin[c * kPartials + 2];
         const double D = s_fin[c * kPartials + 3];
         const double S = s_fin[c * kPartials + 4];
-        const double Nn = (double)n_rows;
         int col_alive = 0;
         if (mode == kPassInit) {
             col_alive = cs.active;
             __syncwarp();
             if (lane == 0) {
-                cs.c0 = (1.0 - cs.alpha) / Nn + cs.alpha * D / Nn;
+                cs.c0 = fma(cs.c0_coef, D, cs.c0_base);
                 store_raw<V>(cs.v_c0, N::from_double(cs.c0));
                 cs.last_sum = S;
                 cs.copy_dst = nullptr;
@@ -367,7 +363,7 @@ __device__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V
                 if (cs.switch_norm && !cs.switched && errs[cs.switch_norm - 1] <= cs.switch_tol)
                     cs.switched = 1;   // hand over to the refinement phase
                 cs.active = active ? 1 : 0;
-                cs.c0 = (1.0 - cs.alpha) / Nn + cs.alpha * D / Nn;
+                cs.c0 = fma(cs.c0_coef, D, cs.c0_base);
                 store_raw<V>(cs.v_c0, N::from_double(cs.c0));
             }
         } else {

@@ -140,6 +140,8 @@ extern "C" pr_status pr_solve_noalloc(const pr_graph *g, double alpha, double to
     ColState cs;
     std::memset(&cs, 0, sizeof(cs));
     cs.alpha = alpha;
+    cs.c0_base = (1.0 - alpha) / (double)g->n;
+    cs.c0_coef = alpha / (double)g->n;
     df64 a = df_from_double(alpha), u = df_from_double(1.0 / (double)g->n);
     std::memcpy(cs.v_alpha, &a, sizeof(a));
     std::memcpy(cs.v_c0, &u, sizeof(u));   // init pass reads the uniform start here

@@ -794,6 +794,8 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             SolveColumn &sc = req.cols[j.cols[k]];
             ColState &cs = hcols[k];
             cs.alpha = sc.alpha;
+            cs.c0_base = (1.0 - sc.alpha) / (double)j.g->n;
+            cs.c0_coef = sc.alpha / (double)j.g->n;
             store_value(cs.v_alpha, prec1, sc.alpha);
             store_value(cs.v_c0, prec1, 1.0 / (double)j.g->n);   // init pass: uniform start value
             cs.active = 1;
