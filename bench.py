@@ -95,7 +95,8 @@ class Workload:
     specs: list                 # (graph index, alpha, tau, norm, max_iter)
     desc: str
     precision: str = "df64"     # batched arm
-    learned: bool = False       # batched arm starts from the learned warm start
+    learned: bool = False       # the learned warm start takes part (trained before timing)
+    start: str = "uniform"      # batched arm's start: uniform, learned, or auto (learned where it pays)
     dgs: list = field(default_factory=list)
     outs: list = field(default_factory=list)
 
@@ -118,13 +119,14 @@ def make_workload(name, gg, rank=0) -> Workload:
     if name == "sweep330":
         g = gg.erdos_renyi_10k(seed=s(1))
         return Workload(name, [g], sweep_specs([0], ALPHAS_SWEEP),
-                        "er-10k (100k edges, 5% dangling), 11 alpha x 10 tau x 3 norms; learned start, auto precision",
-                        precision="auto", learned=True)
+                        ("er-10k (100k edges, 5% dangling), 11 alpha x 10 tau x 3 norms; planner-chosen start "
+                         "(learned where it pays) and precision"),
+                        precision="auto", learned=True, start="auto")
     if name == "sweep330warm":
         g = gg.erdos_renyi_10k(seed=s(1))
         return Workload(name, [g], sweep_specs([0], ALPHAS_SWEEP),
                         "er-10k, 11 alpha x 10 tau x 3 norms; learned start, fp32->df64", precision="mixed",
-                        learned=True)
+                        learned=True, start="learned")
     if name == "multi64":
         gs = [gg.rmat(12 + (i % 9), 16, seed=s(1000 + i)) for i in range(64)]
         specs = [(i, 0.85, 1e-10, 1, 500) for i in range(64)]
@@ -134,8 +136,8 @@ def make_workload(name, gg, rank=0) -> Workload:
         gs = [gg.rmat(22, 16, seed=s(3022)), gg.rmat(24, 16, seed=s(3024)), gg.config_model(8_000_000, seed=s(3008))]
         return Workload(name, gs, sweep_specs(range(3), ALPHAS_TRAIN),
                         ("unseen rmat-s22 (seed 3022), rmat-s24 (seed 3024), config model N=8M (seed 3008); "
-                         "10 alpha x 10 tau x 3 norms each; learned start, auto precision"),
-                        precision="auto", learned=True)
+                         "10 alpha x 10 tau x 3 norms each; planner-chosen start (learned where it pays) and precision"),
+                        precision="auto", learned=True, start="auto")
     if name == "rmat24mixed":
         g = gg.rmat(24, 16, seed=s(24))
         specs = [(0, a, 1e-10, 3, 500) for a in (0.85, 0.95)]
@@ -150,7 +152,7 @@ def make_workload(name, gg, rank=0) -> Workload:
         gs = [gg.rmat(22, 16, seed=s(3022)), gg.rmat(24, 16, seed=s(3024)), gg.config_model(8_000_000, seed=s(3008))]
         specs = [(i, a, 1e-10, 1, 500) for i in range(len(gs)) for a in (0.5, 0.6, 0.7, 0.8, 0.85, 0.9, 0.95)]
         return Workload(name, gs, specs, ("unseen rmat-s22, rmat-s24, config model N=8M; 7 alpha x tau 1e-10 L1; "
-                                          "learned start, fp32->df64"), precision="mixed", learned=True)
+                                          "learned start, fp32->df64"), precision="mixed", learned=True, start="learned")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -359,20 +361,24 @@ def run_ours(args, world, rank, local):
     def solve(w, share=True, init=None, precision=None, loop=None):
         xs = [B.Instance(w.dgs[gi], a, t, nm, mi, out=w.outs[k]) for k, (gi, a, t, nm, mi) in enumerate(w.specs)]
         kw = {}
-        if init == "learned":
-            kw = {"init": "learned", "mlp": mlp}
+        if init in ("learned", "auto"):
+            kw = {"init": init, "mlp": mlp}
         B.pr_solve_batch(xs, precision=precision or w.precision, outputs_on_device=True, stream=sptr, share=share,
                          loop=loop or args.loop, **kw)
         return xs
 
     def batched(w):
-        return solve(w, init="learned" if w.learned else None)
+        return solve(w, init=w.start)
 
     for _ in range(args.warmup):
         flush.zero_()
         for w in wls:
             batched(w)
     torch.cuda.synchronize()
+    learned_cols = {}
+    for w in wls:
+        batched(w)
+        learned_cols[w.name] = B.pr_last_solve_stats()["learned_columns"]
     per_w = {w.name: [] for w in wls}
     launches = 0
     last = {}
@@ -401,7 +407,8 @@ def run_ours(args, world, rank, local):
         xs = last[w.name]
         rec = {"instances": len(w.specs), "graphs": len(w.graphs), "edges": sum(g.nnz for g in w.graphs),
                "trajectories": len(trajectories(w)), "batched_ms": ms_w[w.name],
-               "batched": {"precision": w.precision, "start": "learned" if w.learned else "uniform"},
+               "batched": {"precision": w.precision, "start": w.start,
+                           "learned_start_columns": learned_cols[w.name]},
                "iterations_total": sum(x.iters for x in xs),
                "converged": sum(1 for x in xs if x.converged)}
         # edges traversed: each trajectory's graph times its last tap's iterations
@@ -418,14 +425,19 @@ def run_ours(args, world, rank, local):
                 t_plain += time.perf_counter() - t0
             rec["plain_ms"] = t_plain * 1000.0
             rec["ratio"] = rec["plain_ms"] / rec["batched_ms"]
-            ms_ns, _ = cuda_ms(torch, stream, lambda w=w: solve(w, share=False, init="learned" if w.learned else None))
+            ms_ns, _ = cuda_ms(torch, stream, lambda w=w: solve(w, share=False, init=w.start))
             rec["batched_no_share_ms"] = ms_ns
             rec["ratio_no_share"] = rec["plain_ms"] / ms_ns
         if w.learned:
+            # both fixed starts, each timed once: what the learned start saves
+            # net of its own cost (features, network, softmax)
             ms_u, xu = cuda_ms(torch, stream, lambda w=w: solve(w))
-            rec["uniform_start"] = {"batched_ms": ms_u, "iterations_total": sum(x.iters for x in xu),
-                                    "learned_saves_iterations": sum(x.iters for x in xu) - rec["iterations_total"],
-                                    "learned_net_ms": ms_u - ms_w[w.name]}
+            ms_l, xl = cuda_ms(torch, stream, lambda w=w: solve(w, init="learned"))
+            it_u, it_l = sum(x.iters for x in xu), sum(x.iters for x in xl)
+            rec["uniform_start"] = {"batched_ms": ms_u, "iterations_total": it_u}
+            rec["learned_start"] = {"batched_ms": ms_l, "iterations_total": it_l,
+                                    "saves_iterations": it_u - it_l, "net_ms_saved": ms_u - ms_l}
+            rec["mlp_gain"] = mlp.gain()[0]
             # the start's own cost: features once per graph, network and softmax per alpha
             ws = []
             for dg in w.dgs:
@@ -520,7 +532,9 @@ def roofline_s22(B, gg, torch, sptr, rank, have):
     ratio, tsrc = kernel_traffic_ratio()
     if have is None:
         dg.close()
+    ceiling = gather_ceiling(g, b_gather, gather_us)
     return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "ceiling": ceiling,
             "traffic": ratio * b_gather if ratio else None, "traffic_source": tsrc,
             "kernel": "pr_gather_hub_kernel<df64> (gather half of a one-column pass)",
             "workload": "rmat-s22 ef16 seed22 (N 4,194,304, E %d), alpha .85, tau {1e-6,1e-10} x {L1,L2,Linf}, df64"
@@ -530,6 +544,37 @@ def roofline_s22(B, gg, torch, sptr, rank, have):
             "pass": {"avg_pass_us": pass_us, "algorithmic_bytes_per_pass": b_pass,
                      "achieved": b_pass / (pass_us * 1e-6) / 1e9, "frac": b_pass / (pass_us * 1e-6) / 1e9 / hbm,
                      "update_kernel_us": st["update_ms"] / passes * 1e3}}
+
+
+def gather_ceiling(g, b_gather, gather_us, hub_values=12288):
+    """What the GPU's memory system allows this gather (libprceiling.so, CUDA
+    probes over the same relabelled in-edge stream, no row sums): the index
+    stream alone, every gather through L1/L2, the same with the hub table in
+    shared memory, and uniform random gathers over a table of N values."""
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_2108_02997_gb300 import _build
+    L = C.CDLL(str(_build.build_ceiling()))
+    L.prc_gather_ceiling.argtypes = [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+    L.prc_gather_ceiling.restype = C.c_int
+    off = np.ascontiguousarray(g.offsets, np.int32)
+    src = np.ascontiguousarray(g.sources, np.int32)
+    od = np.ascontiguousarray(g.outdeg, np.int32)
+    us = np.zeros(4, np.float64)
+    rc = L.prc_gather_ceiling(g.n, g.nnz, off.ctypes.data, src.ctypes.data, od.ctypes.data, hub_values, us.ctypes.data)
+    if rc != 0:
+        return {"error": f"probe returned {rc}"}
+    best = min(us[1], us[2])
+    return {"index_stream_us": us[0], "gathers_us": us[1], "gathers_hub_us": us[2], "hub_values": hub_values,
+            "uniform_random_us": us[3], "gathers_per_s": g.nnz / (us[1] * 1e-6),
+            "gathers_hub_per_s": g.nnz / (us[2] * 1e-6), "uniform_random_gathers_per_s": g.nnz / (us[3] * 1e-6),
+            "ceiling_frac_of_peak": b_gather / (best * 1e-6) / 1e9 / peaks()[0],
+            "kernel_vs_ceiling": best / gather_us,
+            "what": ("edge-parallel probes over the same relabelled in-edge stream, eight gathers per thread in "
+                     "flight, values folded by XOR (no row sums): the fastest the memory system serves these "
+                     "random 8-byte reads; kernel_vs_ceiling = probe time / gather kernel time")}
 
 
 def run_e2e(B, torch, wls, mlp, sptr, args, world):
@@ -554,7 +599,7 @@ def run_e2e(B, torch, wls, mlp, sptr, args, world):
         for w, pw, pk, hw in zip(wls, pinned, picks, host):
             hg = [B.Graph(*p) for p in pw]
             xs = [B.Instance(hg[gi], a, t, nm, mi, out=w.outs[k]) for k, (gi, a, t, nm, mi) in enumerate(w.specs)]
-            kw = {"init": "learned", "mlp": mlp} if w.learned else {}
+            kw = {"init": w.start, "mlp": mlp} if w.start != "uniform" else {}
             B.pr_solve_batch(xs, precision=w.precision, outputs_on_device=True, stream=sptr, **kw)
             for k, h in zip(pk, hw):
                 h.copy_(w.outs[k], non_blocking=True)

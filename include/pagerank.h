@@ -99,7 +99,7 @@ typedef enum pr_init {
     PR_INIT_UNIFORM = 0,  /* 1/N everywhere */
     PR_INIT_USER = 1,     /* caller's vector, used as given (not renormalised) */
     PR_INIT_LEARNED = 2,  /* MLP warm start (pr_mlp), renormalised to sum 1 */
-    PR_INIT_CHAIN = 3     /* alpha continuation (pr_solve_batch): on each graph
+    PR_INIT_CHAIN = 3,    /* alpha continuation (pr_solve_batch): on each graph
                              the columns (iterate sequences) are taken in
                              increasing alpha; the first starts from 1/N and each
                              later one from the final iterate of the one before
@@ -107,6 +107,21 @@ typedef enum pr_init {
                              columns of one graph then run one after another
                              (those of different graphs side by side); the
                              alpha sweep of Section 2 in the order it is swept */
+    PR_INIT_AUTO = 4      /* pr_solve_batch with a pr_mlp: per (graph, alpha)
+                             column, the learned start where its predicted
+                             saving exceeds its measured cost, else 1/N. The
+                             network removes about `gain` e-folds of the start's
+                             L1 error (pr_mlp_gain), which at the column's
+                             contraction rate (alpha times the graph's decay
+                             measured by pr_graph_tune, relative to 0.85) saves
+                             gain / ln(1/rate) updates, each worth the tuned
+                             one-column launch time (less the latency that
+                             jobs sharing a launch share, when the graph has
+                             several columns); the cost is the network's device time
+                             per alpha plus the features' per graph, divided
+                             over the graph's alphas (both measured on first
+                             use per graph signature). A network without a
+                             positive gain is never used. */
 } pr_init;
 
 /* Device-side loop control. */
@@ -355,6 +370,17 @@ pr_status pr_mlp_train(pr_mlp *m, const pr_graph *const *graphs, const double *a
                        float *loss_out, void *stream);
 
 /*
+ * The network's gain: the mean over its training sets of
+ * ln(||1/N - r*||_1 / ||r0 - r*||_1), r0 its start and r* the set's target,
+ * measured at the end of pr_mlp_train (epochs > 0); known_out (may be NULL)
+ * is 1 once measured or set. pr_mlp_set_gain sets it for a network created
+ * from saved parameters (finite; PR_INIT_AUTO uses the network only for a
+ * positive gain). No counterpart in the paper.
+ */
+pr_status pr_mlp_gain(const pr_mlp *m, double *gain_out, int32_t *known_out);
+pr_status pr_mlp_set_gain(pr_mlp *m, double gain);
+
+/*
  * Autotuning of the column width (no counterpart in the paper, which solves
  * one instance at a time): times the iteration kernel on graph g for the
  * widths W = 1, 2, 4, ..., max_width (a power of two, 1..32) in `precision`
@@ -450,10 +476,12 @@ pr_status pr_workspace_release(void);
 
 /*
  * Columns (iterate sequences) of the last pr_solve / pr_solve_batch and, of
- * those, the ones solved in mixed precision (FP32 then DF64): with
- * PR_PREC_AUTO, what the planner chose. Host pointers, each may be NULL.
+ * those, the ones solved in mixed precision (FP32 then DF64; with
+ * PR_PREC_AUTO, what the planner chose) and the ones started from the learned
+ * start (with PR_INIT_AUTO, what the cost model chose). Host pointers, each
+ * may be NULL.
  */
-pr_status pr_last_solve_columns(int32_t *columns, int32_t *mixed_columns);
+pr_status pr_last_solve_columns(int32_t *columns, int32_t *mixed_columns, int32_t *learned_columns);
 
 /* Message for the last error on this thread ("" if none). */
 const char *pr_last_error(void);

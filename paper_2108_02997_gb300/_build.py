@@ -2,6 +2,8 @@
 
 * ``libprgraphgen.so`` — the seeded graph generators (plain C, gcc).
 * ``libpagerank.so``  — the C-ABI PageRank library (CUDA, nvcc, sm_103a only).
+* ``libprceiling.so`` — the gather-rate probes bench.py reports beside its
+  roofline (CUDA; measurement only, not part of the library).
 
 Each library is rebuilt when a source file is newer than it, or when the
 extra compiler definitions in the environment variable PR_NVCC_FLAGS (tuning
@@ -24,6 +26,7 @@ BUILD = PKG / "_build"
 
 GRAPHGEN_SO = PKG / "libprgraphgen.so"
 PAGERANK_SO = PKG / "libpagerank.so"
+CEILING_SO = PKG / "libprceiling.so"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -96,6 +99,19 @@ def build_pagerank(force: bool = False, verbose_ptxas: bool = False) -> Path:
     return PAGERANK_SO
 
 
+def build_ceiling(force: bool = False) -> Path:
+    src = CSRC / "gather_ceiling.cu"
+    if force or _stale(CEILING_SO, [src, Path(__file__)]):
+        tmp = CEILING_SO.with_suffix(".so.tmp")
+        _run([_nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", str(tmp), str(src),
+              "-lcudart"])
+        os.replace(tmp, CEILING_SO)
+    return CEILING_SO
+
+
 def build_all(force: bool = False) -> None:
     build_graphgen(force)
-    build_pagerank(force)
+    with _cf.ThreadPoolExecutor(max_workers=2) as ex:
+        futs = [ex.submit(build_pagerank, force), ex.submit(build_ceiling, force)]
+        for f in futs:
+            f.result()

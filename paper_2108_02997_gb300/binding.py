@@ -24,7 +24,7 @@ from . import _build
 PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT, PR_ESTATE, PR_ENOTSUP = range(7)
 PR_NORM_L1, PR_NORM_L2, PR_NORM_LINF = 1, 2, 3
 PR_PREC_DF64, PR_PREC_FP64, PR_PREC_MIXED, PR_PREC_FP32, PR_PREC_AUTO = 0, 1, 2, 3, 4
-PR_INIT_UNIFORM, PR_INIT_USER, PR_INIT_LEARNED, PR_INIT_CHAIN = 0, 1, 2, 3
+PR_INIT_UNIFORM, PR_INIT_USER, PR_INIT_LEARNED, PR_INIT_CHAIN, PR_INIT_AUTO = 0, 1, 2, 3, 4
 PR_LOOP_GRAPH, PR_LOOP_HOST = 0, 1
 PR_GROUP_AUTO, PR_GROUP_PACK, PR_GROUP_SINGLE = 0, 1, 2
 GROUPS = {"auto": PR_GROUP_AUTO, "pack": PR_GROUP_PACK, "single": PR_GROUP_SINGLE}
@@ -79,7 +79,9 @@ SIGNATURES = {
     "pr_mlp_loss_grad": ([_vp, _vp, _d, _vp, _vp, _vp, _vp], _i32),
     "pr_last_solve_stats": ([_vp, _vp, _vp, _vp], _i32),
     "pr_last_solve_kernel_ms": ([_vp, _vp], _i32),
-    "pr_last_solve_columns": ([_vp, _vp], _i32),
+    "pr_last_solve_columns": ([_vp, _vp, _vp], _i32),
+    "pr_mlp_gain": ([_vp, _vp, _vp], _i32),
+    "pr_mlp_set_gain": ([_vp, _d], _i32),
     "pr_graph_tune": ([_vp, _i32, _i32, _vp, _vp], _i32),
     "pr_kernel_occupancy": ([_i32, _i32, _vp], _i32),
     "pr_plan_columns": ([_i32, _vp, _vp, _vp, _vp, _vp], _i32),
@@ -213,8 +215,8 @@ def _make_options(precision="df64", init=None, loop="graph", stream=None, share=
         o.init_vec = addr
         o.init_on_device = 1 if dev else 0
         keep.append(init)
-    elif init == "learned":
-        o.init = PR_INIT_LEARNED
+    elif init in ("learned", "auto"):
+        o.init = PR_INIT_LEARNED if init == "learned" else PR_INIT_AUTO
         o.mlp = mlp.handle if mlp is not None else None
     elif init == "chain":
         o.init = PR_INIT_CHAIN
@@ -262,6 +264,18 @@ class Instance:
     status: int = 0
 
 
+# pr_instance as a numpy record (same layout), so that large batches are
+# marshalled with array operations instead of one ctypes structure per instance
+_INST_DTYPE = np.dtype({"names": ["g", "alpha", "tol", "norm", "max_iter", "ranks_out", "init_vec", "iters",
+                                  "converged", "err", "err_l1", "status", "reserved"],
+                        "formats": [np.uint64, np.float64, np.float64, np.int32, np.int32, np.uint64, np.uint64,
+                                    np.int32, np.int32, np.float64, np.float64, np.int32, np.int32],
+                        "offsets": [0, 8, 16, 24, 28, 32, 40, 48, 52, 56, 64, 72, 76], "itemsize": 80})
+assert _INST_DTYPE.itemsize == C.sizeof(pr_instance)
+for _f, *_ in pr_instance._fields_:
+    assert _INST_DTYPE.fields[_f][1] == getattr(pr_instance, _f).offset, _f
+
+
 def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=None, share=True,
                    switch_tol=1e-6, outputs_on_device=False, mlp=None, check=True, group="auto", max_passes=0,
                    kernels="auto"):
@@ -269,43 +283,56 @@ def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=N
     torch CUDA tensors when ``outputs_on_device``), ``iters``, ``err``,
     ``converged`` and ``status`` of every :class:`Instance`; returns the
     library status."""
-    arr = (pr_instance * max(len(insts), 1))()
+    n = len(insts)
+    arr = np.zeros(max(n, 1), _INST_DTYPE)
     keep = []
-    any_dev = outputs_on_device
-    for i, x in enumerate(insts):
-        if x.out is None:
-            if outputs_on_device:
-                import torch
+    if outputs_on_device:
+        import torch
+        for x in insts:
+            if x.out is None:
                 x.out = torch.empty(x.graph.n, dtype=torch.float64, device="cuda")
-            else:
+            if not (isinstance(x.out, torch.Tensor) and x.out.is_cuda and x.out.is_contiguous()):
+                raise ValueError("every out must be a contiguous CUDA tensor when outputs_on_device")
+        arr["ranks_out"][:n] = [x.out.data_ptr() for x in insts]
+    else:
+        outs = []
+        for x in insts:
+            if x.out is None:
                 x.out = np.empty(x.graph.n, np.float64)
-        addr, dev = _ptr_of(x.out)
-        if dev != bool(outputs_on_device):
-            raise ValueError("every out must live on the device iff outputs_on_device")
-        a = arr[i]
-        a.g = x.graph.handle
-        a.alpha = float(x.alpha)
-        a.tol = float(x.tol)
-        a.norm = int(NORMS[x.norm])
-        a.max_iter = int(x.max_iter)
-        a.ranks_out = addr
-        if x.init is not None:
-            ia, _ = _ptr_of(x.init)
-            a.init_vec = ia
-            keep.append(x.init)
-    if stream is None and any_dev:
+            addr, dev = _ptr_of(x.out)
+            if dev:
+                raise ValueError("every out must live on the device iff outputs_on_device")
+            outs.append(addr)
+        arr["ranks_out"][:n] = outs
+    arr["g"][:n] = [x.graph.handle.value or 0 for x in insts]
+    arr["alpha"][:n] = [x.alpha for x in insts]
+    arr["tol"][:n] = [x.tol for x in insts]
+    arr["norm"][:n] = [NORMS[x.norm] for x in insts]
+    arr["max_iter"][:n] = [x.max_iter for x in insts]
+    if any(x.init is not None for x in insts):
+        inits = []
+        for x in insts:
+            if x.init is not None:
+                inits.append(_ptr_of(x.init)[0])
+                keep.append(x.init)
+            else:
+                inits.append(0)
+        arr["init_vec"][:n] = inits
+    if stream is None and outputs_on_device:
         stream = current_stream_ptr()
     o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, outputs_on_device, mlp, group,
                              max_passes, kernels)
     if any(x.init is not None for x in insts) and o.init == PR_INIT_UNIFORM:
         o.init = PR_INIT_USER
-    st = lib().pr_solve_batch(arr, len(insts), C.byref(o))
+    st = lib().pr_solve_batch(arr.ctypes.data, n, C.byref(o))
+    iters, conv, err, err1, stat = (arr["iters"].tolist(), arr["converged"].tolist(), arr["err"].tolist(),
+                                    arr["err_l1"].tolist(), arr["status"].tolist())
     for i, x in enumerate(insts):
-        x.iters = arr[i].iters
-        x.err = arr[i].err
-        x.err_l1 = arr[i].err_l1
-        x.converged = bool(arr[i].converged)
-        x.status = arr[i].status
+        x.iters = iters[i]
+        x.err = err[i]
+        x.err_l1 = err1[i]
+        x.converged = bool(conv[i])
+        x.status = stat[i]
     if check:
         _check(st, "pr_solve_batch")
     return st
@@ -374,10 +401,11 @@ def pr_last_solve_stats():
     lib().pr_last_solve_stats(C.byref(la), C.byref(pa), C.byref(km), C.byref(tm))
     gm, um = C.c_double(), C.c_double()
     lib().pr_last_solve_kernel_ms(C.byref(gm), C.byref(um))
-    co, mc = C.c_int32(), C.c_int32()
-    lib().pr_last_solve_columns(C.byref(co), C.byref(mc))
+    co, mc, lc = C.c_int32(), C.c_int32(), C.c_int32()
+    lib().pr_last_solve_columns(C.byref(co), C.byref(mc), C.byref(lc))
     return {"launches": la.value, "passes": pa.value, "kernel_ms": km.value, "total_ms": tm.value,
-            "gather_ms": gm.value, "update_ms": um.value, "columns": co.value, "mixed_columns": mc.value}
+            "gather_ms": gm.value, "update_ms": um.value, "columns": co.value, "mixed_columns": mc.value,
+            "learned_columns": lc.value}
 
 
 class MLP:
@@ -429,6 +457,15 @@ class MLP:
         _check(lib().pr_mlp_train(self.handle, gs, al, tg, n, int(epochs), float(lr), C.byref(loss), stream),
                "pr_mlp_train")
         return float(loss.value)
+
+    def gain(self):
+        """(gain, known): e-folds of start error the network removes (pr_mlp_gain)."""
+        g, k = C.c_double(), C.c_int32()
+        _check(lib().pr_mlp_gain(self.handle, C.byref(g), C.byref(k)), "pr_mlp_gain")
+        return g.value, bool(k.value)
+
+    def set_gain(self, gain: float):
+        _check(lib().pr_mlp_set_gain(self.handle, float(gain)), "pr_mlp_set_gain")
 
     def close(self):
         if self.handle is not None and self.handle.value:

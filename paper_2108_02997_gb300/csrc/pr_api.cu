@@ -79,14 +79,15 @@ namespace {
 
 pr_status check_options(const pr_options &o) {
     if (o.precision < PR_PREC_DF64 || o.precision > PR_PREC_AUTO) return pr_fail(PR_EINVAL, "unknown precision");
-    if (o.init < PR_INIT_UNIFORM || o.init > PR_INIT_CHAIN) return pr_fail(PR_EINVAL, "unknown init mode");
+    if (o.init < PR_INIT_UNIFORM || o.init > PR_INIT_AUTO) return pr_fail(PR_EINVAL, "unknown init mode");
     if (o.loop != PR_LOOP_GRAPH && o.loop != PR_LOOP_HOST) return pr_fail(PR_EINVAL, "unknown loop mode");
     if (o.group < PR_GROUP_AUTO || o.group > PR_GROUP_SINGLE) return pr_fail(PR_EINVAL, "unknown group mode");
     if (o.max_passes < 0) return pr_fail(PR_EINVAL, "max_passes must be >= 0");
     if (o.kernels < PR_KERNELS_AUTO || o.kernels > PR_KERNELS_SPLIT) return pr_fail(PR_EINVAL, "unknown kernels mode");
     if ((o.precision == PR_PREC_MIXED || o.precision == PR_PREC_AUTO) && !(o.switch_tol > 0.0 && std::isfinite(o.switch_tol)))
         return pr_fail(PR_EINVAL, "switch_tol must be positive and finite");
-    if (o.init == PR_INIT_LEARNED && !pr_mlp_valid(o.mlp)) return pr_fail(PR_EINVAL, "PR_INIT_LEARNED needs a live pr_mlp");
+    if ((o.init == PR_INIT_LEARNED || o.init == PR_INIT_AUTO) && !pr_mlp_valid(o.mlp))
+        return pr_fail(PR_EINVAL, "PR_INIT_LEARNED and PR_INIT_AUTO need a live pr_mlp");
     return PR_OK;
 }
 
@@ -138,6 +139,16 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
     std::map<std::pair<const void *, const void *>, const double *> init_dev;   // (graph, src) -> device copy
     std::map<std::pair<const pr_graph *, uint64_t>, const double *> learned;
     std::map<const pr_graph *, const void *> learned_feat;
+    std::map<std::pair<const pr_graph *, uint64_t>, bool> auto_use;   // PR_INIT_AUTO decisions per (graph, alpha)
+    std::map<const pr_graph *, int> alphas_on;                          // distinct alphas per graph
+    if (opt.init == PR_INIT_AUTO) {
+        std::set<std::pair<const pr_graph *, uint64_t>> seen;
+        for (int i : ok) {
+            uint64_t ab;
+            std::memcpy(&ab, &inst[i].alpha, 8);
+            if (seen.insert({inst[i].g, ab}).second) alphas_on[inst[i].g]++;
+        }
+    }
     auto start_for = [&](const pr_instance &in, const double **out) -> pr_status {
         *out = nullptr;
         if (opt.init == PR_INIT_UNIFORM || opt.init == PR_INIT_CHAIN) return PR_OK;   // chain: set per level below
@@ -161,6 +172,33 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
         auto key = std::make_pair(in.g, abits);
         auto it = learned.find(key);
         if (it != learned.end()) { *out = it->second; return PR_OK; }
+        if (opt.init == PR_INIT_AUTO) {
+            // the learned start where its predicted saving exceeds its measured
+            // cost: the network removes `gain` e-folds of the start's error, which
+            // at the column's contraction rate (alpha scaled by the graph's
+            // measured decay) saves gain / ln(1/rate) updates; an update saved on
+            // a column whose launches other columns share is worth the launch
+            // time less the latency they share. It costs the network once per
+            // alpha and the features once per graph
+            auto dit = auto_use.find(key);
+            if (dit == auto_use.end()) {
+                const double gain = pr_mlp_gain_value(opt.mlp);
+                bool use = false;
+                if (gain > 0.0 && in.alpha > 0.0) {
+                    double t1 = 0.0, lat = 0.0, rho = 0.0, feat_us = 0.0, net_us = 0.0;
+                    pr_status ps = pr_graph_pass_model(const_cast<pr_graph *>(in.g), st, &t1, &lat, &rho);
+                    if (ps == PR_OK) ps = pr_learned_cost(opt.mlp, in.g, st, &feat_us, &net_us);
+                    if (ps != PR_OK) return ps;
+                    double rate = rho > 0.0 ? std::min(in.alpha, in.alpha * rho / 0.85) : in.alpha;
+                    rate = std::min(std::max(rate, 1e-3), 1.0 - 1e-9);
+                    const double per_update = alphas_on[in.g] > 1 ? std::max(t1 - lat, 0.05 * t1) : t1;
+                    const double saved = gain / std::log(1.0 / rate) * per_update;
+                    use = saved > net_us + feat_us / std::max(1, alphas_on[in.g]);
+                }
+                dit = auto_use.emplace(key, use).first;
+            }
+            if (!dit->second) return PR_OK;   // uniform start
+        }
         // the features depend on the graph only: one pass per graph serves every alpha
         auto fit = learned_feat.find(in.g);
         if (fit == learned_feat.end()) {
@@ -212,7 +250,9 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
             sc.g = in.g;
             sc.alpha = in.alpha;
             sc.init_dev = start;
-            sc.init_relabelled = opt.init == PR_INIT_LEARNED;   // learned starts come in relabelled order
+            // learned starts come in relabelled order
+            sc.learned = (opt.init == PR_INIT_LEARNED || opt.init == PR_INIT_AUTO) && start != nullptr;
+            sc.init_relabelled = sc.learned;
             if (opt.share_trajectories) col_of[key] = c;
         }
         SolveColumn &sc = req.cols[c];

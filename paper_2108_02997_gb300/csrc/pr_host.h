@@ -64,6 +64,7 @@ struct SolveColumn {
     bool init_relabelled = false;       // init_dev in relabelled order (else caller order)
     double *hist_host = nullptr;
     int32_t hist_cap = 0;
+    bool learned = false;               // init_dev is the learned start
     double *final_dev = nullptr;        // optional: device, n doubles (caller order) receiving the
                                         // column's final iterate (its last stopping rule's answer)
 };
@@ -78,10 +79,11 @@ struct SolveStats {
     double update_ms = 0.0; //   and the update kernels' share
     int columns = 0;        // columns (iterate sequences) solved
     int mixed_columns = 0;  //   of which in mixed precision
+    int learned_columns = 0;//   of which from the learned start
     void add(const SolveStats &o) {
         launches += o.launches; passes += o.passes; kernel_ms += o.kernel_ms; total_ms += o.total_ms;
         gather_ms += o.gather_ms; update_ms += o.update_ms; columns += o.columns;
-        mixed_columns += o.mixed_columns;
+        mixed_columns += o.mixed_columns; learned_columns += o.learned_columns;
     }
 };
 
@@ -147,6 +149,14 @@ size_t pr_learned_features_bytes(const pr_graph *g);
 pr_status pr_learned_features(const pr_graph *g, void *feat, cudaStream_t st);
 pr_status pr_learned_start(const pr_mlp *m, const pr_graph *g, double alpha, double *d_out, bool relabelled,
                            cudaStream_t st, const void *feat = nullptr);
+// PR_INIT_AUTO's inputs: the network's gain (e-folds of start error removed;
+// 0 when unknown), the learned start's device time on g (features once per
+// graph, network per alpha; measured once per device and graph signature),
+// and the tuned one-column launch time, the latency that jobs sharing a
+// launch share, and the L1 decay rate of g (pr_plan.cu).
+double pr_mlp_gain_value(const pr_mlp *m);
+pr_status pr_learned_cost(const pr_mlp *m, const pr_graph *g, cudaStream_t st, double *feat_us, double *net_us);
+pr_status pr_graph_pass_model(pr_graph *g, cudaStream_t st, double *t1_us, double *lat_us, double *rho_l1);
 
 // Live-handle registry: guards every entry point against stale handles.
 void registry_add(const void *p);

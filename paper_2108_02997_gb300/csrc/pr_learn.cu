@@ -18,9 +18,11 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
+#include <tuple>
 #include <vector>
 
 #include "pr_internal.cuh"
@@ -51,6 +53,11 @@ struct pr_mlp {
     uint32_t magic;
     MlpDev d;
     int step;
+    // Mean over the training sets of ln(||1/N - r*||_1 / ||r0 - r*||_1): how
+    // many e-folds of the start's error the network removes (measured at the
+    // end of pr_mlp_train, or set by the caller); PR_INIT_AUTO's input.
+    double gain;
+    int has_gain;
 };
 
 bool pr_mlp_valid(const pr_mlp *m) { return m && registry_has(m) && m->magic == kMlpMagic; }
@@ -802,6 +809,57 @@ pr_status loss_grad(pr_mlp *m, const float *feat, const float *target, int32_t n
     return PR_OK;
 }
 
+// Per-CTA partial sums of |r0[v] - t[v]| and |1/n - t[v]| (FP64, fixed
+// order within a CTA); r0 and t both in caller order.
+__global__ void start_error_kernel(const double *__restrict__ r0, const double *__restrict__ t, int32_t n,
+                                   double *__restrict__ part) {
+    __shared__ double s_a[256], s_b[256];
+    double a = 0.0, b = 0.0;
+    const double u = 1.0 / (double)n;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        a += fabs(r0[v] - t[v]);
+        b += fabs(u - t[v]);
+    }
+    s_a[threadIdx.x] = a;
+    s_b[threadIdx.x] = b;
+    __syncthreads();
+    for (int m = 128; m > 0; m >>= 1) {
+        if ((int)threadIdx.x < m) {
+            s_a[threadIdx.x] += s_a[threadIdx.x + m];
+            s_b[threadIdx.x] += s_b[threadIdx.x + m];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s_a[0];
+        part[2 * blockIdx.x + 1] = s_b[0];
+    }
+}
+
+// ln(e_uniform / e_learned) of one (graph, alpha, target) set.
+pr_status start_gain(const pr_mlp *m, const pr_graph *g, double alpha, const double *target, cudaStream_t st,
+                     double *out) {
+    const int32_t n = g->n;
+    DBuf r0, part;
+    const int ctas = std::max(1, std::min(grid_for(n, 256), 1024));
+    pr_status s = dmalloc(r0, (size_t)n * sizeof(double), st);
+    if (s == PR_OK) s = dmalloc(part, 2 * (size_t)ctas * sizeof(double), st);
+    if (s == PR_OK) s = pr_learned_start(m, g, alpha, (double *)r0.p, false, st);
+    if (s != PR_OK) return s;
+    start_error_kernel<<<ctas, 256, 0, st>>>((const double *)r0.p, target, n, (double *)part.p);
+    PR_CUDA(cudaGetLastError());
+    std::vector<double> h(2 * (size_t)ctas);
+    PR_CUDA(cudaMemcpyAsync(h.data(), part.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PR_CUDA(cudaStreamSynchronize(st));
+    double el = 0.0, eu = 0.0;
+    for (int c = 0; c < ctas; c++) {
+        el += h[2 * c];
+        eu += h[2 * c + 1];
+    }
+    *out = (el > 0.0 && eu > 0.0) ? std::log(eu / el) : 0.0;
+    return PR_OK;
+}
+
 void free_mlp(pr_mlp *m) {
     if (!m) return;
     cudaFree(m->d.master);
@@ -865,6 +923,8 @@ extern "C" pr_status pr_mlp_create(const float *params, pr_mlp **out) {
     if (!m) return pr_fail(PR_ENOMEM, "host allocation failed");
     m->magic = kMlpMagic;
     m->step = 0;
+    m->gain = 0.0;
+    m->has_gain = 0;
     cudaError_t e = cudaMalloc((void **)&m->d.master, kParams * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d.m, kParams * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d.v, kParams * sizeof(float));
@@ -997,5 +1057,81 @@ extern "C" pr_status pr_mlp_train(pr_mlp *m, const pr_graph *const *graphs, cons
         for (float x : last_loss) t += x;
         *loss_out = t / (float)nsets;
     }
+    // the trained network's gain over the uniform start on its own sets
+    if (epochs > 0) {
+        double sum = 0.0;
+        for (int i = 0; i < nsets; i++) {
+            double gi = 0.0;
+            if ((s = start_gain(m, graphs[i], alphas[i], targets[i], st, &gi)) != PR_OK) return s;
+            sum += gi;
+        }
+        m->gain = sum / (double)nsets;
+        m->has_gain = 1;
+    }
+    return PR_OK;
+}
+
+extern "C" pr_status pr_mlp_gain(const pr_mlp *m, double *gain_out, int32_t *known_out) {
+    pr_clear_error();
+    if (!pr_mlp_valid(m)) return pr_fail(PR_ESTATE, "not a live pr_mlp handle");
+    if (gain_out) *gain_out = m->gain;
+    if (known_out) *known_out = m->has_gain;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_mlp_set_gain(pr_mlp *m, double gain) {
+    pr_clear_error();
+    if (!pr_mlp_valid(m)) return pr_fail(PR_ESTATE, "not a live pr_mlp handle");
+    if (!std::isfinite(gain)) return pr_fail(PR_EINVAL, "gain must be finite");
+    m->gain = gain;
+    m->has_gain = 1;
+    return PR_OK;
+}
+
+double pr_mlp_gain_value(const pr_mlp *m) { return m && m->has_gain ? m->gain : 0.0; }
+
+// Device time of the learned start on g (CUDA events): the features, once per
+// graph, and the network with its softmax, once per alpha. Measured on the
+// first request per device and graph signature and kept.
+pr_status pr_learned_cost(const pr_mlp *m, const pr_graph *g, cudaStream_t st, double *feat_us, double *net_us) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, uint64_t, int32_t>, std::pair<double, double>> cache;
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, g->signature, g->n);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *feat_us = it->second.first;
+            *net_us = it->second.second;
+            return PR_OK;
+        }
+    }
+    DBuf feat, r0;
+    pr_status s = dmalloc(feat, pr_learned_features_bytes(g), st);
+    if (s == PR_OK) s = dmalloc(r0, (size_t)g->n * sizeof(double), st);
+    if (s != PR_OK) return s;
+    cudaEvent_t e0, e1, e2;
+    PR_CUDA(cudaEventCreate(&e0));
+    PR_CUDA(cudaEventCreate(&e1));
+    PR_CUDA(cudaEventCreate(&e2));
+    struct EvG { cudaEvent_t a, b, c; ~EvG() { cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c); } } evg{e0, e1, e2};
+    // one untimed round (first launches), then the timed one
+    for (int round = 0; round < 2; round++) {
+        PR_CUDA(cudaEventRecord(e0, st));
+        if ((s = pr_learned_features(g, feat.p, st)) != PR_OK) return s;
+        PR_CUDA(cudaEventRecord(e1, st));
+        if ((s = pr_learned_start(m, g, 0.85, (double *)r0.p, true, st, feat.p)) != PR_OK) return s;
+        PR_CUDA(cudaEventRecord(e2, st));
+    }
+    PR_CUDA(cudaEventSynchronize(e2));
+    float f = 0.f, t = 0.f;
+    PR_CUDA(cudaEventElapsedTime(&f, e0, e1));
+    PR_CUDA(cudaEventElapsedTime(&t, e1, e2));
+    *feat_us = 1e3 * f;
+    *net_us = 1e3 * t;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = {*feat_us, *net_us};
     return PR_OK;
 }

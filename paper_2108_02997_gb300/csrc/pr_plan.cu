@@ -484,6 +484,16 @@ pr_status pr_plan_request(const SolveRequest &req, int group, std::vector<SubSol
     return PR_OK;
 }
 
+pr_status pr_graph_pass_model(pr_graph *g, cudaStream_t st, double *t1_us, double *lat_us, double *rho_l1) {
+    TuneEntry t;
+    pr_status s = tune(g, PR_PREC_DF64, 1, st, t);
+    if (s != PR_OK) return s;
+    *t1_us = t.us[0] > 0.0 ? t.us[0] : 0.0;
+    *lat_us = t.lat > 0.0 ? t.lat : 0.0;
+    *rho_l1 = t.decay.rho[0];
+    return PR_OK;
+}
+
 extern "C" pr_status pr_plan_columns(int32_t count, const double *iters, const double *us_per_launch, int32_t *job_of,
                                      int32_t *width_of, double *cost_out) {
     pr_clear_error();

@@ -419,10 +419,11 @@ extern "C" pr_status pr_last_solve_kernel_ms(double *gather_ms, double *update_m
     return PR_OK;
 }
 
-extern "C" pr_status pr_last_solve_columns(int32_t *columns, int32_t *mixed_columns) {
+extern "C" pr_status pr_last_solve_columns(int32_t *columns, int32_t *mixed_columns, int32_t *learned_columns) {
     std::lock_guard<std::mutex> lk(g_stats_mu);
     if (columns) *columns = g_last_stats.columns;
     if (mixed_columns) *mixed_columns = g_last_stats.mixed_columns;
+    if (learned_columns) *learned_columns = g_last_stats.learned_columns;
     return PR_OK;
 }
 
@@ -937,6 +938,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     PR_CUDA(cudaStreamSynchronize(st));
     stats.columns = ncols;
     stats.mixed_columns = mixed ? ncols : 0;
+    for (const auto &c : req.cols) stats.learned_columns += c.learned ? 1 : 0;
     req.stats = stats;
     return PR_OK;
 }

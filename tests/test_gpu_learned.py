@@ -173,3 +173,52 @@ def test_training_lowers_loss_and_warm_start_saves_iterations(B, orc, gg):
                             what=f"learned alpha {a}")
         assert lrn.iters < uni.iters, (a, lrn.iters, uni.iters)
     m.close()
+
+
+def test_auto_start_follows_its_cost_model(B, orc, gg):
+    """PR_INIT_AUTO: training measures the network's gain over the uniform
+    start; with no gain every column starts from 1/N (the uniform batch's
+    answers exactly), with an overwhelming gain every column takes the learned
+    start (the learned batch's answers exactly), and with the measured gain the
+    answers meet the accuracy bound whichever start each column got."""
+    import torch
+    sets, keep = [], []
+    for i in range(4):
+        g = gg.rmat(11 + (i % 2), 16, seed=2100 + i)
+        dg = B.Graph.from_csr(g)
+        keep.append(dg)
+        for a in (0.6, 0.85, 0.95):
+            r = torch.empty(g.n, dtype=torch.float64, device="cuda")
+            B.pr_solve(dg, a, 1e-12, 1, 1000, out=r)
+            sets.append((dg, a, r))
+    m = B.MLP(B.init_mlp_params(seed=12))
+    assert m.gain() == (0.0, False)
+    m.train(sets, epochs=80, lr=3e-3)
+    gain, known = m.gain()
+    assert known and gain > 0.0, gain
+    g = gg.rmat(14, 16, seed=2199)
+    alphas = (0.6, 0.8, 0.9)
+    with B.Graph.from_csr(g) as dg:
+        def run(init, mlp=m):
+            xs = [B.Instance(dg, a, 1e-10, 1, 500) for a in alphas]
+            B.pr_solve_batch(xs, init=init, mlp=mlp)
+            return xs, B.pr_last_solve_stats()["learned_columns"]
+        uni = [B.Instance(dg, a, 1e-10, 1, 500) for a in alphas]
+        B.pr_solve_batch(uni)
+        lrn, nl = run("learned")
+        assert nl == len(alphas)
+        m.set_gain(0.0)
+        xs, nl = run("auto")
+        assert nl == 0 and all(np.array_equal(x.out, y.out) and x.iters == y.iters for x, y in zip(xs, uni))
+        m.set_gain(50.0)
+        xs, nl = run("auto")
+        assert nl == len(alphas) and all(np.array_equal(x.out, y.out) and x.iters == y.iters for x, y in zip(xs, lrn))
+        m.set_gain(gain)
+        xs, nl = run("auto")
+        assert 0 <= nl <= len(alphas)
+        for a, x in zip(alphas, xs):
+            ref = orc.pagerank(g, a, 1e-13, 1, 10000)
+            assert_bound_parity(orc, g, a, 1e-10, 1, 500, x.out, x.iters, x.converged, ref.ranks, what=f"auto alpha {a}")
+    m.close()
+    for d in keep:
+        d.close()
