@@ -129,3 +129,42 @@ def test_learned_start_calls_reject_bad_arguments_before_device_work(L):
     assert L.pr_mlp_train(bogus, None, None, None, 1, 1, C.c_float(1e-3), None, None) == 5
     assert L.pr_mlp_destroy(None) == 0
     assert L.pr_mlp_destroy(bogus) == 5
+
+
+def _struct_fields(text, name):
+    """(type, field) pairs of a `typedef struct name { ... } name;` in a header."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct " + name + r" \{(.*?)\} " + name + ";", text, flags=re.S)
+    assert m, name
+    out = []
+    for decl in m.group(1).split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        f = re.match(r"(.*?)\**\s*\b([a-z_0-9]+)(\[\d+\])?$", decl)
+        assert f, decl
+        out.append(f.group(2))
+    return out
+
+
+def test_options_and_instance_layouts_match_the_header():
+    """The binding's pr_options and pr_instance mirror the header's structures
+    field by field and byte by byte (both compilers lay them out the same)."""
+    from paper_2108_02997_gb300 import binding as Bd
+    text = (ROOT / "include" / "pagerank.h").read_text()
+    for name, cls in (("pr_options", Bd.pr_options), ("pr_instance", Bd.pr_instance)):
+        assert _struct_fields(text, name) == [f[0] for f in cls._fields_], name
+    assert C.sizeof(Bd.pr_instance) == 80 and C.sizeof(Bd.pr_options) % 8 == 0
+
+
+def test_header_describes_the_workspace_pool_and_its_release():
+    """The header's device-memory convention names what the library keeps
+    between calls and how to return it (the workspace pool, pr_workspace_info,
+    pr_workspace_release), and the no-alloc entry point's limits."""
+    text = (ROOT / "include" / "pagerank.h").read_text()
+    conv = text[:text.index("#ifndef PAGERANK_H")]
+    assert "stream-ordered" in conv and "4 GiB" in conv
+    assert "pr_workspace_info" in conv and "pr_workspace_release" in conv
+    assert "cudaMalloc with cudaMalloc" not in conv and "releases it\n *     before returning" not in conv
+    noalloc = text[text.index("pr_solve_noalloc —"):text.index("pr_status pr_solve_noalloc(")]
+    assert "captured" in noalloc and "40 MiB" in noalloc and "device memory of that device" in noalloc
