@@ -43,9 +43,11 @@ void free_tables(pr_graph *g) {
         cudaFree(t.d_slot_base);
         t = TileTable();
     }
-    cudaFree(g->hub_table.d_tiles);
-    cudaFree(g->hub_table.d_slot_base);
-    g->hub_table = TileTable();
+    for (auto &t : g->hub_tables) {
+        cudaFree(t.d_tiles);
+        cudaFree(t.d_slot_base);
+        t = TileTable();
+    }
 }
 
 void free_graph(pr_graph *g) {
@@ -285,12 +287,13 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     return PR_OK;
 }
 
-// The one-column gather kernel with a shared-memory hub table stages fewer
-// values per warp (kHubTile), so its rows tiles are smaller.
-pr_status pr_graph_hub_tiles(pr_graph *g, const TileTable **out) {
-    TileTable &t = g->hub_table;
+// The hub gather kernel (one or two columns) stages hub_tile_edges(W)
+// vectors per warp, so its rows tiles have a size of their own.
+pr_status pr_graph_hub_tiles(pr_graph *g, int W, const TileTable **out) {
+    if (W != 1 && W != 2) return pr_fail(PR_EINVAL, "internal: hub tiles for one or two columns");
+    TileTable &t = g->hub_tables[W - 1];
     if (!t.d_tiles) {
-        pr_status s = build_tile_table(g, 1, kHubTile, tile_rows(1), chunk_edges(1), t);
+        pr_status s = build_tile_table(g, W, hub_tile_edges(W), tile_rows(1), chunk_edges(1), t);
         if (s != PR_OK) return s;
     }
     *out = &t;

@@ -25,7 +25,7 @@ struct pr_graph {
     int32_t *d_inv = nullptr;        // caller -> relabelled
     std::vector<ClassRange> classes; // in-degree classes in relabelled order
     TileTable tables[6];             // W = 1, 2, 4, 8, 16, 32
-    TileTable hub_table;             // W = 1, tiles of the hub gather kernel
+    TileTable hub_tables[2];         // W = 1, 2: tiles of the hub gather kernel
     uint64_t signature = 0;          // hash of n, nnz and the in-degree class layout
 };
 constexpr uint32_t kGraphMagic = 0x50524731u;   // "PRG1"
@@ -50,7 +50,7 @@ pr_status pr_cuda_fail(cudaError_t e, const char *what);
 // ------------------------------------------------------------------ internals
 int w_index(int W);   // 1,2,4,..,32 -> 0..5
 pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out);
-pr_status pr_graph_hub_tiles(pr_graph *g, const TileTable **out);
+pr_status pr_graph_hub_tiles(pr_graph *g, int W, const TileTable **out);
 bool pr_graph_valid(const pr_graph *g);
 
 // Solve driver (pr_solve.cu)

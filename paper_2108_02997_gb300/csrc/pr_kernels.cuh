@@ -903,41 +903,56 @@ __global__ void __launch_bounds__(kBlock, kUpdateMinBlocks) pr_update_kernel(Job
     finish_pass<V, W>(jobs, job, glob, acc, local, kPassIterate);
 }
 
-// ---------------------------------------------------------------- the hub gather kernel (one column, split passes)
-// The gather half of a one-column pass (row sums only, like the gather form
-// of pr_iter_kernel) with one CTA of kHubBlock threads per SM. The CTA first
-// copies the contributions of vertices [0, hub_n) into shared memory: after
-// the relabelling these are the highest in-/out-degree classes, the sources
-// most often gathered (R-MAT scale 22: the first 16,384 ids originate 40 % of
-// the in-edges). A gather of a source below hub_n then reads shared memory,
-// the others the global contribution array through L1/L2, whose random-sector
-// rate bounds the kernel.
-template <typename V>
-__device__ __forceinline__ V ld_gather(const V *p) {
-    return __ldg(p);
-}
-template <>
-__device__ __forceinline__ df64 ld_gather<df64>(const df64 *p) {
-    const float2 f = __ldg(reinterpret_cast<const float2 *>(p));
-    return {f.x, f.y};
+// ---------------------------------------------------------------- the hub gather kernel (split passes)
+// The gather half of a pass (row sums only) for jobs of W columns whose W
+// values of a vertex fit one vector load (W x value size <= 16 bytes: one
+// column, or two df64/FP64 columns, or up to four FP32 columns), with one CTA
+// of kHubBlock threads per SM. The CTA first copies the contribution vectors
+// of vertices [0, hub_n) into shared memory: after the relabelling these are
+// the highest in-/out-degree classes, the sources most often gathered (R-MAT
+// scale 22: the first 12,288 ids originate 37 % of the in-edges). A gather of
+// a source below hub_n then reads shared memory, the others the global
+// contribution array through L1/L2, whose random-sector rate bounds the
+// kernel; a vector of W columns costs one sector like a single value, so the
+// W columns share the index stream and the random reads.
+template <typename V, int W>
+__device__ __forceinline__ VecV<V, W> ld_gather_vec(const V *p) {
+    static_assert(sizeof(VecV<V, W>) == 4 || sizeof(VecV<V, W>) == 8 || sizeof(VecV<V, W>) == 16, "vector size");
+    VecV<V, W> r;
+    if constexpr (sizeof(VecV<V, W>) == 16) {
+        const float4 f = __ldg(reinterpret_cast<const float4 *>(p));
+        memcpy(&r, &f, 16);
+    } else if constexpr (sizeof(VecV<V, W>) == 8) {
+        const float2 f = __ldg(reinterpret_cast<const float2 *>(p));
+        memcpy(&r, &f, 8);
+    } else {
+        const float f = __ldg(reinterpret_cast<const float *>(p));
+        memcpy(&r, &f, 4);
+    }
+    return r;
 }
 
-template <typename V>
+template <typename V, int W>
 __global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
     using N = Num<V>;
-    constexpr int PER = kHubTile / 32;       // staged gathers per lane (rows tiles)
+    using VV = VecV<V, W>;
+    constexpr int TV = hub_tile_edges(W);   // staged vectors per warp (rows tiles)
+    constexpr int PER = TV / 32;            // staged gathers per lane
     constexpr int TR = tile_rows(1);
-    constexpr int kOffRegs = TR / 32 + 1;    // row offsets of a rows tile, in registers
-    constexpr int CPER = kHubChunkPer;       // gathers per lane in flight (chunk tiles)
+    constexpr int kOffRegs = TR / 32 + 1;   // row offsets of a rows tile, in registers
+    constexpr int CPER = kHubChunkPer / W;  // vector gathers per lane in flight (chunk tiles)
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     JobDev &job = jobs[cta_job[blockIdx.x]];
-    const ColState &cs = job.cols[0];
-    // CTA-uniform: nothing to gather when the job or its column has stopped
-    if (!job.alive || !cs.active || *(volatile int32_t *)&glob->error) return;
+    // CTA-uniform: nothing to gather when the job or all its columns have stopped
+    bool any_active = job.cols[0].active != 0;
+    if constexpr (W > 1)
+        for (int c = 1; c < job.ncols; c++) any_active |= job.cols[c].active != 0;
+    if (!job.alive || !any_active || *(volatile int32_t *)&glob->error) return;
     const int local = blockIdx.x - job.gcta_begin;
     const int cta_count = job.gcta_count;
-    const V *__restrict__ c_prev = reinterpret_cast<const V *>(job.contrib[cs.cur]);
+    // the contributions of the active columns, vertex-major (W values per vertex)
+    const V *__restrict__ c_prev = reinterpret_cast<const V *>(job.contrib[W == 1 ? job.cols[0].cur : job.cur]);
     V *__restrict__ rowsum = reinterpret_cast<V *>(job.rowsum);
     const int32_t *__restrict__ src = job.src;
     const int32_t *__restrict__ off = job.off;
@@ -946,18 +961,32 @@ __global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub_kernel(JobDev *job
     V *chunk_part = reinterpret_cast<V *>(job.chunk_part);
     uint32_t *chunk_cnt = job.chunk_cnt;
     const int ntiles = job.ntiles;
-    // at most what the launch's shared memory holds for this value type
-    const int hub_n = min(job.hub_n, kHubBytes / (int)sizeof(V));
+    // at most what the launch's shared memory holds for this vector type
+    const int hub_n = min(job.hub_n, kHubBytes / (int)sizeof(VV));
     extern __shared__ __align__(16) unsigned char pr_hub_smem[];
-    V *s_vals = reinterpret_cast<V *>(pr_hub_smem) + warp * kHubTile;   // this warp's staged values
-    V *s_hub = reinterpret_cast<V *>(pr_hub_smem) + kHubWarps * kHubTile;
-    for (int i = tid; i < hub_n; i += kHubBlock) s_hub[i] = ld_cg_v<V>(c_prev + i);
+    VV *s_vals = reinterpret_cast<VV *>(pr_hub_smem) + warp * TV;   // this warp's staged vectors
+    VV *s_hub = reinterpret_cast<VV *>(pr_hub_smem) + kHubWarps * TV;
+    for (int i = tid; i < hub_n; i += kHubBlock) {
+        VV x;
+#pragma unroll
+        for (int j = 0; j < W; j++) x.v[j] = ld_cg_v<V>(c_prev + (size_t)i * W + j);
+        s_hub[i] = x;
+    }
     __syncthreads();
-    auto gather = [&](int32_t u) -> V { return u < hub_n ? s_hub[u] : ld_gather<V>(c_prev + u); };
+    auto gather = [&](int32_t u) -> VV {
+        if constexpr (W == 1) return u < hub_n ? s_hub[u] : ld_gather_vec<V, W>(c_prev + u);
+        else return u < hub_n ? s_hub[u] : ld_gather_vec<V, W>(c_prev + (size_t)u * W);
+    };
+    auto zero_vec = [&]() -> VV {
+        VV z;
+#pragma unroll
+        for (int j = 0; j < W; j++) z.v[j] = N::zero();
+        return z;
+    };
 
     // rows tile: indices and row offsets requested first, PER independent
-    // gathers per lane staged in shared memory, then lane groups of 2^glog
-    // lanes add each row's values in a fixed order
+    // vector gathers per lane staged in shared memory, then lane groups of
+    // 2^glog lanes add each row's vectors in a fixed order
     auto rows_tile = [&](const Tile &T) {
         const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
         int32_t u[PER];
@@ -974,9 +1003,9 @@ __global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub_kernel(JobDev *job
             o[j] = i <= nr ? off[T.r0 + i] - T.e0 : 0;
         }
         {
-            V x[PER];
+            VV x[PER];
 #pragma unroll
-            for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather(u[k]) : N::zero();
+            for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather(u[k]) : zero_vec();
 #pragma unroll
             for (int k = 0; k < PER; k++)
                 if (u[k] >= 0) s_vals[lane + 32 * k] = x[k];
@@ -1000,27 +1029,36 @@ __global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub_kernel(JobDev *job
             }
             const int32_t la = __shfl_sync(0xffffffffu, oa, r & 31), lb = __shfl_sync(0xffffffffu, ob, r & 31);
             const int32_t ha = __shfl_sync(0xffffffffu, oa, (r + 1) & 31), hb = __shfl_sync(0xffffffffu, ob, (r + 1) & 31);
-            EdgeSum<V> sum;
-            sum.init();
+            EdgeSum<V> sum[W];
+#pragma unroll
+            for (int j = 0; j < W; j++) sum[j].init();
             if (valid) {
                 const int lo = (r >> 5) == j0 ? la : lb, hi = ((r + 1) >> 5) == j0 ? ha : hb;
-                for (int e = lo + es; e < hi; e += g) sum.add(s_vals[e]);
+                for (int e = lo + es; e < hi; e += g) {
+                    const VV y = s_vals[e];
+#pragma unroll
+                    for (int j = 0; j < W; j++) sum[j].add(y.v[j]);
+                }
             }
-            V sv = sum.get();
-            for (int m = 1; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-            if (valid && es == 0) rowsum[T.r0 + r] = sv;
+#pragma unroll
+            for (int j = 0; j < W; j++) {
+                V sv = sum[j].get();
+                for (int m = 1; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                if (valid && es == 0) rowsum[(size_t)(T.r0 + r) * W + j] = sv;
+            }
         }
         __syncwarp();
     };
-    // chunk of a long row: the warp strides over the chunk, CPER gathers per
-    // lane in flight and the next step's indices requested meanwhile; lane l
-    // adds in-edges l, l + 32, ... in order; the last chunk of a row to finish
-    // adds the chunk sums in chunk order
+    // chunk of a long row: the warp strides over the chunk, CPER vector
+    // gathers per lane in flight and the next step's indices requested
+    // meanwhile; lane l adds in-edges l, l + 32, ... in order; the last chunk
+    // of a row to finish adds the chunk sums in chunk order
     auto chunk_tile = [&](const Tile &T) {
         const int32_t v = T.r0;
         const int nv = T.e1 - T.e0;
-        EdgeSum<V> sum;
-        sum.init();
+        EdgeSum<V> sum[W];
+#pragma unroll
+        for (int j = 0; j < W; j++) sum[j].init();
         int32_t u[CPER];
 #pragma unroll
         for (int k = 0; k < CPER; k++) {
@@ -1028,9 +1066,9 @@ __global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub_kernel(JobDev *job
             u[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
         }
         for (int base = lane; base < nv; base += 32 * CPER) {
-            V x[CPER];
+            VV x[CPER];
 #pragma unroll
-            for (int k = 0; k < CPER; k++) x[k] = u[k] >= 0 ? gather(u[k]) : N::zero();
+            for (int k = 0; k < CPER; k++) x[k] = u[k] >= 0 ? gather(u[k]) : zero_vec();
             int32_t un[CPER];
 #pragma unroll
             for (int k = 0; k < CPER; k++) {
@@ -1039,17 +1077,30 @@ __global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub_kernel(JobDev *job
             }
 #pragma unroll
             for (int k = 0; k < CPER; k++)
-                if (u[k] >= 0) sum.add(x[k]);
+                if (u[k] >= 0) {
+#pragma unroll
+                    for (int j = 0; j < W; j++) sum[j].add(x[k].v[j]);
+                }
 #pragma unroll
             for (int k = 0; k < CPER; k++) u[k] = un[k];
         }
-        V sv = sum.get();
-        for (int m = 1; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+        V sv[W];
+#pragma unroll
+        for (int j = 0; j < W; j++) {
+            sv[j] = sum[j].get();
+            for (int m = 1; m < 32; m <<= 1) sv[j] = N::add_pos(sv[j], N::shfl_xor(sv[j], m));
+        }
         if (T.slot < 0) {
-            if (lane == 0) rowsum[v] = sv;
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < W; j++) rowsum[(size_t)v * W + j] = sv[j];
+            }
         } else {
             const int32_t base = slot_base[T.slot];
-            if (lane == 0) chunk_part[base + T.k] = sv;
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < W; j++) chunk_part[(size_t)(base + T.k) * W + j] = sv[j];
+            }
             __threadfence();
             __syncwarp();
             int last = 0;
@@ -1057,13 +1108,15 @@ __global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub_kernel(JobDev *job
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
                 __threadfence();
-                V t = N::zero();
-                for (int32_t q = lane; q < T.nch; q += 32) t = N::add_pos(t, ld_cg_v<V>(chunk_part + base + q));
-                for (int m = 1; m < 32; m <<= 1) t = N::add_pos(t, N::shfl_xor(t, m));
-                if (lane == 0) {
-                    rowsum[v] = t;
-                    chunk_cnt[T.slot] = 0;
+#pragma unroll
+                for (int j = 0; j < W; j++) {
+                    V t = N::zero();
+                    for (int32_t q = lane; q < T.nch; q += 32)
+                        t = N::add_pos(t, ld_cg_v<V>(chunk_part + (size_t)(base + q) * W + j));
+                    for (int m = 1; m < 32; m <<= 1) t = N::add_pos(t, N::shfl_xor(t, m));
+                    if (lane == 0) rowsum[(size_t)v * W + j] = t;
                 }
+                if (lane == 0) chunk_cnt[T.slot] = 0;
             }
             __syncwarp();
         }

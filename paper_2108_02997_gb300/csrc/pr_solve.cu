@@ -174,18 +174,24 @@ void *update_ptr(int W) {
         default: return (void *)pr_update_kernel<V, 32>;
     }
 }
-// The one-column gather kernel with the shared-memory hub table (split passes).
-bool hub_gather(int W) { return kHubGather && W == 1; }
-void *hub_gather_kernel_for(int prec) {
+// Split passes of one or two columns gather with the hub kernel (a vertex's
+// values fit one 16-byte load in every value type, so both phases of mixed
+// precision use it alike); wider jobs with the multi-column gather kernel.
+bool hub_gather(int W) { return kHubGather && hub_width_ok(W, 8); }
+template <typename V>
+void *hub_ptr(int W) {
+    return W == 1 ? (void *)pr_gather_hub_kernel<V, 1> : (void *)pr_gather_hub_kernel<V, 2>;
+}
+void *hub_gather_kernel_for(int prec, int W) {
     switch (prec) {
-        case PR_PREC_FP64: return (void *)pr_gather_hub_kernel<double>;
-        case PR_PREC_FP32: return (void *)pr_gather_hub_kernel<float>;
-        default: return (void *)pr_gather_hub_kernel<df64>;
+        case PR_PREC_FP64: return hub_ptr<double>(W);
+        case PR_PREC_FP32: return hub_ptr<float>(W);
+        default: return hub_ptr<df64>(W);
     }
 }
 int gather_block(int W) { return hub_gather(W) ? kHubBlock : kBlock; }
 void *gather_kernel_for(int prec, int W) {
-    if (hub_gather(W)) return hub_gather_kernel_for(prec);
+    if (hub_gather(W)) return hub_gather_kernel_for(prec, W);
     switch (prec) {
         case PR_PREC_FP64: return gather_ptr<double>(W);
         case PR_PREC_FP32: return gather_ptr<float>(W);
@@ -267,7 +273,7 @@ pr_status setup_split(int prec, int W, int *occ_gather, int *occ_update) {
     auto it = done.find(key);
     if (it == done.end()) {
         PR_CUDA(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        pr_status s = set_carveout(kg, smem, W == 1, gather_block(W));
+        pr_status s = set_carveout(kg, smem, W == 1 || hub_gather(W), gather_block(W));
         if (s != PR_OK) return s;
         const std::pair<int, int> occ{resident_ctas(kg, smem, gather_block(W)),
                                       resident_ctas(update_kernel_for(prec, W), 0)};
@@ -356,13 +362,12 @@ size_t pr_tile_smem_bytes(int prec, int W) {
     if (W == 1) return 0;
     return (size_t)kWarps * vec_warp_bytes(vbytes, W, false);
 }
-// The hub gather kernel's contributions held in shared memory (values), at most.
-int hub_capacity(int prec) { return kHubBytes / (prec == PR_PREC_FP32 ? 4 : 8); }
 // The gather-only kernel's: no previous ranks or out-degrees staged; the hub
-// gather kernel's: every warp's staged values, then the hub table.
+// gather kernel's: every warp's staged vectors, then the hub table (at most
+// kHubBytes of vectors).
 size_t gather_smem_bytes(int prec, int W) {
     const int vbytes = prec == PR_PREC_FP32 ? 4 : 8;
-    if (hub_gather(W)) return (size_t)kHubWarps * kHubTile * vbytes + (size_t)hub_capacity(prec) * vbytes;
+    if (hub_gather(W)) return (size_t)kHubWarps * hub_tile_edges(W) * W * vbytes + (size_t)kHubBytes;
     if (W == 1) return 0;
     return (size_t)kWarps * vec_warp_bytes(vbytes, W, true);
 }
@@ -660,7 +665,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     const bool hub = split && hub_gather(W);
     double total_work = 0.0;
     for (auto &j : jobs) {
-        s = hub ? pr_graph_hub_tiles(const_cast<pr_graph *>(j.g), &j.tt)
+        s = hub ? pr_graph_hub_tiles(const_cast<pr_graph *>(j.g), W, &j.tt)
                 : pr_graph_tiles(const_cast<pr_graph *>(j.g), W, &j.tt);
         if (s != PR_OK) return s;
         total_work += std::max(j.tt->work, 1.0);
