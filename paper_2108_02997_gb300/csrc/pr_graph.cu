@@ -287,11 +287,11 @@ pr_status pr_graph_tiles(pr_graph *g, int W, const TileTable **out) {
     return PR_OK;
 }
 
-// The hub gather kernel (one or two columns) stages hub_tile_edges(W)
+// The hub gather kernel (one, two or four columns) stages hub_tile_edges(W)
 // vectors per warp, so its rows tiles have a size of their own.
 pr_status pr_graph_hub_tiles(pr_graph *g, int W, const TileTable **out) {
-    if (W != 1 && W != 2) return pr_fail(PR_EINVAL, "internal: hub tiles for one or two columns");
-    TileTable &t = g->hub_tables[W - 1];
+    if (W != 1 && W != 2 && W != 4) return pr_fail(PR_EINVAL, "internal: hub tiles for one, two or four columns");
+    TileTable &t = g->hub_tables[w_index(W)];
     if (!t.d_tiles) {
         pr_status s = build_tile_table(g, W, hub_tile_edges(W), tile_rows(1), chunk_edges(1), t);
         if (s != PR_OK) return s;

@@ -25,7 +25,7 @@ struct pr_graph {
     int32_t *d_inv = nullptr;        // caller -> relabelled
     std::vector<ClassRange> classes; // in-degree classes in relabelled order
     TileTable tables[6];             // W = 1, 2, 4, 8, 16, 32
-    TileTable hub_tables[2];         // W = 1, 2: tiles of the hub gather kernel
+    TileTable hub_tables[3];         // W = 1, 2, 4: tiles of the hub gather kernel
     uint64_t signature = 0;          // hash of n, nnz and the in-degree class layout
 };
 constexpr uint32_t kGraphMagic = 0x50524731u;   // "PRG1"

@@ -128,11 +128,14 @@ static_assert(kHubTile % 32 == 0 && kHubTile <= 256, "hub tiles hold 32..256 val
 #define PR_HUB_TILE_VECTORS 128
 #endif
 // In-edges per rows tile of the hub gather kernel: kHubTile for one column,
-// PR_HUB_TILE_VECTORS for several (their staged vectors are wider).
-__host__ __device__ constexpr int hub_tile_edges(int W) { return W == 1 ? kHubTile : PR_HUB_TILE_VECTORS; }
-// Jobs of W columns gather with the hub kernel when a vertex's W values fit
-// one vector load of at most 16 bytes.
-__host__ __device__ constexpr bool hub_width_ok(int W, int vbytes) { return (W == 1 || W == 2 || W == 4) && W * vbytes <= 16; }
+// PR_HUB_TILE_VECTORS for two, half that for four (their staged vectors are
+// wider).
+__host__ __device__ constexpr int hub_tile_edges(int W) {
+    return W == 1 ? kHubTile : (W == 2 ? PR_HUB_TILE_VECTORS : PR_HUB_TILE_VECTORS / 2);
+}
+// Jobs of W columns gather with the hub kernel when a vertex's W values fill at
+// most one 32-byte sector.
+__host__ __device__ constexpr bool hub_width_ok(int W, int vbytes) { return (W == 1 || W == 2 || W == 4) && W * vbytes <= 32; }
 constexpr int kMinBlocks = PR_MIN_BLOCKS;
 constexpr int kVecTileEdges = 256;
 __host__ __device__ constexpr int tile_edges(int W) { return W == 1 ? kTileValues : kVecTileEdges; }

@@ -905,8 +905,8 @@ __global__ void __launch_bounds__(kBlock, kUpdateMinBlocks) pr_update_kernel(Job
 
 // ---------------------------------------------------------------- the hub gather kernel (split passes)
 // The gather half of a pass (row sums only) for jobs of W columns whose W
-// values of a vertex fit one vector load (W x value size <= 16 bytes: one
-// column, or two df64/FP64 columns, or up to four FP32 columns), with one CTA
+// values of a vertex fill at most one 32-byte L2 sector (one, two or four
+// columns; four df64/FP64 columns are read with two 16-byte loads), with one CTA
 // of kHubBlock threads per SM. The CTA first copies the contribution vectors
 // of vertices [0, hub_n) into shared memory: after the relabelling these are
 // the highest in-/out-degree classes, the sources most often gathered (R-MAT
@@ -917,9 +917,16 @@ __global__ void __launch_bounds__(kBlock, kUpdateMinBlocks) pr_update_kernel(Job
 // W columns share the index stream and the random reads.
 template <typename V, int W>
 __device__ __forceinline__ VecV<V, W> ld_gather_vec(const V *p) {
-    static_assert(sizeof(VecV<V, W>) == 4 || sizeof(VecV<V, W>) == 8 || sizeof(VecV<V, W>) == 16, "vector size");
+    static_assert(sizeof(VecV<V, W>) == 4 || sizeof(VecV<V, W>) == 8 || sizeof(VecV<V, W>) == 16 ||
+                      sizeof(VecV<V, W>) == 32, "vector size");
     VecV<V, W> r;
-    if constexpr (sizeof(VecV<V, W>) == 16) {
+    if constexpr (sizeof(VecV<V, W>) == 32) {
+        // one 32-byte sector: two 16-byte loads of the same sector
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        memcpy(&r, &a, 16);
+        memcpy(reinterpret_cast<unsigned char *>(&r) + 16, &b, 16);
+    } else if constexpr (sizeof(VecV<V, W>) == 16) {
         const float4 f = __ldg(reinterpret_cast<const float4 *>(p));
         memcpy(&r, &f, 16);
     } else if constexpr (sizeof(VecV<V, W>) == 8) {
@@ -969,7 +976,7 @@ __global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub_kernel(JobDev *job
     for (int i = tid; i < hub_n; i += kHubBlock) {
         VV x;
 #pragma unroll
-        for (int j = 0; j < W; j++) x.v[j] = ld_cg_v<V>(c_prev + (size_t)i * W + j);
+        for (int j = 0; j < W; j++) x.v[j] = ld_cg_v<V>(c_prev + i * W + j);
         s_hub[i] = x;
     }
     __syncthreads();

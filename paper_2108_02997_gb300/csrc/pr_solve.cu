@@ -174,13 +174,18 @@ void *update_ptr(int W) {
         default: return (void *)pr_update_kernel<V, 32>;
     }
 }
-// Split passes of one or two columns gather with the hub kernel (a vertex's
-// values fit one 16-byte load in every value type, so both phases of mixed
-// precision use it alike); wider jobs with the multi-column gather kernel.
+// Split passes of one, two or four columns gather with the hub kernel (a
+// vertex's values fill at most one 32-byte sector in every value type, so both
+// phases of mixed precision use it alike); wider jobs with the multi-column
+// gather kernel.
 bool hub_gather(int W) { return kHubGather && hub_width_ok(W, 8); }
 template <typename V>
 void *hub_ptr(int W) {
-    return W == 1 ? (void *)pr_gather_hub_kernel<V, 1> : (void *)pr_gather_hub_kernel<V, 2>;
+    switch (W) {
+        case 1: return (void *)pr_gather_hub_kernel<V, 1>;
+        case 2: return (void *)pr_gather_hub_kernel<V, 2>;
+        default: return (void *)pr_gather_hub_kernel<V, 4>;
+    }
 }
 void *hub_gather_kernel_for(int prec, int W) {
     switch (prec) {

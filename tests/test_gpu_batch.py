@@ -346,15 +346,16 @@ def test_workspace_pool_info_and_release(B, er):
         assert B.workspace_info()[0] > 0
 
 
+@pytest.mark.parametrize("width", [2, 4])
 @pytest.mark.parametrize("precision", ["df64", "fp64", "fp32"])
-def test_two_column_split_passes(B, orc, gg, precision):
-    """Jobs of two columns with split passes (the hub gather kernel reading
-    both columns of a source with one vector load) on a graph with rows of
-    every tile kind: short rows, rows cut into one chunk and rows cut into
-    several (5,000 and 9,000 in-edges)."""
+def test_hub_kernel_several_columns(B, orc, gg, precision, width):
+    """Jobs of two and four columns with split passes (the hub gather kernel
+    reading all columns of a source with one vector load, two for four FP64
+    columns) on a graph with rows of every tile kind: short rows, rows cut
+    into one chunk and rows cut into several (5,000 and 9,000 in-edges)."""
     from tests.test_gpu_parity import adversarial
     g = adversarial(gg)["thresholds"]
-    alphas = (0.7, 0.9)
+    alphas = (0.7, 0.9) if width == 2 else (0.6, 0.7, 0.85, 0.95)
     with B.Graph.from_csr(g) as dg:
         xs = [B.Instance(dg, a, 1e-10 if precision != "fp32" else 1e-5, 1, 500) for a in alphas]
         B.pr_solve_batch(xs, group="pack", kernels="split", precision=precision)
@@ -362,7 +363,7 @@ def test_two_column_split_passes(B, orc, gg, precision):
             if precision == "fp32":
                 star = orc.pagerank(g, a, 1e-13, 1, 10000)
                 assert_bound_parity(orc, g, a, 1e-5, 1, 500, x.out, x.iters, x.converged, star.ranks,
-                                    what=f"fp32 W2 alpha {a}")
+                                    what=f"fp32 W{width} alpha {a}")
             else:
                 ref = orc.pagerank(g, a, 1e-10, 1, 500, history=True)
-                assert_fp64_parity(x.out, x.iters, x.err, ref, 1e-10, 1, f"{precision} W2 alpha {a}")
+                assert_fp64_parity(x.out, x.iters, x.err, ref, 1e-10, 1, f"{precision} W{width} alpha {a}")
