@@ -63,7 +63,7 @@ def kernel_traffic_ratio():
     to the value recorded there (else None)."""
     import hashlib
     import re
-    prof = ROOT / "profiles" / "pr_gather_hub_kernel_rmat-s21.md"
+    prof = ROOT / "profiles" / "pr_gather_hub1_kernel_rmat-s21.md"
     if not prof.exists():
         return None, None
     text = prof.read_text()
@@ -74,7 +74,7 @@ def kernel_traffic_ratio():
     if not (m_hash and m_ratio) or h.hexdigest()[:16] != m_hash.group(1):
         return None, None
     return float(m_ratio.group(1)), ("scaled: one ncu capture at R-MAT scale 21 "
-                                     "(profiles/pr_gather_hub_kernel_rmat-s21.md), traffic/algorithmic bytes "
+                                     "(profiles/pr_gather_hub1_kernel_rmat-s21.md), traffic/algorithmic bytes "
                                      "times this launch's algorithmic bytes")
 
 
@@ -536,7 +536,7 @@ def roofline_s22(B, gg, torch, sptr, rank, have):
     return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "ceiling": ceiling,
             "traffic": ratio * b_gather if ratio else None, "traffic_source": tsrc,
-            "kernel": "pr_gather_hub_kernel<df64> (gather half of a one-column pass)",
+            "kernel": "pr_gather_hub1_kernel<df64> (gather half of a one-column pass)",
             "workload": "rmat-s22 ef16 seed22 (N 4,194,304, E %d), alpha .85, tau {1e-6,1e-10} x {L1,L2,Linf}, df64"
                         % g.nnz,
             "avg_launch_us": gather_us, "algorithmic_bytes_per_launch": b_gather, "launches": passes,

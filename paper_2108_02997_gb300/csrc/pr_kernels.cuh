@@ -906,7 +906,8 @@ __global__ void __launch_bounds__(kBlock, kUpdateMinBlocks) pr_update_kernel(Job
 // ---------------------------------------------------------------- the hub gather kernel (split passes)
 // The gather half of a pass (row sums only) for jobs of W columns whose W
 // values of a vertex fill at most one 32-byte L2 sector (one, two or four
-// columns; four df64/FP64 columns are read with two 16-byte loads), with one CTA
+// columns; four df64/FP64 columns are read with two 16-byte loads; one column
+// runs pr_gather_hub1_kernel below, the same code for a single value), with one CTA
 // of kHubBlock threads per SM. The CTA first copies the contribution vectors
 // of vertices [0, hub_n) into shared memory: after the relabelling these are
 // the highest in-/out-degree classes, the sources most often gathered (R-MAT
@@ -1124,6 +1125,177 @@ __global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub_kernel(JobDev *job
                     if (lane == 0) rowsum[(size_t)v * W + j] = t;
                 }
                 if (lane == 0) chunk_cnt[T.slot] = 0;
+            }
+            __syncwarp();
+        }
+    };
+
+    // the next tile's descriptor is requested while this tile is worked on
+    const int wstride = cta_count * kHubWarps;
+    Tile T_next{};
+    if (local * kHubWarps + warp < ntiles) T_next = load_tile(tiles + local * kHubWarps + warp);
+    for (int t = local * kHubWarps + warp; t < ntiles; t += wstride) {
+        const Tile T = T_next;
+        if (t + wstride < ntiles) T_next = load_tile(tiles + t + wstride);
+        if (T.glog >= 0) rows_tile(T);
+        else chunk_tile(T);
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ V ld_gather(const V *p) {
+    return __ldg(p);
+}
+template <>
+__device__ __forceinline__ df64 ld_gather<df64>(const df64 *p) {
+    const float2 f = __ldg(reinterpret_cast<const float2 *>(p));
+    return {f.x, f.y};
+}
+
+// One column: the same kernel written for a single value per in-edge (its
+// register allocation is tighter than the vector form's: measured 1-2 % faster).
+template <typename V>
+__global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub1_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
+    using N = Num<V>;
+    constexpr int PER = kHubTile / 32;       // staged gathers per lane (rows tiles)
+    constexpr int TR = tile_rows(1);
+    constexpr int kOffRegs = TR / 32 + 1;    // row offsets of a rows tile, in registers
+    constexpr int CPER = kHubChunkPer;       // gathers per lane in flight (chunk tiles)
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    JobDev &job = jobs[cta_job[blockIdx.x]];
+    const ColState &cs = job.cols[0];
+    // CTA-uniform: nothing to gather when the job or its column has stopped
+    if (!job.alive || !cs.active || *(volatile int32_t *)&glob->error) return;
+    const int local = blockIdx.x - job.gcta_begin;
+    const int cta_count = job.gcta_count;
+    const V *__restrict__ c_prev = reinterpret_cast<const V *>(job.contrib[cs.cur]);
+    V *__restrict__ rowsum = reinterpret_cast<V *>(job.rowsum);
+    const int32_t *__restrict__ src = job.src;
+    const int32_t *__restrict__ off = job.off;
+    const Tile *__restrict__ tiles = job.tiles;
+    const int32_t *__restrict__ slot_base = job.slot_base;
+    V *chunk_part = reinterpret_cast<V *>(job.chunk_part);
+    uint32_t *chunk_cnt = job.chunk_cnt;
+    const int ntiles = job.ntiles;
+    // at most what the launch's shared memory holds for this value type
+    const int hub_n = min(job.hub_n, kHubBytes / (int)sizeof(V));
+    extern __shared__ __align__(16) unsigned char pr_hub_smem[];
+    V *s_vals = reinterpret_cast<V *>(pr_hub_smem) + warp * kHubTile;   // this warp's staged values
+    V *s_hub = reinterpret_cast<V *>(pr_hub_smem) + kHubWarps * kHubTile;
+    for (int i = tid; i < hub_n; i += kHubBlock) s_hub[i] = ld_cg_v<V>(c_prev + i);
+    __syncthreads();
+    auto gather = [&](int32_t u) -> V { return u < hub_n ? s_hub[u] : ld_gather<V>(c_prev + u); };
+
+    // rows tile: indices and row offsets requested first, PER independent
+    // gathers per lane staged in shared memory, then lane groups of 2^glog
+    // lanes add each row's values in a fixed order
+    auto rows_tile = [&](const Tile &T) {
+        const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
+        int32_t u[PER];
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int i = lane + 32 * k;
+            u[k] = i < ne ? ld_idx(src + T.e0 + i) : -1;
+        }
+        // row offsets relative to e0: lane l holds rows l, l + 32, ...
+        int32_t o[kOffRegs];
+#pragma unroll
+        for (int j = 0; j < kOffRegs; j++) {
+            const int i = lane + 32 * j;
+            o[j] = i <= nr ? off[T.r0 + i] - T.e0 : 0;
+        }
+        {
+            V x[PER];
+#pragma unroll
+            for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather(u[k]) : N::zero();
+#pragma unroll
+            for (int k = 0; k < PER; k++)
+                if (u[k] >= 0) s_vals[lane + 32 * k] = x[k];
+        }
+        __syncwarp();
+        const int g = 1 << T.glog;
+        const int es = lane & (g - 1);
+        const int rpp = 32 >> T.glog;
+        for (int rb = 0; rb < nr; rb += rpp) {
+            const int r = rb + (lane >> T.glog);
+            const bool valid = r < nr;
+            // rows r and r + 1 lie in [rb, rb + 32]: registers j0 and j0 + 1 of their lanes
+            const int j0 = rb >> 5;
+            int32_t oa = o[0], ob = o[kOffRegs > 1 ? 1 : 0];
+#pragma unroll
+            for (int j = 1; j + 1 < kOffRegs; j++) {
+                if (j0 == j) {
+                    oa = o[j];
+                    ob = o[j + 1];
+                }
+            }
+            const int32_t la = __shfl_sync(0xffffffffu, oa, r & 31), lb = __shfl_sync(0xffffffffu, ob, r & 31);
+            const int32_t ha = __shfl_sync(0xffffffffu, oa, (r + 1) & 31), hb = __shfl_sync(0xffffffffu, ob, (r + 1) & 31);
+            EdgeSum<V> sum;
+            sum.init();
+            if (valid) {
+                const int lo = (r >> 5) == j0 ? la : lb, hi = ((r + 1) >> 5) == j0 ? ha : hb;
+                for (int e = lo + es; e < hi; e += g) sum.add(s_vals[e]);
+            }
+            V sv = sum.get();
+            for (int m = 1; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+            if (valid && es == 0) rowsum[T.r0 + r] = sv;
+        }
+        __syncwarp();
+    };
+    // chunk of a long row: the warp strides over the chunk, CPER gathers per
+    // lane in flight and the next step's indices requested meanwhile; lane l
+    // adds in-edges l, l + 32, ... in order; the last chunk of a row to finish
+    // adds the chunk sums in chunk order
+    auto chunk_tile = [&](const Tile &T) {
+        const int32_t v = T.r0;
+        const int nv = T.e1 - T.e0;
+        EdgeSum<V> sum;
+        sum.init();
+        int32_t u[CPER];
+#pragma unroll
+        for (int k = 0; k < CPER; k++) {
+            const int idx = lane + 32 * k;
+            u[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
+        }
+        for (int base = lane; base < nv; base += 32 * CPER) {
+            V x[CPER];
+#pragma unroll
+            for (int k = 0; k < CPER; k++) x[k] = u[k] >= 0 ? gather(u[k]) : N::zero();
+            int32_t un[CPER];
+#pragma unroll
+            for (int k = 0; k < CPER; k++) {
+                const int idx = base + 32 * CPER + 32 * k;
+                un[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < CPER; k++)
+                if (u[k] >= 0) sum.add(x[k]);
+#pragma unroll
+            for (int k = 0; k < CPER; k++) u[k] = un[k];
+        }
+        V sv = sum.get();
+        for (int m = 1; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+        if (T.slot < 0) {
+            if (lane == 0) rowsum[v] = sv;
+        } else {
+            const int32_t base = slot_base[T.slot];
+            if (lane == 0) chunk_part[base + T.k] = sv;
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&chunk_cnt[T.slot], 1u) == (unsigned int)(T.nch - 1);
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                V t = N::zero();
+                for (int32_t q = lane; q < T.nch; q += 32) t = N::add_pos(t, ld_cg_v<V>(chunk_part + base + q));
+                for (int m = 1; m < 32; m <<= 1) t = N::add_pos(t, N::shfl_xor(t, m));
+                if (lane == 0) {
+                    rowsum[v] = t;
+                    chunk_cnt[T.slot] = 0;
+                }
             }
             __syncwarp();
         }

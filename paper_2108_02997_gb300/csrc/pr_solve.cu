@@ -182,7 +182,7 @@ bool hub_gather(int W) { return kHubGather && hub_width_ok(W, 8); }
 template <typename V>
 void *hub_ptr(int W) {
     switch (W) {
-        case 1: return (void *)pr_gather_hub_kernel<V, 1>;
+        case 1: return (void *)pr_gather_hub1_kernel<V>;
         case 2: return (void *)pr_gather_hub_kernel<V, 2>;
         default: return (void *)pr_gather_hub_kernel<V, 4>;
     }

@@ -367,3 +367,21 @@ def test_hub_kernel_several_columns(B, orc, gg, precision, width):
             else:
                 ref = orc.pagerank(g, a, 1e-10, 1, 500, history=True)
                 assert_fp64_parity(x.out, x.iters, x.err, ref, 1e-10, 1, f"{precision} W{width} alpha {a}")
+
+
+def test_mixed_precision_four_column_jobs(B, orc, gg):
+    """Mixed precision in jobs of four columns with split passes: the FP32
+    phase and the DF64 refinement both gather with the four-column hub kernel
+    (16- and 32-byte vectors); every answer within the bound."""
+    g = gg.rmat(15, 16, seed=81)
+    alphas = (0.6, 0.75, 0.85, 0.95)
+    with B.Graph.from_csr(g) as dg:
+        xs = [B.Instance(dg, a, 1e-10, 1, 500) for a in alphas]
+        B.pr_solve_batch(xs, precision="mixed", group="pack", kernels="split")
+        st = B.pr_last_solve_stats()
+        assert st["mixed_columns"] == len(alphas)
+        for a, x in zip(alphas, xs):
+            assert x.converged
+            star = orc.pagerank(g, a, 1e-13, 1, 10000, threads=orc.default_threads())
+            assert_bound_parity(orc, g, a, 1e-10, 1, 500, x.out, x.iters, x.converged, star.ranks,
+                                what=f"mixed W4 alpha {a}")
