@@ -276,6 +276,105 @@ for _f, *_ in pr_instance._fields_:
     assert _INST_DTYPE.fields[_f][1] == getattr(pr_instance, _f).offset, _f
 
 
+class PreparedBatch:
+    """A batch of :class:`Instance` marshalled once into the library's
+    ``pr_instance`` array, to be solved any number of times (repeated sweeps
+    over the same graphs and outputs pay no per-instance Python work per call).
+    ``out`` buffers are allocated here when missing (numpy, or torch CUDA
+    tensors when ``outputs_on_device``). After :meth:`solve` the results are
+    numpy arrays in instance order: ``iters``, ``err``, ``err_l1``,
+    ``converged``, ``status``; :meth:`fill` copies them into the instances."""
+
+    def __init__(self, insts, outputs_on_device=False):
+        n = len(insts)
+        self.insts = list(insts)
+        self.outputs_on_device = bool(outputs_on_device)
+        arr = np.zeros(max(n, 1), _INST_DTYPE)
+        self._keep = []
+        if outputs_on_device:
+            import torch
+            for x in insts:
+                if x.out is None:
+                    x.out = torch.empty(x.graph.n, dtype=torch.float64, device="cuda")
+                if not (isinstance(x.out, torch.Tensor) and x.out.is_cuda and x.out.is_contiguous()):
+                    raise ValueError("every out must be a contiguous CUDA tensor when outputs_on_device")
+            arr["ranks_out"][:n] = [x.out.data_ptr() for x in insts]
+        else:
+            outs = []
+            for x in insts:
+                if x.out is None:
+                    x.out = np.empty(x.graph.n, np.float64)
+                addr, dev = _ptr_of(x.out)
+                if dev:
+                    raise ValueError("every out must live on the device iff outputs_on_device")
+                outs.append(addr)
+            arr["ranks_out"][:n] = outs
+        arr["g"][:n] = [x.graph.handle.value or 0 for x in insts]
+        arr["alpha"][:n] = [x.alpha for x in insts]
+        arr["tol"][:n] = [x.tol for x in insts]
+        arr["norm"][:n] = [NORMS[x.norm] for x in insts]
+        arr["max_iter"][:n] = [x.max_iter for x in insts]
+        self.has_init = any(x.init is not None for x in insts)
+        if self.has_init:
+            inits = []
+            for x in insts:
+                if x.init is not None:
+                    inits.append(_ptr_of(x.init)[0])
+                    self._keep.append(x.init)
+                else:
+                    inits.append(0)
+            arr["init_vec"][:n] = inits
+        self.arr = arr
+        self.n = n
+
+    def solve(self, *, precision="df64", init=None, loop="graph", stream=None, share=True, switch_tol=1e-6,
+              mlp=None, check=True, group="auto", max_passes=0, kernels="auto"):
+        """One pr_solve_batch call over the prepared instances; returns its status."""
+        if stream is None and self.outputs_on_device:
+            stream = current_stream_ptr()
+        o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, self.outputs_on_device, mlp,
+                                 group, max_passes, kernels)
+        if self.has_init and o.init == PR_INIT_UNIFORM:
+            o.init = PR_INIT_USER
+        st = lib().pr_solve_batch(self.arr.ctypes.data, self.n, C.byref(o))
+        if check:
+            _check(st, "pr_solve_batch")
+        return st
+
+    @property
+    def iters(self):
+        return self.arr["iters"][:self.n]
+
+    @property
+    def err(self):
+        return self.arr["err"][:self.n]
+
+    @property
+    def err_l1(self):
+        return self.arr["err_l1"][:self.n]
+
+    @property
+    def converged(self):
+        return self.arr["converged"][:self.n].astype(bool)
+
+    @property
+    def status(self):
+        return self.arr["status"][:self.n]
+
+    def fill(self):
+        """Copy the last call's results into the instances; returns them."""
+        iters, conv, err, err1, stat = (self.arr["iters"].tolist(), self.arr["converged"].tolist(),
+                                        self.arr["err"].tolist(), self.arr["err_l1"].tolist(),
+                                        self.arr["status"].tolist())
+        for i, x in enumerate(self.insts):
+            x.iters = iters[i]
+            x.err = err[i]
+            x.err_l1 = err1[i]
+            x.converged = bool(conv[i])
+            x.status = stat[i]
+        return self.insts
+
+
 def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=None, share=True,
                    switch_tol=1e-6, outputs_on_device=False, mlp=None, check=True, group="auto", max_passes=0,
                    kernels="auto"):
@@ -283,56 +382,10 @@ def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=N
     torch CUDA tensors when ``outputs_on_device``), ``iters``, ``err``,
     ``converged`` and ``status`` of every :class:`Instance`; returns the
     library status."""
-    n = len(insts)
-    arr = np.zeros(max(n, 1), _INST_DTYPE)
-    keep = []
-    if outputs_on_device:
-        import torch
-        for x in insts:
-            if x.out is None:
-                x.out = torch.empty(x.graph.n, dtype=torch.float64, device="cuda")
-            if not (isinstance(x.out, torch.Tensor) and x.out.is_cuda and x.out.is_contiguous()):
-                raise ValueError("every out must be a contiguous CUDA tensor when outputs_on_device")
-        arr["ranks_out"][:n] = [x.out.data_ptr() for x in insts]
-    else:
-        outs = []
-        for x in insts:
-            if x.out is None:
-                x.out = np.empty(x.graph.n, np.float64)
-            addr, dev = _ptr_of(x.out)
-            if dev:
-                raise ValueError("every out must live on the device iff outputs_on_device")
-            outs.append(addr)
-        arr["ranks_out"][:n] = outs
-    arr["g"][:n] = [x.graph.handle.value or 0 for x in insts]
-    arr["alpha"][:n] = [x.alpha for x in insts]
-    arr["tol"][:n] = [x.tol for x in insts]
-    arr["norm"][:n] = [NORMS[x.norm] for x in insts]
-    arr["max_iter"][:n] = [x.max_iter for x in insts]
-    if any(x.init is not None for x in insts):
-        inits = []
-        for x in insts:
-            if x.init is not None:
-                inits.append(_ptr_of(x.init)[0])
-                keep.append(x.init)
-            else:
-                inits.append(0)
-        arr["init_vec"][:n] = inits
-    if stream is None and outputs_on_device:
-        stream = current_stream_ptr()
-    o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, outputs_on_device, mlp, group,
-                             max_passes, kernels)
-    if any(x.init is not None for x in insts) and o.init == PR_INIT_UNIFORM:
-        o.init = PR_INIT_USER
-    st = lib().pr_solve_batch(arr.ctypes.data, n, C.byref(o))
-    iters, conv, err, err1, stat = (arr["iters"].tolist(), arr["converged"].tolist(), arr["err"].tolist(),
-                                    arr["err_l1"].tolist(), arr["status"].tolist())
-    for i, x in enumerate(insts):
-        x.iters = iters[i]
-        x.err = err[i]
-        x.err_l1 = err1[i]
-        x.converged = bool(conv[i])
-        x.status = stat[i]
+    pb = PreparedBatch(insts, outputs_on_device)
+    st = pb.solve(precision=precision, init=init, loop=loop, stream=stream, share=share, switch_tol=switch_tol,
+                  mlp=mlp, check=False, group=group, max_passes=max_passes, kernels=kernels)
+    pb.fill()
     if check:
         _check(st, "pr_solve_batch")
     return st

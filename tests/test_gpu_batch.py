@@ -385,3 +385,29 @@ def test_mixed_precision_four_column_jobs(B, orc, gg):
             star = orc.pagerank(g, a, 1e-13, 1, 10000, threads=orc.default_threads())
             assert_bound_parity(orc, g, a, 1e-10, 1, 500, x.out, x.iters, x.converged, star.ranks,
                                 what=f"mixed W4 alpha {a}")
+
+
+def test_prepared_batch_repeats_the_same_solve(B, orc, er):
+    """A PreparedBatch marshals its instances once; every solve gives the
+    answers pr_solve_batch gives for the same instances."""
+    import torch
+    alphas = (0.6, 0.85)
+    with B.Graph.from_csr(er) as dg:
+        outs = [torch.empty(er.n, dtype=torch.float64, device="cuda") for _ in range(6)]
+        specs = [(a, t, nm) for a in alphas for t, nm in ((1e-6, 1), (1e-10, 1), (1e-9, 3))]
+        pb = B.PreparedBatch([B.Instance(dg, a, t, nm, 500, out=outs[k]) for k, (a, t, nm) in enumerate(specs)],
+                             outputs_on_device=True)
+        ref = [B.Instance(dg, a, t, nm, 500) for a, t, nm in specs]
+        B.pr_solve_batch(ref)
+        for call in range(2):
+            for o in outs:
+                o.fill_(float("nan"))
+            pb.solve()
+            assert list(pb.iters) == [x.iters for x in ref]
+            for k, x in enumerate(ref):
+                assert np.array_equal(outs[k].cpu().numpy(), x.out)
+        xs = pb.fill()
+        for x, r, (a, t, nm) in zip(xs, ref, specs):
+            assert x.iters == r.iters and x.converged == r.converged and x.err == r.err
+            o = orc.pagerank(er, a, t, nm, 500, history=True)
+            assert_fp64_parity(x.out.cpu().numpy(), x.iters, x.err, o, t, nm, f"prepared alpha {a} tau {t}")
