@@ -745,8 +745,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="headline", choices=("headline",) + SINGLE)
-    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
-                    help="device loop of the timed solves (host: one launch per iteration)")
+    ap.add_argument("--loop", default="auto", choices=["auto", "graph", "persistent", "host"],
+                    help="loop of the timed solves (auto: persistent passes where they apply, else the CUDA "
+                         "graph's while-loop; host: one launch per iteration)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-instance GPU solver comparison")

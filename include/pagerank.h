@@ -124,14 +124,26 @@ typedef enum pr_init {
                              positive gain is never used. */
 } pr_init;
 
-/* Device-side loop control. */
+/* Device-side loop control (Section 2's iteration until the stopping rule
+ * holds or the cap is reached). */
 typedef enum pr_loop {
-    PR_LOOP_GRAPH = 0,    /* default: one CUDA graph whose while-node repeats the
-                             iteration kernel until every instance has stopped;
-                             the stop decision is taken on the device */
-    PR_LOOP_HOST = 1      /* one launch per iteration and a device-to-host read
+    PR_LOOP_GRAPH = 0,    /* one CUDA graph whose while-node repeats the
+                             iteration kernel(s) until every instance has
+                             stopped; the stop decision is taken on the device */
+    PR_LOOP_HOST = 1,     /* one launch per iteration and a device-to-host read
                              of the stop flag after each (the plain per-instance
                              baseline; also used to time single launches) */
+    PR_LOOP_PERSISTENT = 2, /* every iteration pass in one cooperative launch:
+                             the CTAs stay resident and wait, on a device
+                             counter, for each pass's stop decision (no launch
+                             between passes). Used where a pass is one fused
+                             kernel and its whole grid fits on the device at
+                             once; otherwise the solve runs as PR_LOOP_GRAPH.
+                             Each wait is bounded (2 s of device time): a wait
+                             that runs out ends the solve with PR_ETIMEOUT and
+                             leaves the context usable */
+    PR_LOOP_AUTO = 3      /* default: PR_LOOP_PERSISTENT where it applies, else
+                             PR_LOOP_GRAPH */
 } pr_loop;
 
 /* How pr_solve_batch packs its columns (iterate sequences) into jobs. A job
@@ -192,7 +204,7 @@ typedef struct pr_options {
                                    share (graph, alpha, start, precision) read their
                                    answers off one iterate sequence; 0 gives every
                                    instance its own column */
-    int32_t loop;               /* pr_loop; default PR_LOOP_GRAPH */
+    int32_t loop;               /* pr_loop; default PR_LOOP_AUTO */
     const pr_mlp *mlp;          /* PR_INIT_LEARNED: trained network */
     double *err_history;        /* pr_solve only, optional host buffer of
                                    3*max_iter doubles: row i-1 = (L1, L2, Linf)
@@ -204,7 +216,10 @@ typedef struct pr_options {
                                    the context stays usable); 0 (default) =
                                    the largest max_iter + 3 */
     int32_t kernels;            /* pr_kernels; default PR_KERNELS_AUTO */
-    int32_t reserved[5];        /* zero */
+    int32_t persist_wait_us;    /* PR_LOOP_PERSISTENT: bound of one wait for a
+                                   pass's decision, microseconds; 0 (default)
+                                   = 2,000,000 */
+    int32_t reserved[4];        /* zero */
 } pr_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -444,7 +459,8 @@ pr_status pr_kernel_occupancy(int32_t precision, int32_t width, int32_t *ctas_pe
  *   passes    : iteration passes executed on the device
  *   kernel_ms : PR_LOOP_HOST only: sum over iteration passes of the CUDA-event
  *               time between the events recorded just before and just after
- *               each pass's launches on the solve's stream; 0 for PR_LOOP_GRAPH
+ *               each pass's launches on the solve's stream; 0 for the device
+ *               loops (PR_LOOP_GRAPH, PR_LOOP_PERSISTENT)
  *   total_ms  : CUDA-event time of the whole device loop (all phases)
  */
 pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms);
@@ -482,6 +498,23 @@ pr_status pr_workspace_release(void);
  * may be NULL.
  */
 pr_status pr_last_solve_columns(int32_t *columns, int32_t *mixed_columns, int32_t *learned_columns);
+
+/*
+ * How the last solve on any thread looped: the number of its phases (one per
+ * precision phase and sub-solve) that ran as a CUDA graph while-loop, as a
+ * host loop and as persistent passes (pr_loop). Host pointers, each may be
+ * NULL.
+ */
+pr_status pr_last_solve_loops(int32_t *graph_phases, int32_t *host_phases, int32_t *persistent_phases);
+
+/*
+ * Test hook for the bounded waits of persistent passes: while `on` is nonzero,
+ * solves that run persistent passes never release a pass's decision, so every
+ * CTA's wait runs out after persist_wait_us and the solve returns PR_ETIMEOUT
+ * (no GPU fault is involved; the context stays usable). Process-wide; always
+ * PR_OK.
+ */
+pr_status pr_test_hold_decisions(int32_t on);
 
 /* Message for the last error on this thread ("" if none). */
 const char *pr_last_error(void);

@@ -25,7 +25,8 @@ PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT, PR_ESTATE, PR_ENOTSUP = rang
 PR_NORM_L1, PR_NORM_L2, PR_NORM_LINF = 1, 2, 3
 PR_PREC_DF64, PR_PREC_FP64, PR_PREC_MIXED, PR_PREC_FP32, PR_PREC_AUTO = 0, 1, 2, 3, 4
 PR_INIT_UNIFORM, PR_INIT_USER, PR_INIT_LEARNED, PR_INIT_CHAIN, PR_INIT_AUTO = 0, 1, 2, 3, 4
-PR_LOOP_GRAPH, PR_LOOP_HOST = 0, 1
+PR_LOOP_GRAPH, PR_LOOP_HOST, PR_LOOP_PERSISTENT, PR_LOOP_AUTO = 0, 1, 2, 3
+LOOPS = {"graph": PR_LOOP_GRAPH, "host": PR_LOOP_HOST, "persistent": PR_LOOP_PERSISTENT, "auto": PR_LOOP_AUTO}
 PR_GROUP_AUTO, PR_GROUP_PACK, PR_GROUP_SINGLE = 0, 1, 2
 GROUPS = {"auto": PR_GROUP_AUTO, "pack": PR_GROUP_PACK, "single": PR_GROUP_SINGLE}
 PR_KERNELS_AUTO, PR_KERNELS_FUSED, PR_KERNELS_SPLIT = 0, 1, 2
@@ -42,7 +43,7 @@ class pr_options(C.Structure):
                 ("switch_tol", C.c_double), ("stream", C.c_void_p),
                 ("share_trajectories", C.c_int32), ("loop", C.c_int32), ("mlp", C.c_void_p),
                 ("err_history", C.c_void_p), ("group", C.c_int32), ("max_passes", C.c_int32),
-                ("kernels", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("kernels", C.c_int32), ("persist_wait_us", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class pr_instance(C.Structure):
@@ -80,6 +81,8 @@ SIGNATURES = {
     "pr_last_solve_stats": ([_vp, _vp, _vp, _vp], _i32),
     "pr_last_solve_kernel_ms": ([_vp, _vp], _i32),
     "pr_last_solve_columns": ([_vp, _vp, _vp], _i32),
+    "pr_last_solve_loops": ([_vp, _vp, _vp], _i32),
+    "pr_test_hold_decisions": ([_i32], _i32),
     "pr_mlp_gain": ([_vp, _vp, _vp], _i32),
     "pr_mlp_set_gain": ([_vp, _d], _i32),
     "pr_graph_tune": ([_vp, _i32, _i32, _vp, _vp], _i32),
@@ -196,14 +199,17 @@ class SolveResult:
     err_history: np.ndarray | None = None
 
 
-def _make_options(precision="df64", init=None, loop="graph", stream=None, share=True, switch_tol=1e-6,
-                  outputs_on_device=False, mlp=None, group="auto", max_passes=0, kernels="auto"):
+def _make_options(precision="df64", init=None, loop="auto", stream=None, share=True, switch_tol=1e-6,
+                  outputs_on_device=False, mlp=None, group="auto", max_passes=0, kernels="auto", persist_wait_us=0):
     o = default_options()
+    o.persist_wait_us = int(persist_wait_us)
     o.kernels = KERNELS[kernels] if isinstance(kernels, str) else int(kernels)
     o.group = GROUPS[group] if isinstance(group, str) else int(group)
     o.max_passes = int(max_passes)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    o.loop = PR_LOOP_HOST if loop == "host" else PR_LOOP_GRAPH
+    if loop not in LOOPS:
+        raise ValueError(f"loop must be one of {sorted(LOOPS)}")
+    o.loop = LOOPS[loop]
     o.share_trajectories = 1 if share else 0
     o.switch_tol = switch_tol
     o.outputs_on_device = 1 if outputs_on_device else 0
@@ -226,7 +232,7 @@ def _make_options(precision="df64", init=None, loop="graph", stream=None, share=
 
 
 def pr_solve(g: Graph, alpha: float, tol: float, norm=PR_NORM_L1, max_iter: int = 500, *,
-             precision="df64", init=None, out=None, loop="graph", stream=None, history=False,
+             precision="df64", init=None, out=None, loop="auto", stream=None, history=False,
              switch_tol=1e-6, mlp=None, kernels="auto") -> SolveResult:
     """Solve one instance. ``out``: numpy array (host) or torch CUDA tensor
     (device) of n float64; allocated as numpy when omitted."""
@@ -327,13 +333,13 @@ class PreparedBatch:
         self.arr = arr
         self.n = n
 
-    def solve(self, *, precision="df64", init=None, loop="graph", stream=None, share=True, switch_tol=1e-6,
-              mlp=None, check=True, group="auto", max_passes=0, kernels="auto"):
+    def solve(self, *, precision="df64", init=None, loop="auto", stream=None, share=True, switch_tol=1e-6,
+              mlp=None, check=True, group="auto", max_passes=0, kernels="auto", persist_wait_us=0):
         """One pr_solve_batch call over the prepared instances; returns its status."""
         if stream is None and self.outputs_on_device:
             stream = current_stream_ptr()
         o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, self.outputs_on_device, mlp,
-                                 group, max_passes, kernels)
+                                 group, max_passes, kernels, persist_wait_us)
         if self.has_init and o.init == PR_INIT_UNIFORM:
             o.init = PR_INIT_USER
         st = lib().pr_solve_batch(self.arr.ctypes.data, self.n, C.byref(o))
@@ -375,20 +381,27 @@ class PreparedBatch:
         return self.insts
 
 
-def pr_solve_batch(insts, *, precision="df64", init=None, loop="graph", stream=None, share=True,
+def pr_solve_batch(insts, *, precision="df64", init=None, loop="auto", stream=None, share=True,
                    switch_tol=1e-6, outputs_on_device=False, mlp=None, check=True, group="auto", max_passes=0,
-                   kernels="auto"):
+                   kernels="auto", persist_wait_us=0):
     """Solve many instances together. Fills ``out`` (allocated as numpy, or as
     torch CUDA tensors when ``outputs_on_device``), ``iters``, ``err``,
     ``converged`` and ``status`` of every :class:`Instance`; returns the
     library status."""
     pb = PreparedBatch(insts, outputs_on_device)
     st = pb.solve(precision=precision, init=init, loop=loop, stream=stream, share=share, switch_tol=switch_tol,
-                  mlp=mlp, check=False, group=group, max_passes=max_passes, kernels=kernels)
+                  mlp=mlp, check=False, group=group, max_passes=max_passes, kernels=kernels,
+                  persist_wait_us=persist_wait_us)
     pb.fill()
     if check:
         _check(st, "pr_solve_batch")
     return st
+
+
+def hold_decisions(on: bool) -> None:
+    """Test hook (pr_test_hold_decisions): while on, persistent passes never
+    release a decision, so their bounded waits run out (PR_ETIMEOUT)."""
+    _check(lib().pr_test_hold_decisions(1 if on else 0), "pr_test_hold_decisions")
 
 
 def pr_graph_tune(g: "Graph", precision="df64", max_width: int = 32, stream=None):
@@ -456,9 +469,12 @@ def pr_last_solve_stats():
     lib().pr_last_solve_kernel_ms(C.byref(gm), C.byref(um))
     co, mc, lc = C.c_int32(), C.c_int32(), C.c_int32()
     lib().pr_last_solve_columns(C.byref(co), C.byref(mc), C.byref(lc))
+    lg, lh, lp = C.c_int32(), C.c_int32(), C.c_int32()
+    lib().pr_last_solve_loops(C.byref(lg), C.byref(lh), C.byref(lp))
     return {"launches": la.value, "passes": pa.value, "kernel_ms": km.value, "total_ms": tm.value,
             "gather_ms": gm.value, "update_ms": um.value, "columns": co.value, "mixed_columns": mc.value,
-            "learned_columns": lc.value}
+            "learned_columns": lc.value,
+            "loop_phases": {"graph": lg.value, "host": lh.value, "persistent": lp.value}}
 
 
 class MLP:

@@ -69,7 +69,7 @@ extern "C" void pr_options_default(pr_options *opt) {
     opt->init = PR_INIT_UNIFORM;
     opt->switch_tol = 1e-6;
     opt->share_trajectories = 1;
-    opt->loop = PR_LOOP_GRAPH;
+    opt->loop = PR_LOOP_AUTO;
     opt->group = PR_GROUP_AUTO;
 }
 
@@ -80,10 +80,11 @@ namespace {
 pr_status check_options(const pr_options &o) {
     if (o.precision < PR_PREC_DF64 || o.precision > PR_PREC_AUTO) return pr_fail(PR_EINVAL, "unknown precision");
     if (o.init < PR_INIT_UNIFORM || o.init > PR_INIT_AUTO) return pr_fail(PR_EINVAL, "unknown init mode");
-    if (o.loop != PR_LOOP_GRAPH && o.loop != PR_LOOP_HOST) return pr_fail(PR_EINVAL, "unknown loop mode");
+    if (o.loop < PR_LOOP_GRAPH || o.loop > PR_LOOP_AUTO) return pr_fail(PR_EINVAL, "unknown loop mode");
     if (o.group < PR_GROUP_AUTO || o.group > PR_GROUP_SINGLE) return pr_fail(PR_EINVAL, "unknown group mode");
     if (o.max_passes < 0) return pr_fail(PR_EINVAL, "max_passes must be >= 0");
     if (o.kernels < PR_KERNELS_AUTO || o.kernels > PR_KERNELS_SPLIT) return pr_fail(PR_EINVAL, "unknown kernels mode");
+    if (o.persist_wait_us < 0) return pr_fail(PR_EINVAL, "persist_wait_us must be >= 0");
     if ((o.precision == PR_PREC_MIXED || o.precision == PR_PREC_AUTO) && !(o.switch_tol > 0.0 && std::isfinite(o.switch_tol)))
         return pr_fail(PR_EINVAL, "switch_tol must be positive and finite");
     if ((o.init == PR_INIT_LEARNED || o.init == PR_INIT_AUTO) && !pr_mlp_valid(o.mlp))
@@ -225,6 +226,7 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
     req.stream = st;
     req.max_passes = opt.max_passes;
     req.kernels = opt.kernels;
+    req.persist_wait_us = opt.persist_wait_us;
     std::map<std::tuple<const pr_graph *, uint64_t, const double *>, int> col_of;
     std::vector<std::vector<std::pair<int, int>>> col_taps;   // (instance, tap index)
     for (int i : ok) {
@@ -288,6 +290,7 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
         part.stream = req.stream;
         part.max_passes = req.max_passes;
         part.kernels = req.kernels;
+        part.persist_wait_us = req.persist_wait_us;
         for (int c : cols) part.cols.push_back(req.cols[c]);
         std::vector<SubSolve> plan;
         pr_status ps = pr_plan_request(part, opt.group, plan);
@@ -300,6 +303,7 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
             sub.stream = part.stream;
             sub.max_passes = part.max_passes;
             sub.kernels = part.kernels;
+            sub.persist_wait_us = part.persist_wait_us;
             std::vector<int> cmap;   // sub-request column -> request column
             for (const auto &jc : sp.jobs) {
                 std::vector<int> local;

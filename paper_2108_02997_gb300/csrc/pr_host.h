@@ -80,10 +80,12 @@ struct SolveStats {
     int columns = 0;        // columns (iterate sequences) solved
     int mixed_columns = 0;  //   of which in mixed precision
     int learned_columns = 0;//   of which from the learned start
+    int loop_phases[3] = {0, 0, 0};  // phases run per loop form (pr_loop: graph, host, persistent)
     void add(const SolveStats &o) {
         launches += o.launches; passes += o.passes; kernel_ms += o.kernel_ms; total_ms += o.total_ms;
         gather_ms += o.gather_ms; update_ms += o.update_ms; columns += o.columns;
         mixed_columns += o.mixed_columns; learned_columns += o.learned_columns;
+        for (int i = 0; i < 3; i++) loop_phases[i] += o.loop_phases[i];
     }
 };
 
@@ -98,8 +100,13 @@ struct SolveRequest {
     std::vector<std::vector<int>> jobs;
     int max_passes = 0;     // 0: the largest max_iter + 3
     int kernels = PR_KERNELS_AUTO;
+    int persist_wait_us = 0;   // persistent passes: bound of one wait (0: the default)
     SolveStats stats;       // out
 };
+
+// Test hook: while set, persistent passes never release a decision, so that
+// every wait runs out (pr_test_hold_decisions).
+bool pr_hold_decisions();
 
 pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out);
 void pr_record_last_stats(const SolveStats &s);

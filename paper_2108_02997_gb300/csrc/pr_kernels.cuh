@@ -34,9 +34,10 @@
 #include "pr_internal.cuh"
 
 enum PassMode { kPassInit = 0, kPassIterate = 1 };
-// Iteration kernel forms: the whole pass in one kernel, or the gather half of
-// a split pass that only writes row sums.
-enum KernelMode { kModeFused = 0, kModeGather = 1 };
+// Iteration kernel forms: the whole pass in one kernel, the gather half of a
+// split pass that only writes row sums, or the whole pass repeated inside one
+// cooperative launch until the stopping decision (persistent passes).
+enum KernelMode { kModeFused = 0, kModeGather = 1, kModePersist = 2 };
 
 // ---------------------------------------------------------------- small helpers
 template <typename V>
@@ -56,6 +57,21 @@ template <> __device__ __forceinline__ float ld_cg_v<float>(const float *p) { re
 template <> __device__ __forceinline__ df64 ld_cg_v<df64>(const df64 *p) {
     float2 f = __ldcg(reinterpret_cast<const float2 *>(p));
     return {f.x, f.y};
+}
+
+// Pass counter hand-over of persistent passes (gpu-scope acquire / release).
+__device__ __forceinline__ int32_t ld_acquire_gpu(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int32_t *p, int32_t v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // An in-edge index of the one-column kernels (read once per pass: with
@@ -187,7 +203,11 @@ __device__ __forceinline__ void row_update(const int32_t *__restrict__ outdeg, c
 // ---------------------------------------------------------------- pass bookkeeping
 // CTA partials of the thread accumulators, then the job finalizer (last CTA of
 // the job) and the global decision (last job). Shared by both kernels.
-template <typename V, int W>
+// kPersist (persistent passes): every store of the CTA's pass is made visible
+// at gpu scope before it arrives, since the job's CTAs read the new
+// contributions in the next pass of the same launch, and the pass counter is
+// released after the decision it announces.
+template <typename V, int W, bool kPersist = false>
 __device__ __noinline__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V> &acc, int local, int mode) {
     using N = Num<V>;
     using Acc = typename N::Acc;
@@ -222,6 +242,7 @@ __device__ __noinline__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *g
     }
     __syncthreads();
     if (tid == 0) {
+        if constexpr (kPersist) __threadfence();
         unsigned int old = atomicAdd(&job.arrive, 1u);
         s_flag = (old == (unsigned int)(job.cta_count - 1));
     }
@@ -395,13 +416,18 @@ __device__ __noinline__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *g
             int any = (unsigned int)(old & 0xffffffffull) + (alive ? 1u : 0u) > 0u;
             glob->arrive_alive = 0ull;
             if (mode == kPassIterate) {
-                glob->pass = g_pass + 1;
                 if (*(volatile int32_t *)&glob->error) any = 0;
                 if (any && g_pass + 1 >= g_cap) {
                     glob->error = kErrPassCap;
                     any = 0;
                 }
                 glob->alive = any;
+                if constexpr (kPersist) {
+                    __threadfence();
+                    if (!*(volatile int32_t *)&glob->hold) st_release_gpu(&glob->pass, g_pass + 1);
+                } else {
+                    glob->pass = g_pass + 1;
+                }
                 if (!any && glob->cond) cudaGraphSetConditional((cudaGraphConditionalHandle)glob->cond, 0u);
             } else {
                 glob->alive = any;
@@ -451,6 +477,38 @@ __global__ void __launch_bounds__(kBlock) pr_init_kernel(JobDev *jobs, GlobalDev
     finish_pass<V, W>(jobs, job, glob, acc, local, kPassInit);
 }
 
+// ---------------------------------------------------------------- persistent passes
+// The CTA waits until the decision of pass `pass` (the pass counter moves on)
+// and returns whether another pass runs. Thread 0 polls with a gpu-scope
+// acquire; the CTA barrier then orders every thread's next reads after the
+// stores the decision published. The wait is bounded: after `limit_ns` of the
+// global timer the CTA records kErrWait and stops, and every CTA that reads
+// the error stops too, so a broken hand-over ends the launch with an error the
+// host reports instead of hanging.
+static __device__ __noinline__ bool persist_wait(GlobalDev *glob, int32_t pass, unsigned long long limit_ns) {
+    __shared__ int s_go;
+    if (threadIdx.x == 0) {
+        int go = 0;
+        const unsigned long long t0 = global_ns();
+        for (unsigned int spin = 0;; spin++) {
+            if (ld_acquire_gpu(&glob->pass) != pass) {
+                __threadfence();
+                go = *(volatile int32_t *)&glob->alive && !*(volatile int32_t *)&glob->error;
+                break;
+            }
+            if (*(volatile int32_t *)&glob->error) break;
+            if ((spin & 15u) == 15u && global_ns() - t0 > limit_ns) {
+                atomicCAS(&glob->error, kErrNone, kErrWait);
+                break;
+            }
+            __nanosleep(64);
+        }
+        s_go = go;
+    }
+    __syncthreads();
+    return s_go != 0;
+}
+
 // ---------------------------------------------------------------- the iteration kernel
 template <typename V, int W, int Mode = kModeFused>
 __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGatherMinBlocks : kMinBlocks)
@@ -458,6 +516,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
     pr_iter_kernel(JobDev *jobs, GlobalDev *glob, const int32_t *cta_job) {
     using N = Num<V>;
     constexpr bool kGather = Mode == kModeGather;
+    constexpr bool kPersist = Mode == kModePersist;
     static_assert(32 % W == 0, "W must divide the warp");
     constexpr bool kStaged = (W == 1);       // one column: values staged in shared memory
     constexpr int VT = kStaged ? kTileValues : 32;   // gathered values per warp step
@@ -513,300 +572,313 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
             if (glob->cond) cudaGraphSetConditional((cudaGraphConditionalHandle)glob->cond, 0u);
         }
     }
-    const ColView<V> cv = col_view<V>(job, col);
-    const bool need_prev = cv.has && (cv.active || cv.copy_dst);
-    RowAcc<V> acc;
-    acc.init();
-    const bool work = job.alive && !*(volatile int32_t *)&glob->error;
-    // several columns: the active columns read the job's shared buffer parity
-    const unsigned int act_mask = __ballot_sync(0xffffffffu, cv.active);
-    const V *c_all = reinterpret_cast<const V *>(job.contrib[job.cur]);
-    auto gather1 = [&](int32_t u) -> V { return cv.c_prev[(size_t)u * W + col]; };
+    // persistent passes: the pass below repeats in this launch until the
+    // stopping decision (the CTA's tiles stay the same in every pass)
+    int32_t my_pass = 0;
+    unsigned long long wait_ns = kPersistWaitNs;
+    if constexpr (kPersist) {
+        my_pass = *(volatile int32_t *)&glob->pass;
+        if (glob->wait_us) wait_ns = 1000ull * glob->wait_us;
+    }
+    for (;;) {
+        const ColView<V> cv = col_view<V>(job, col);
+        const bool need_prev = cv.has && (cv.active || cv.copy_dst);
+        RowAcc<V> acc;
+        acc.init();
+        const bool work = job.alive && !*(volatile int32_t *)&glob->error;
+        // several columns: the active columns read the job's shared buffer parity
+        const unsigned int act_mask = __ballot_sync(0xffffffffu, cv.active);
+        const V *c_all = reinterpret_cast<const V *>(job.contrib[job.cur]);
+        auto gather1 = [&](int32_t u) -> V { return cv.c_prev[(size_t)u * W + col]; };
 
-    if (work) {
-        const int wstride = cta_count * kWarps;
-        // ---------------- rows tile, several columns. Sources, offsets,
-        // out-degrees and previous ranks are staged first; then per column
-        // group: one vector gather per in-edge into shared memory, and lane
-        // groups add each row's vectors; last, lane (row, column) pairs update rows.
-        auto rows_tile_vec = [&](const Tile &T) {
-            if constexpr (!kStaged) {
-                const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
-#pragma unroll
-                for (int k = 0; k < kVecTileEdges / 32; k++) {
-                    const int i = lane + 32 * k;
-                    if (i < ne) v_src[i] = src[T.e0 + i];
-                }
-                for (int i = lane; i <= nr; i += 32) v_off[i] = off[T.r0 + i] - T.e0;
-                if constexpr (!kGather) {
-                    for (int i = lane; i < nr; i += 32) v_od[i] = outdeg[T.r0 + i];
-                    if (need_prev)
-                        for (int i = lane; i < nr * W; i += 32) v_prev[i] = cv.r_prev[(size_t)T.r0 * W + i];
-                }
-                __syncwarp();
-                const int g = 1 << T.glog;
-                const int es = lane & (g - 1);
-                const int rpp = 32 >> T.glog;
-#pragma unroll 1
-                for (int cg = 0; cg < NG; cg++) {
-                    if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
-#pragma unroll
-                    for (int k0 = 0; k0 < kVecTileEdges / 32; k0 += kVecGatherBatch) {
-                        VV x[kVecGatherBatch];
-#pragma unroll
-                        for (int k = 0; k < kVecGatherBatch; k++) {
-                            const int i = lane + 32 * (k0 + k);
-                            if (i < ne) x[k] = load_vec<V, CP>(c_all + (size_t)v_src[i] * W + cg * CP);
-                        }
-#pragma unroll
-                        for (int k = 0; k < kVecGatherBatch; k++) {
-                            const int i = lane + 32 * (k0 + k);
-                            if (i < ne) v_vals[i] = x[k];
-                        }
+        if (work) {
+            const int wstride = cta_count * kWarps;
+            // ---------------- rows tile, several columns. Sources, offsets,
+            // out-degrees and previous ranks are staged first; then per column
+            // group: one vector gather per in-edge into shared memory, and lane
+            // groups add each row's vectors; last, lane (row, column) pairs update rows.
+            auto rows_tile_vec = [&](const Tile &T) {
+                if constexpr (!kStaged) {
+                    const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
+    #pragma unroll
+                    for (int k = 0; k < kVecTileEdges / 32; k++) {
+                        const int i = lane + 32 * k;
+                        if (i < ne) v_src[i] = src[T.e0 + i];
+                    }
+                    for (int i = lane; i <= nr; i += 32) v_off[i] = off[T.r0 + i] - T.e0;
+                    if constexpr (!kGather) {
+                        for (int i = lane; i < nr; i += 32) v_od[i] = outdeg[T.r0 + i];
+                        if (need_prev)
+                            for (int i = lane; i < nr * W; i += 32) v_prev[i] = cv.r_prev[(size_t)T.r0 * W + i];
                     }
                     __syncwarp();
+                    const int g = 1 << T.glog;
+                    const int es = lane & (g - 1);
+                    const int rpp = 32 >> T.glog;
+    #pragma unroll 1
+                    for (int cg = 0; cg < NG; cg++) {
+                        if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
+    #pragma unroll
+                        for (int k0 = 0; k0 < kVecTileEdges / 32; k0 += kVecGatherBatch) {
+                            VV x[kVecGatherBatch];
+    #pragma unroll
+                            for (int k = 0; k < kVecGatherBatch; k++) {
+                                const int i = lane + 32 * (k0 + k);
+                                if (i < ne) x[k] = load_vec<V, CP>(c_all + (size_t)v_src[i] * W + cg * CP);
+                            }
+    #pragma unroll
+                            for (int k = 0; k < kVecGatherBatch; k++) {
+                                const int i = lane + 32 * (k0 + k);
+                                if (i < ne) v_vals[i] = x[k];
+                            }
+                        }
+                        __syncwarp();
+                        for (int rb = 0; rb < nr; rb += rpp) {
+                            const int r = rb + (lane >> T.glog);
+                            const bool valid = r < nr;
+                            EdgeSum<V> sum[CP];
+    #pragma unroll
+                            for (int j = 0; j < CP; j++) sum[j].init();
+                            if (valid) {
+                                const int lo = v_off[r], hi = v_off[r + 1];
+                                for (int e = lo + es; e < hi; e += g) {
+                                    const VV y = v_vals[e];
+    #pragma unroll
+                                    for (int j = 0; j < CP; j++) sum[j].add(y.v[j]);
+                                }
+                            }
+    #pragma unroll
+                            for (int j = 0; j < CP; j++) {
+                                V sv = sum[j].get();
+                                for (int m = 1; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                                if (valid && es == 0) v_rsum[r * W + cg * CP + j] = sv;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    if constexpr (kGather) {
+                        // element i of the rows belongs to column i % W == lane % W
+                        if (cv.active)
+                            for (int i = lane; i < nr * W; i += 32) rowsum[(size_t)T.r0 * W + i] = v_rsum[i];
+                    } else {
+                        if (need_prev)
+                            for (int i = lane; i < nr * W; i += 32)
+                                row_update_pd<V, W>(perm, cv, acc, T.r0 + i / W, col, v_rsum[i], v_prev[i], v_od[i / W]);
+                    }
+                    __syncwarp();
+                }
+            };
+            // ---------------- rows tile, one column: indices, offsets, previous
+            // ranks and out-degrees are all requested before any gather waits
+            auto rows_tile_w1 = [&](const Tile &T) {
+                if constexpr (kStaged) {
+                    const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
+                    int32_t u[PER];
+    #pragma unroll
+                    for (int k = 0; k < PER; k++) {
+                        const int idx = lane + 32 * k;
+                        u[k] = (cv.active && idx < ne * W) ? ld_idx(src + T.e0 + idx / W) : -1;
+                    }
+                    // row offsets relative to e0 in registers: lane l holds rows l, l + 32, ...
+                    int32_t o[kOffRegs];
+    #pragma unroll
+                    for (int j = 0; j < kOffRegs; j++) {
+                        const int i = lane + 32 * j;
+                        o[j] = i <= nr ? off[T.r0 + i] - T.e0 : 0;
+                    }
+                    // element i of the rows belongs to column i % W == lane % W
+                    if constexpr (!kGather) {
+                        if (need_prev)
+                            for (int i = lane; i < nr * W; i += 32) s_prev[warp][i] = cv.r_prev[(size_t)T.r0 * W + i];
+                        for (int i = lane; i < nr; i += 32) s_od[warp][i] = outdeg[T.r0 + i];
+                    }
+                    {
+                        V x[PER];
+    #pragma unroll
+                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
+    #pragma unroll
+                        for (int k = 0; k < PER; k++)
+                            if (u[k] >= 0) s_vals[warp][lane + 32 * k] = x[k];
+                    }
+                    __syncwarp();
+                    const int g = 1 << T.glog;
+                    const int es = (lane & (g - 1)) / W;
+                    const int ES = g / W;
+                    const int rpp = 32 >> T.glog;
                     for (int rb = 0; rb < nr; rb += rpp) {
                         const int r = rb + (lane >> T.glog);
                         const bool valid = r < nr;
-                        EdgeSum<V> sum[CP];
-#pragma unroll
-                        for (int j = 0; j < CP; j++) sum[j].init();
-                        if (valid) {
-                            const int lo = v_off[r], hi = v_off[r + 1];
-                            for (int e = lo + es; e < hi; e += g) {
-                                const VV y = v_vals[e];
-#pragma unroll
-                                for (int j = 0; j < CP; j++) sum[j].add(y.v[j]);
+                        // rows r and r + 1 lie in [rb, rb + 32]: registers j0 and j0 + 1 of their lanes
+                        const int j0 = rb >> 5;
+                        int32_t oa = o[0], ob = o[kOffRegs > 1 ? 1 : 0];
+    #pragma unroll
+                        for (int j = 1; j + 1 < kOffRegs; j++) {
+                            if (j0 == j) {
+                                oa = o[j];
+                                ob = o[j + 1];
                             }
                         }
-#pragma unroll
+                        const int32_t la = __shfl_sync(0xffffffffu, oa, r & 31), lb = __shfl_sync(0xffffffffu, ob, r & 31);
+                        const int32_t ha = __shfl_sync(0xffffffffu, oa, (r + 1) & 31),
+                                      hb = __shfl_sync(0xffffffffu, ob, (r + 1) & 31);
+                        EdgeSum<V> sum;
+                        sum.init();
+                        if (valid && cv.active) {
+                            const int lo = (r >> 5) == j0 ? la : lb, hi = ((r + 1) >> 5) == j0 ? ha : hb;
+                            for (int e = lo + es; e < hi; e += ES) sum.add(s_vals[warp][e * W + col]);
+                        }
+                        V sv = sum.get();
+                        for (int m = W; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                        if constexpr (kGather) {
+                            if (valid && es == 0 && cv.active) rowsum[T.r0 + r] = sv;
+                        } else if constexpr (kTU) {
+                            if (valid && es == 0) s_sum[warp][r] = sv;
+                        } else {
+                            if (valid && es == 0 && need_prev)
+                                row_update_pd<V, W>(perm, cv, acc, T.r0 + r, col, sv, s_prev[warp][r * W + col],
+                                                    s_od[warp][r]);
+                        }
+                    }
+                    __syncwarp();
+                    if constexpr (kTU && !kGather) {
+                        // every lane updates rows: consecutive rows on consecutive lanes
+                        if (need_prev)
+                            for (int r = lane; r < nr; r += 32)
+                                row_update_pd<V, W>(perm, cv, acc, T.r0 + r, col, s_sum[warp][r], s_prev[warp][r],
+                                                    s_od[warp][r]);
+                        __syncwarp();
+                    }
+                }
+            };
+            // ---------------- one chunk of a long row
+            auto chunk_tile = [&](const Tile &T) {
+                // ---------------- one chunk of a long row, VT values per step
+                const int32_t v = T.r0;
+                const int nv = (T.e1 - T.e0) * W;
+                EdgeSum<V> sum;
+                sum.init();
+                if constexpr (!kStaged) {
+                    // several columns: per column group, lanes stride over the
+                    // chunk's in-edges with vector loads, four in flight
+                    const int ne = T.e1 - T.e0;
+    #pragma unroll 1
+                    for (int cg = 0; cg < NG; cg++) {
+                        if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
+                        EdgeSum<V> vs[CP];
+    #pragma unroll
+                        for (int j = 0; j < CP; j++) vs[j].init();
+                        const V *cb = c_all + cg * CP;
+                        int i = lane;
+                        for (; i + 96 < ne; i += 128) {
+                            const int32_t u0 = src[T.e0 + i], u1 = src[T.e0 + i + 32];
+                            const int32_t u2 = src[T.e0 + i + 64], u3 = src[T.e0 + i + 96];
+                            const VV x0 = load_vec<V, CP>(cb + (size_t)u0 * W), x1 = load_vec<V, CP>(cb + (size_t)u1 * W);
+                            const VV x2 = load_vec<V, CP>(cb + (size_t)u2 * W), x3 = load_vec<V, CP>(cb + (size_t)u3 * W);
+    #pragma unroll
+                            for (int j = 0; j < CP; j++) {
+                                vs[j].add(x0.v[j]); vs[j].add(x1.v[j]); vs[j].add(x2.v[j]); vs[j].add(x3.v[j]);
+                            }
+                        }
+                        for (; i < ne; i += 32) {
+                            const VV x0 = load_vec<V, CP>(cb + (size_t)src[T.e0 + i] * W);
+    #pragma unroll
+                            for (int j = 0; j < CP; j++) vs[j].add(x0.v[j]);
+                        }
+    #pragma unroll
                         for (int j = 0; j < CP; j++) {
-                            V sv = sum[j].get();
-                            for (int m = 1; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-                            if (valid && es == 0) v_rsum[r * W + cg * CP + j] = sv;
+                            V sv = vs[j].get();
+                            for (int m = 1; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
+                            if (lane == 0) v_rsum[cg * CP + j] = sv;
                         }
                     }
                     __syncwarp();
                 }
-                if constexpr (kGather) {
-                    // element i of the rows belongs to column i % W == lane % W
-                    if (cv.active)
-                        for (int i = lane; i < nr * W; i += 32) rowsum[(size_t)T.r0 * W + i] = v_rsum[i];
-                } else {
-                    if (need_prev)
-                        for (int i = lane; i < nr * W; i += 32)
-                            row_update_pd<V, W>(perm, cv, acc, T.r0 + i / W, col, v_rsum[i], v_prev[i], v_od[i / W]);
-                }
-                __syncwarp();
-            }
-        };
-        // ---------------- rows tile, one column: indices, offsets, previous
-        // ranks and out-degrees are all requested before any gather waits
-        auto rows_tile_w1 = [&](const Tile &T) {
-            if constexpr (kStaged) {
-                const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
-                int32_t u[PER];
-#pragma unroll
-                for (int k = 0; k < PER; k++) {
-                    const int idx = lane + 32 * k;
-                    u[k] = (cv.active && idx < ne * W) ? ld_idx(src + T.e0 + idx / W) : -1;
-                }
-                // row offsets relative to e0 in registers: lane l holds rows l, l + 32, ...
-                int32_t o[kOffRegs];
-#pragma unroll
-                for (int j = 0; j < kOffRegs; j++) {
-                    const int i = lane + 32 * j;
-                    o[j] = i <= nr ? off[T.r0 + i] - T.e0 : 0;
-                }
-                // element i of the rows belongs to column i % W == lane % W
-                if constexpr (!kGather) {
-                    if (need_prev)
-                        for (int i = lane; i < nr * W; i += 32) s_prev[warp][i] = cv.r_prev[(size_t)T.r0 * W + i];
-                    for (int i = lane; i < nr; i += 32) s_od[warp][i] = outdeg[T.r0 + i];
-                }
-                {
-                    V x[PER];
-#pragma unroll
-                    for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
-#pragma unroll
-                    for (int k = 0; k < PER; k++)
-                        if (u[k] >= 0) s_vals[warp][lane + 32 * k] = x[k];
-                }
-                __syncwarp();
-                const int g = 1 << T.glog;
-                const int es = (lane & (g - 1)) / W;
-                const int ES = g / W;
-                const int rpp = 32 >> T.glog;
-                for (int rb = 0; rb < nr; rb += rpp) {
-                    const int r = rb + (lane >> T.glog);
-                    const bool valid = r < nr;
-                    // rows r and r + 1 lie in [rb, rb + 32]: registers j0 and j0 + 1 of their lanes
-                    const int j0 = rb >> 5;
-                    int32_t oa = o[0], ob = o[kOffRegs > 1 ? 1 : 0];
-#pragma unroll
-                    for (int j = 1; j + 1 < kOffRegs; j++) {
-                        if (j0 == j) {
-                            oa = o[j];
-                            ob = o[j + 1];
-                        }
-                    }
-                    const int32_t la = __shfl_sync(0xffffffffu, oa, r & 31), lb = __shfl_sync(0xffffffffu, ob, r & 31);
-                    const int32_t ha = __shfl_sync(0xffffffffu, oa, (r + 1) & 31),
-                                  hb = __shfl_sync(0xffffffffu, ob, (r + 1) & 31);
-                    EdgeSum<V> sum;
-                    sum.init();
-                    if (valid && cv.active) {
-                        const int lo = (r >> 5) == j0 ? la : lb, hi = ((r + 1) >> 5) == j0 ? ha : hb;
-                        for (int e = lo + es; e < hi; e += ES) sum.add(s_vals[warp][e * W + col]);
-                    }
-                    V sv = sum.get();
-                    for (int m = W; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-                    if constexpr (kGather) {
-                        if (valid && es == 0 && cv.active) rowsum[T.r0 + r] = sv;
-                    } else if constexpr (kTU) {
-                        if (valid && es == 0) s_sum[warp][r] = sv;
-                    } else {
-                        if (valid && es == 0 && need_prev)
-                            row_update_pd<V, W>(perm, cv, acc, T.r0 + r, col, sv, s_prev[warp][r * W + col],
-                                                s_od[warp][r]);
-                    }
-                }
-                __syncwarp();
-                if constexpr (kTU && !kGather) {
-                    // every lane updates rows: consecutive rows on consecutive lanes
-                    if (need_prev)
-                        for (int r = lane; r < nr; r += 32)
-                            row_update_pd<V, W>(perm, cv, acc, T.r0 + r, col, s_sum[warp][r], s_prev[warp][r],
-                                                s_od[warp][r]);
-                    __syncwarp();
-                }
-            }
-        };
-        // ---------------- one chunk of a long row
-        auto chunk_tile = [&](const Tile &T) {
-            // ---------------- one chunk of a long row, VT values per step
-            const int32_t v = T.r0;
-            const int nv = (T.e1 - T.e0) * W;
-            EdgeSum<V> sum;
-            sum.init();
-            if constexpr (!kStaged) {
-                // several columns: per column group, lanes stride over the
-                // chunk's in-edges with vector loads, four in flight
-                const int ne = T.e1 - T.e0;
-#pragma unroll 1
-                for (int cg = 0; cg < NG; cg++) {
-                    if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
-                    EdgeSum<V> vs[CP];
-#pragma unroll
-                    for (int j = 0; j < CP; j++) vs[j].init();
-                    const V *cb = c_all + cg * CP;
-                    int i = lane;
-                    for (; i + 96 < ne; i += 128) {
-                        const int32_t u0 = src[T.e0 + i], u1 = src[T.e0 + i + 32];
-                        const int32_t u2 = src[T.e0 + i + 64], u3 = src[T.e0 + i + 96];
-                        const VV x0 = load_vec<V, CP>(cb + (size_t)u0 * W), x1 = load_vec<V, CP>(cb + (size_t)u1 * W);
-                        const VV x2 = load_vec<V, CP>(cb + (size_t)u2 * W), x3 = load_vec<V, CP>(cb + (size_t)u3 * W);
-#pragma unroll
-                        for (int j = 0; j < CP; j++) {
-                            vs[j].add(x0.v[j]); vs[j].add(x1.v[j]); vs[j].add(x2.v[j]); vs[j].add(x3.v[j]);
-                        }
-                    }
-                    for (; i < ne; i += 32) {
-                        const VV x0 = load_vec<V, CP>(cb + (size_t)src[T.e0 + i] * W);
-#pragma unroll
-                        for (int j = 0; j < CP; j++) vs[j].add(x0.v[j]);
-                    }
-#pragma unroll
-                    for (int j = 0; j < CP; j++) {
-                        V sv = vs[j].get();
-                        for (int m = 1; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-                        if (lane == 0) v_rsum[cg * CP + j] = sv;
-                    }
-                }
-                __syncwarp();
-            }
-            if (kStaged && cv.active) {
-                // the next step's indices are requested while this step's
-                // gathers are in flight
-                int32_t u[PER];
-#pragma unroll
-                for (int k = 0; k < PER; k++) {
-                    const int idx = lane + 32 * k;
-                    u[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
-                }
-                for (int base = lane; base < nv; base += VT) {
-                    V x[PER];
-#pragma unroll
-                    for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
-                    int32_t un[PER];
-#pragma unroll
+                if (kStaged && cv.active) {
+                    // the next step's indices are requested while this step's
+                    // gathers are in flight
+                    int32_t u[PER];
+    #pragma unroll
                     for (int k = 0; k < PER; k++) {
-                        const int idx = base + VT + 32 * k;
-                        un[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
+                        const int idx = lane + 32 * k;
+                        u[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
                     }
-#pragma unroll
-                    for (int k = 0; k < PER; k++)
-                        if (u[k] >= 0) sum.add(x[k]);
-#pragma unroll
-                    for (int k = 0; k < PER; k++) u[k] = un[k];
+                    for (int base = lane; base < nv; base += VT) {
+                        V x[PER];
+    #pragma unroll
+                        for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
+                        int32_t un[PER];
+    #pragma unroll
+                        for (int k = 0; k < PER; k++) {
+                            const int idx = base + VT + 32 * k;
+                            un[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
+                        }
+    #pragma unroll
+                        for (int k = 0; k < PER; k++)
+                            if (u[k] >= 0) sum.add(x[k]);
+    #pragma unroll
+                        for (int k = 0; k < PER; k++) u[k] = un[k];
+                    }
                 }
-            }
-            V sv = sum.get();
-            if constexpr (kStaged) {
-                for (int m = W; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
-            } else {
-                if (lane < W) sv = v_rsum[lane];
-                __syncwarp();
-            }
-            if (T.slot < 0) {
-                if constexpr (kGather) {
-                    if (lane < W && cv.active) rowsum[(size_t)v * W + lane] = sv;
+                V sv = sum.get();
+                if constexpr (kStaged) {
+                    for (int m = W; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
                 } else {
-                    if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, sv);
+                    if (lane < W) sv = v_rsum[lane];
+                    __syncwarp();
                 }
-            } else {
-                const int32_t base = slot_base[T.slot];
-                if (lane < W) chunk_part[(size_t)(base + T.k) * W + lane] = sv;
-                __threadfence();
-                __syncwarp();
-                int last = 0;
-                if (lane == 0) last = atomicAdd(&chunk_cnt[T.slot], 1u) == (unsigned int)(T.nch - 1);
-                last = __shfl_sync(0xffffffffu, last, 0);
-                if (last) {
-                    // the row's chunk sums, lane-parallel in a fixed order:
-                    // lane slot q0 adds chunks q0, q0 + 32/W, ... then a fixed tree
-                    __threadfence();
-                    constexpr int QS = 32 / W;
-                    V t = N::zero();
-                    for (int32_t q = lane / W; q < T.nch; q += QS)
-                        t = N::add_pos(t, ld_cg_v<V>(chunk_part + (size_t)(base + q) * W + col));
-                    for (int m = W; m < 32; m <<= 1) t = N::add_pos(t, N::shfl_xor(t, m));
+                if (T.slot < 0) {
                     if constexpr (kGather) {
-                        if (lane < W && cv.active) rowsum[(size_t)v * W + lane] = t;
+                        if (lane < W && cv.active) rowsum[(size_t)v * W + lane] = sv;
                     } else {
-                        if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, t);
+                        if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, sv);
                     }
-                    if (lane == 0) chunk_cnt[T.slot] = 0;
+                } else {
+                    const int32_t base = slot_base[T.slot];
+                    if (lane < W) chunk_part[(size_t)(base + T.k) * W + lane] = sv;
+                    __threadfence();
+                    __syncwarp();
+                    int last = 0;
+                    if (lane == 0) last = atomicAdd(&chunk_cnt[T.slot], 1u) == (unsigned int)(T.nch - 1);
+                    last = __shfl_sync(0xffffffffu, last, 0);
+                    if (last) {
+                        // the row's chunk sums, lane-parallel in a fixed order:
+                        // lane slot q0 adds chunks q0, q0 + 32/W, ... then a fixed tree
+                        __threadfence();
+                        constexpr int QS = 32 / W;
+                        V t = N::zero();
+                        for (int32_t q = lane / W; q < T.nch; q += QS)
+                            t = N::add_pos(t, ld_cg_v<V>(chunk_part + (size_t)(base + q) * W + col));
+                        for (int m = W; m < 32; m <<= 1) t = N::add_pos(t, N::shfl_xor(t, m));
+                        if constexpr (kGather) {
+                            if (lane < W && cv.active) rowsum[(size_t)v * W + lane] = t;
+                        } else {
+                            if (lane < W && cv.has) row_update<V, W>(outdeg, perm, cv, acc, v, col, t);
+                        }
+                        if (lane == 0) chunk_cnt[T.slot] = 0;
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
-            }
-        };
+            };
 
-        // the next tile's descriptor is requested while this tile is worked on
-        Tile T_next{};
-        if (local * kWarps + warp < ntiles) T_next = load_tile(tiles + local * kWarps + warp);
-        for (int t = local * kWarps + warp; t < ntiles; t += wstride) {
-            const Tile T = T_next;
-            if (t + wstride < ntiles) T_next = load_tile(tiles + t + wstride);
-            if (T.glog >= 0) {
-                if constexpr (kStaged) rows_tile_w1(T);
-                else rows_tile_vec(T);
-            } else {
-                chunk_tile(T);
+            // the next tile's descriptor is requested while this tile is worked on
+            Tile T_next{};
+            if (local * kWarps + warp < ntiles) T_next = load_tile(tiles + local * kWarps + warp);
+            for (int t = local * kWarps + warp; t < ntiles; t += wstride) {
+                const Tile T = T_next;
+                if (t + wstride < ntiles) T_next = load_tile(tiles + t + wstride);
+                if (T.glog >= 0) {
+                    if constexpr (kStaged) rows_tile_w1(T);
+                    else rows_tile_vec(T);
+                } else {
+                    chunk_tile(T);
+                }
             }
         }
+        if constexpr (!kGather) finish_pass<V, W, kPersist>(jobs, job, glob, acc, local, kPassIterate);
+        if constexpr (!kPersist) break;
+        if (!persist_wait(glob, my_pass, wait_ns)) break;
+        my_pass++;
     }
-    if constexpr (!kGather) finish_pass<V, W>(jobs, job, glob, acc, local, kPassIterate);
 }
 
 // ---------------------------------------------------------------- the update kernel (split passes)

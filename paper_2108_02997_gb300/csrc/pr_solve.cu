@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
 
 #include "pr_kernels.cuh"
@@ -149,6 +150,25 @@ void *iter_ptr(int W) {
         case 8: return (void *)pr_iter_kernel<V, 8>;
         case 16: return (void *)pr_iter_kernel<V, 16>;
         default: return (void *)pr_iter_kernel<V, 32>;
+    }
+}
+// Persistent passes: the fused pass repeated in one cooperative launch.
+template <typename V>
+void *persist_ptr(int W) {
+    switch (W) {
+        case 1: return (void *)pr_iter_kernel<V, 1, kModePersist>;
+        case 2: return (void *)pr_iter_kernel<V, 2, kModePersist>;
+        case 4: return (void *)pr_iter_kernel<V, 4, kModePersist>;
+        case 8: return (void *)pr_iter_kernel<V, 8, kModePersist>;
+        case 16: return (void *)pr_iter_kernel<V, 16, kModePersist>;
+        default: return (void *)pr_iter_kernel<V, 32, kModePersist>;
+    }
+}
+void *persist_kernel_for(int prec, int W) {
+    switch (prec) {
+        case PR_PREC_FP64: return persist_ptr<double>(W);
+        case PR_PREC_FP32: return persist_ptr<float>(W);
+        default: return persist_ptr<df64>(W);
     }
 }
 // Split passes: the gather-only and update kernels.
@@ -401,6 +421,35 @@ pr_status pr_kernel_setup(int prec, int W, int *blocks_per_sm) {
     return PR_OK;
 }
 
+namespace {
+// Persistent passes: opt the persistent kernel into the fused kernel's dynamic
+// shared memory (once per device, precision and width) and report how many of
+// its CTAs are resident per SM; 0 where the device has no cooperative launch
+// (a cooperative grid must be resident as a whole).
+pr_status persist_setup(int prec, int W, int *blocks_per_sm) {
+    static std::mutex mu;
+    static std::map<SetupKey, int> done;
+    void *k = persist_kernel_for(prec, W);
+    const size_t smem = pr_tile_smem_bytes(prec, W);
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    const SetupKey key{dev, prec & 3, w_index(W)};
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find(key);
+    if (it == done.end()) {
+        int coop = 0, occ = 0;
+        PR_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        if (coop) {
+            PR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBlock, smem));
+        }
+        it = done.emplace(key, std::max(occ, 0)).first;
+    }
+    *blocks_per_sm = it->second;
+    return PR_OK;
+}
+}  // namespace
+
 void pr_record_last_stats(const SolveStats &st) {
     std::lock_guard<std::mutex> lk(g_stats_mu);
     g_last_stats = st;
@@ -437,6 +486,24 @@ extern "C" pr_status pr_last_solve_columns(int32_t *columns, int32_t *mixed_colu
     return PR_OK;
 }
 
+namespace {
+std::atomic<int> g_hold_decisions{0};
+}
+bool pr_hold_decisions() { return g_hold_decisions.load() != 0; }
+
+extern "C" pr_status pr_test_hold_decisions(int32_t on) {
+    g_hold_decisions.store(on ? 1 : 0);
+    return PR_OK;
+}
+
+extern "C" pr_status pr_last_solve_loops(int32_t *graph_phases, int32_t *host_phases, int32_t *persistent_phases) {
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    if (graph_phases) *graph_phases = g_last_stats.loop_phases[PR_LOOP_GRAPH];
+    if (host_phases) *host_phases = g_last_stats.loop_phases[PR_LOOP_HOST];
+    if (persistent_phases) *persistent_phases = g_last_stats.loop_phases[PR_LOOP_PERSISTENT];
+    return PR_OK;
+}
+
 extern "C" pr_status pr_last_solve_stats(int32_t *launches, int32_t *passes, double *kernel_ms, double *total_ms) {
     std::lock_guard<std::mutex> lk(g_stats_mu);
     if (launches) *launches = g_last_stats.launches;
@@ -451,7 +518,7 @@ namespace {
 // One phase of a solve in one value type: init pass + loop of iteration passes.
 pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Arena &ar, size_t off_jobs,
                     size_t off_glob, size_t off_ctajob, int total_ctas, size_t off_gctajob, int total_gctas,
-                    int pass_cap, int loop, cudaStream_t st, LoopStats &stats) {
+                    int pass_cap, int loop, int wait_us, cudaStream_t st, LoopStats &stats) {
     // split passes: the pass is the gather kernel then the update kernel
     void *kiter = split ? update_kernel_for(prec, W) : pr_iter_kernel_for(prec, W);
     void *kgather = split ? gather_kernel_for(prec, W) : nullptr;
@@ -477,7 +544,25 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
     dim3 grid(total_ctas), ggrid(split ? total_gctas : 1), block(kBlock), gblock(gather_block(W));
     const size_t iter_smem = split ? 0 : smem, gather_smem = split ? gather_smem_bytes(prec, W) : 0;
     PR_CUDA(cudaEventRecord(ev0, st));
-    if (loop == PR_LOOP_HOST) {
+    if (loop >= PR_LOOP_GRAPH && loop <= PR_LOOP_PERSISTENT) stats.loop_phases[loop]++;
+    if (loop == PR_LOOP_PERSISTENT) {
+        // the init pass, then every iteration pass in one cooperative launch
+        // (the caller checked that the grid is resident as a whole)
+        hg.cond = 0;
+        hg.wait_us = (uint32_t)wait_us;
+        hg.hold = pr_hold_decisions() ? 1 : 0;
+        PR_CUDA(cudaMemcpyAsync(d_glob, &hg, sizeof(hg), cudaMemcpyHostToDevice, st));
+        PR_CUDA(cudaLaunchKernel(kinit, grid, block, args, 0, st));
+        PR_CUDA(cudaLaunchCooperativeKernel(persist_kernel_for(prec, W), grid, block, args, iter_smem, st));
+        stats.launches += 2;
+        GlobalDev back;
+        std::memset(&back, 0, sizeof(back));
+        PR_CUDA(cudaMemcpyAsync(&back, d_glob, sizeof(back), cudaMemcpyDeviceToHost, st));
+        PR_CUDA(cudaStreamSynchronize(st));
+        stats.passes += back.pass;
+        if (back.error == kErrWait) return pr_fail(PR_ETIMEOUT, "a persistent pass waited too long for its decision");
+        if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
+    } else if (loop == PR_LOOP_HOST) {
         hg.cond = 0;
         PR_CUDA(cudaMemcpyAsync(d_glob, &hg, sizeof(hg), cudaMemcpyHostToDevice, st));
         PR_CUDA(cudaLaunchKernel(kinit, grid, block, args, 0, st));
@@ -845,9 +930,26 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
     PR_CUDA(cudaMemcpyAsync(ar.at<int32_t>(off_ctajob), ctajob.data(), ctajob.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     PR_CUDA(cudaMemcpyAsync(ar.at<int32_t>(off_gctajob), gctajob.data(), gctajob.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     const int pass_cap = req.max_passes > 0 ? req.max_passes : max_iter_all + 3;
+    // ---- loop form: persistent passes where they are asked for (or left to
+    // the library), the pass is one fused kernel and its whole grid is
+    // resident at once; else the CUDA graph's while-loop (or the host loop)
+    int loop = req.loop;
+    if (loop == PR_LOOP_AUTO || loop == PR_LOOP_PERSISTENT) {
+        loop = PR_LOOP_GRAPH;
+        if (!split) {
+            int op = 0;
+            if ((s = persist_setup(prec1, W, &op)) != PR_OK) return s;
+            if (mixed) {
+                int op2 = 0;
+                if ((s = persist_setup(PR_PREC_DF64, W, &op2)) != PR_OK) return s;
+                op = std::min(op, op2);
+            }
+            if (op > 0 && total_ctas <= sms * op) loop = PR_LOOP_PERSISTENT;
+        }
+    }
     // ---- phase 1 (or the only phase)
     s = run_phase(prec1, W, split, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, off_gctajob, total_gctas,
-                  pass_cap, req.loop, st, stats);
+                  pass_cap, loop, req.persist_wait_us, st, stats);
     if (s != PR_OK) return s;
     // ---- mixed precision: refinement phase in DF64 from the FP32 iterates
     if (mixed) {
@@ -885,7 +987,7 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             PR_CUDA(cudaMemcpyAsync(ar.at<JobDev>(off_jobs), hjobs.data(), hjobs.size() * sizeof(JobDev),
                                     cudaMemcpyHostToDevice, st));
             s = run_phase(PR_PREC_DF64, W, split, jobs, ar, off_jobs, off_glob, off_ctajob, total_ctas, off_gctajob,
-                          total_gctas, pass_cap, req.loop, st, stats);
+                          total_gctas, pass_cap, loop, req.persist_wait_us, st, stats);
             if (s != PR_OK) return s;
         }
     }

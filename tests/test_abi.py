@@ -98,6 +98,9 @@ def test_solve_rejects_bad_handles_and_arguments(L):
     o = binding.default_options()
     o.kernels = 3
     assert L.pr_solve_batch(None, 0, C.byref(o)) == 1 and b"kernels" in L.pr_last_error()
+    o = binding.default_options()
+    o.loop = 4
+    assert L.pr_solve_batch(None, 0, C.byref(o)) == 1 and b"loop" in L.pr_last_error()
     assert L.pr_solve_batch(None, -1, None) == 1
 
 
@@ -105,7 +108,7 @@ def test_options_defaults(L):
     from paper_2108_02997_gb300 import binding
     o = binding.default_options()
     assert o.precision == binding.PR_PREC_DF64 and o.switch_tol == 1e-6 and o.share_trajectories == 1
-    assert o.loop == binding.PR_LOOP_GRAPH and o.init == binding.PR_INIT_UNIFORM
+    assert o.loop == binding.PR_LOOP_AUTO and o.init == binding.PR_INIT_UNIFORM
     assert o.group == binding.PR_GROUP_AUTO and o.max_passes == 0
 
 
