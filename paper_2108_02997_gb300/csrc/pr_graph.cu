@@ -39,24 +39,18 @@ pr_status dalloc(T **p, size_t count) {
 
 void free_tables(pr_graph *g) {
     for (auto &t : g->tables) {
-        cudaFree(t.d_tiles);
-        cudaFree(t.d_slot_base);
+        cudaFree(t.d_mem);
         t = TileTable();
     }
     for (auto &t : g->hub_tables) {
-        cudaFree(t.d_tiles);
-        cudaFree(t.d_slot_base);
+        cudaFree(t.d_mem);
         t = TileTable();
     }
 }
 
 void free_graph(pr_graph *g) {
     if (!g) return;
-    cudaFree(g->d_off);
-    cudaFree(g->d_src);
-    cudaFree(g->d_outdeg);
-    cudaFree(g->d_perm);
-    cudaFree(g->d_inv);
+    cudaFree(g->d_mem);
     free_tables(g);
     g->magic = 0;
     delete g;
@@ -252,10 +246,14 @@ pr_status build_tile_table(pr_graph *g, int W, int TE, int TR, int CH, TileTable
     nt.n_long = (int32_t)tot[2];
     // every row adds its in-edges and a fixed per-row cost, W columns each
     nt.work = ((double)g->nnz + 4.0 * (double)g->n) * W;
-    pr_status s = dalloc(&nt.d_tiles, (size_t)nt.ntiles);
+    // tiles and long-row slot bases in one allocation
+    const size_t tiles_bytes = ((sizeof(Tile) * (size_t)std::max(nt.ntiles, 1)) + 255) & ~size_t(255);
+    unsigned char *mem = nullptr;
+    pr_status s = dalloc(&mem, tiles_bytes + sizeof(int32_t) * (size_t)std::max(nt.n_long, 1));
     if (s != PR_OK) return s;
-    s = dalloc(&nt.d_slot_base, (size_t)nt.n_long);
-    if (s != PR_OK) { cudaFree(nt.d_tiles); return s; }
+    nt.d_mem = mem;
+    nt.d_tiles = reinterpret_cast<Tile *>(mem);
+    nt.d_slot_base = reinterpret_cast<int32_t *>(mem + tiles_bytes);
     e = cudaMemcpy(d_base.p, base.data(), sizeof(int64_t) * (size_t)nseg * 3, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nseg > 0) {
         tile_segments_kernel<true><<<blocks, 128>>>(static_cast<const TileSeg *>(d_segs.p), nseg, g->d_off, TE, TR, CH,
@@ -265,8 +263,7 @@ pr_status build_tile_table(pr_graph *g, int W, int TE, int TR, int CH, TileTable
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
-        cudaFree(nt.d_tiles);
-        cudaFree(nt.d_slot_base);
+        cudaFree(nt.d_mem);
         return pr_cuda_fail(e, "tile table (write)");
     }
     t = nt;
@@ -618,12 +615,23 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     g->nnz = nnz;
     g->n_dangling = n_dangling;
     cudaGetDevice(&g->device);
+    // the graph's five arrays in one allocation (256-byte aligned sections)
     pr_status s;
-    if ((s = dalloc(&g->d_off, n_off)) != PR_OK || (s = dalloc(&g->d_src, n_src)) != PR_OK ||
-        (s = dalloc(&g->d_outdeg, n_od)) != PR_OK || (s = dalloc(&g->d_perm, (size_t)n)) != PR_OK ||
-        (s = dalloc(&g->d_inv, (size_t)n)) != PR_OK) {
-        free_graph(g);
-        return s;
+    {
+        auto sec = [](size_t count) { return (sizeof(int32_t) * count + 255) & ~size_t(255); };
+        const size_t o_src = sec(n_off), o_od = o_src + sec(n_src), o_perm = o_od + sec(n_od),
+                     o_inv = o_perm + sec((size_t)n), total = o_inv + sec((size_t)n);
+        unsigned char *mem = nullptr;
+        if ((s = dalloc(&mem, total)) != PR_OK) {
+            free_graph(g);
+            return s;
+        }
+        g->d_mem = mem;
+        g->d_off = reinterpret_cast<int32_t *>(mem);
+        g->d_src = reinterpret_cast<int32_t *>(mem + o_src);
+        g->d_outdeg = reinterpret_cast<int32_t *>(mem + o_od);
+        g->d_perm = reinterpret_cast<int32_t *>(mem + o_perm);
+        g->d_inv = reinterpret_cast<int32_t *>(mem + o_inv);
     }
     e = d_old_off.alloc(sizeof(int32_t) * ((size_t)n + 1));
     if (e == cudaSuccess) e = d_old_src.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1));
@@ -667,20 +675,22 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     const int32_t nchunks = (int32_t)(((int64_t)n + kSortChunk - 1) / kSortChunk);
     const int64_t mlen = (int64_t)kKeys * nchunks;
     const int64_t nsums = std::max<int64_t>((mlen + kScanTile - 1) / kScanTile, ((int64_t)n + kScanTile - 1) / kScanTile);
-    DevTmp d_key, d_M, d_Ms, d_sums, d_cmax, d_starts, d_newdeg;
+    // class starts, largest in-degrees and new-offset bounds share one block
+    // (one read-back)
+    DevTmp d_key, d_M, d_Ms, d_sums, d_meta, d_newdeg;
     e = d_key.alloc(sizeof(int32_t) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMalloc(&d_M.p, sizeof(int32_t) * (size_t)mlen);
-    if (e == cudaSuccess) e = cudaMalloc(&d_Ms.p, sizeof(int32_t) * (size_t)mlen);
+    if (e == cudaSuccess) e = d_M.alloc(sizeof(int32_t) * (size_t)mlen);
+    if (e == cudaSuccess) e = d_Ms.alloc(sizeof(int32_t) * (size_t)mlen);
     if (e == cudaSuccess) e = d_sums.alloc(sizeof(int32_t) * (size_t)nsums);
-    if (e == cudaSuccess) e = d_cmax.alloc(sizeof(int32_t) * kClasses);
-    if (e == cudaSuccess) e = d_starts.alloc(sizeof(int32_t) * kClasses);
+    if (e == cudaSuccess) e = d_meta.alloc(sizeof(int32_t) * (3 * kClasses + 1));
     if (e == cudaSuccess) e = d_newdeg.alloc(sizeof(int32_t) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMemset(d_cmax.p, 0, sizeof(int32_t) * kClasses);
+    int32_t *m_starts = static_cast<int32_t *>(d_meta.p), *m_cmax = m_starts + kClasses, *m_bound = m_cmax + kClasses;
+    if (e == cudaSuccess) e = cudaMemset(m_cmax, 0, sizeof(int32_t) * kClasses);
     if (e == cudaSuccess) e = cudaMemset(g->d_off, 0, sizeof(int32_t) * n_off);
     if (e == cudaSuccess) e = cudaMemset(g->d_src, 0, sizeof(int32_t) * n_src);
     if (e == cudaSuccess) e = cudaMemset(g->d_outdeg, 0, sizeof(int32_t) * n_od);
     int32_t *key = static_cast<int32_t *>(d_key.p), *M = static_cast<int32_t *>(d_M.p), *Ms = static_cast<int32_t *>(d_Ms.p);
-    int32_t *sums = static_cast<int32_t *>(d_sums.p), *cmax = static_cast<int32_t *>(d_cmax.p);
+    int32_t *sums = static_cast<int32_t *>(d_sums.p), *cmax = m_cmax;
     if (e == cudaSuccess) {
         class_keys_kernel<<<blocks_for(n, 256), 256>>>(old_off, old_od, n, key, cmax);
         chunk_hist_kernel<<<nchunks, kSortThreads>>>(key, n, nchunks, M);
@@ -694,22 +704,16 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
     }
     if (e == cudaSuccess) {
         const int32_t total = (int32_t)nnz;
-        class_starts_kernel<<<1, 64>>>(Ms, nchunks, static_cast<int32_t *>(d_starts.p));
+        class_starts_kernel<<<1, 64>>>(Ms, nchunks, m_starts);
         e = cudaMemcpy(g->d_off + n, &total, sizeof(int32_t), cudaMemcpyHostToDevice);
     }
     // the new offsets at the class starts (and at n), for the signature
-    int32_t h_starts[kClasses], h_cmax[kClasses], h_bound[kClasses + 1];
-    DevTmp d_bound;
+    int32_t h_meta[3 * kClasses + 1];
+    const int32_t *h_starts = h_meta, *h_cmax = h_meta + kClasses, *h_bound = h_meta + 2 * kClasses;
     if (e == cudaSuccess) {
-        e = d_bound.alloc(sizeof(h_bound));
-        if (e == cudaSuccess) {
-            class_bounds_kernel<<<1, 64>>>(g->d_off, static_cast<const int32_t *>(d_starts.p), n,
-                                           static_cast<int32_t *>(d_bound.p));
-            e = cudaMemcpy(h_bound, d_bound.p, sizeof(h_bound), cudaMemcpyDeviceToHost);
-        }
+        class_bounds_kernel<<<1, 64>>>(g->d_off, m_starts, n, m_bound);
+        e = cudaMemcpy(h_meta, d_meta.p, sizeof(h_meta), cudaMemcpyDeviceToHost);
     }
-    if (e == cudaSuccess) e = cudaMemcpy(h_starts, d_starts.p, sizeof(h_starts), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(h_cmax, d_cmax.p, sizeof(h_cmax), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && nnz > 0) {
         // rows in the new order: 1024+ in-edges (classes 11 and up), then
         // 32..1023 (classes 6..10), then the rest

@@ -18,6 +18,7 @@ struct pr_graph {
     int64_t nnz;
     int32_t n_dangling;
     int32_t device;
+    void *d_mem = nullptr;           // one device allocation holding the five arrays below
     int32_t *d_off = nullptr;        // n+1 (padded for 16-byte bulk copies)
     int32_t *d_src = nullptr;        // nnz (padded)
     int32_t *d_outdeg = nullptr;     // n (padded)
