@@ -23,14 +23,18 @@
  *     memory of the current device. Which one an argument is, is stated per
  *     argument.
  *   - Device memory. A graph's arrays are allocated by pr_graph_create and
- *     freed by pr_graph_destroy. Everything else (solve and training
- *     workspaces, graph-creation scratch) comes from one stream-ordered
- *     memory pool per device (cudaMallocFromPoolAsync on the call's stream,
- *     cudaFreeAsync before the call returns; cudaMalloc only if the pool
- *     cannot serve a request). The pool keeps up to 4 GiB of freed memory
- *     reserved between calls so that repeated calls do not pay the
- *     synchronising cudaMalloc/cudaFree; pr_workspace_info reports what it
- *     holds and pr_workspace_release returns the unused part to the device.
+ *     freed by pr_graph_destroy, from a stream-ordered memory pool of their
+ *     own per device (graph pool). Everything else (solve and training
+ *     workspaces, graph-creation scratch) comes from a second stream-ordered
+ *     memory pool per device, the workspace pool (cudaMallocFromPoolAsync on
+ *     the call's stream, cudaFreeAsync before the call returns). Either falls
+ *     back to cudaMalloc only if its pool cannot serve a request. Each pool
+ *     keeps up to 16 GiB of freed memory reserved so that repeated calls and
+ *     graphs do not pay the synchronising cudaMalloc/cudaFree and the page
+ *     mapping behind them; pr_workspace_info reports what the workspace pool
+ *     holds and pr_workspace_release returns the unused part of both pools
+ *     to the device. pr_graph_destroy waits for the device before it returns
+ *     a graph's memory.
  *     pr_solve_noalloc allocates nothing (see there).
  *   - Per-device set-up (kernel attributes, residencies, the tuning table,
  *     the no-alloc array's address) is done once per device and process; the

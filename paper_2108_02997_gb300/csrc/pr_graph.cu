@@ -21,36 +21,20 @@
 
 namespace {
 
-template <typename T>
-pr_status dalloc(T **p, size_t count) {
-    *p = nullptr;
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        if (e == cudaErrorMemoryAllocation) {
-            cudaGetLastError();
-            return pr_fail(PR_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
-        }
-        return pr_cuda_fail(e, "cudaMalloc");
-    }
-    return PR_OK;
-}
-
 void free_tables(pr_graph *g) {
     for (auto &t : g->tables) {
-        cudaFree(t.d_mem);
+        pr_graph_free(t.d_mem, t.d_mem_pooled);
         t = TileTable();
     }
     for (auto &t : g->hub_tables) {
-        cudaFree(t.d_mem);
+        pr_graph_free(t.d_mem, t.d_mem_pooled);
         t = TileTable();
     }
 }
 
 void free_graph(pr_graph *g) {
     if (!g) return;
-    cudaFree(g->d_mem);
+    pr_graph_free(g->d_mem, g->d_mem_pooled);
     free_tables(g);
     g->magic = 0;
     delete g;
@@ -248,10 +232,13 @@ pr_status build_tile_table(pr_graph *g, int W, int TE, int TR, int CH, TileTable
     nt.work = ((double)g->nnz + 4.0 * (double)g->n) * W;
     // tiles and long-row slot bases in one allocation
     const size_t tiles_bytes = ((sizeof(Tile) * (size_t)std::max(nt.ntiles, 1)) + 255) & ~size_t(255);
-    unsigned char *mem = nullptr;
-    pr_status s = dalloc(&mem, tiles_bytes + sizeof(int32_t) * (size_t)std::max(nt.n_long, 1));
+    void *vmem = nullptr;
+    bool pooled = false;
+    pr_status s = pr_graph_alloc(&vmem, tiles_bytes + sizeof(int32_t) * (size_t)std::max(nt.n_long, 1), &pooled);
     if (s != PR_OK) return s;
+    unsigned char *mem = static_cast<unsigned char *>(vmem);
     nt.d_mem = mem;
+    nt.d_mem_pooled = pooled;
     nt.d_tiles = reinterpret_cast<Tile *>(mem);
     nt.d_slot_base = reinterpret_cast<int32_t *>(mem + tiles_bytes);
     e = cudaMemcpy(d_base.p, base.data(), sizeof(int64_t) * (size_t)nseg * 3, cudaMemcpyHostToDevice);
@@ -263,7 +250,7 @@ pr_status build_tile_table(pr_graph *g, int W, int TE, int TR, int CH, TileTable
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
-        cudaFree(nt.d_mem);
+        pr_graph_free(nt.d_mem, nt.d_mem_pooled);
         return pr_cuda_fail(e, "tile table (write)");
     }
     t = nt;
@@ -621,11 +608,12 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t nnz, const int32_t *in_o
         auto sec = [](size_t count) { return (sizeof(int32_t) * count + 255) & ~size_t(255); };
         const size_t o_src = sec(n_off), o_od = o_src + sec(n_src), o_perm = o_od + sec(n_od),
                      o_inv = o_perm + sec((size_t)n), total = o_inv + sec((size_t)n);
-        unsigned char *mem = nullptr;
-        if ((s = dalloc(&mem, total)) != PR_OK) {
+        void *vmem = nullptr;
+        if ((s = pr_graph_alloc(&vmem, total, &g->d_mem_pooled)) != PR_OK) {
             free_graph(g);
             return s;
         }
+        unsigned char *mem = static_cast<unsigned char *>(vmem);
         g->d_mem = mem;
         g->d_off = reinterpret_cast<int32_t *>(mem);
         g->d_src = reinterpret_cast<int32_t *>(mem + o_src);

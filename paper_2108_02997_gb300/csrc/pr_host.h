@@ -19,6 +19,7 @@ struct pr_graph {
     int32_t n_dangling;
     int32_t device;
     void *d_mem = nullptr;           // one device allocation holding the five arrays below
+    bool d_mem_pooled = false;       //   from the graph pool (else cudaMalloc)
     int32_t *d_off = nullptr;        // n+1 (padded for 16-byte bulk copies)
     int32_t *d_src = nullptr;        // nnz (padded)
     int32_t *d_outdeg = nullptr;     // n (padded)
@@ -129,6 +130,11 @@ pr_status pr_kernel_setup(int precision, int W, int *blocks_per_sm);
 // CTAs a job of ntiles warp tiles is given in a fused pass (at most one per
 // kMinTilesPerWarp tiles of each warp).
 int tile_ctas(int32_t ntiles);
+
+// Graph arrays from the per-device graph pool (pr_solve.cu); pr_graph_free
+// waits for the device, as cudaFree does, before returning them.
+pr_status pr_graph_alloc(void **p, size_t bytes, bool *pooled);
+void pr_graph_free(void *p, bool pooled);
 
 // Stream-ordered device buffer from the per-device workspace pool
 // (pr_solve.cu): released with cudaFreeAsync on the stream it was taken on,

@@ -174,6 +174,7 @@ struct Tile {
 struct TileTable {
     int W = 0;                   // column width this table was built for
     void *d_mem = nullptr;       // one device allocation holding d_tiles and d_slot_base
+    bool d_mem_pooled = false;   //   from the graph pool (else cudaMalloc)
     Tile *d_tiles = nullptr;
     int32_t ntiles = 0;
     int32_t n_long = 0;          // rows split into more than one chunk

@@ -166,7 +166,7 @@ def test_header_describes_the_workspace_pool_and_its_release():
     pr_workspace_release), and the no-alloc entry point's limits."""
     text = (ROOT / "include" / "pagerank.h").read_text()
     conv = text[:text.index("#ifndef PAGERANK_H")]
-    assert "stream-ordered" in conv and "4 GiB" in conv
+    assert "stream-ordered" in conv and "16 GiB" in conv and "graph pool" in conv
     assert "pr_workspace_info" in conv and "pr_workspace_release" in conv
     assert "cudaMalloc with cudaMalloc" not in conv and "releases it\n *     before returning" not in conv
     noalloc = text[text.index("pr_solve_noalloc —"):text.index("pr_status pr_solve_noalloc(")]
