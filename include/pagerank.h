@@ -138,14 +138,18 @@ typedef enum pr_loop {
                              of the stop flag after each (the plain per-instance
                              baseline; also used to time single launches) */
     PR_LOOP_PERSISTENT = 2, /* every iteration pass in one cooperative launch:
-                             the CTAs stay resident and wait, on a device
-                             counter, for each pass's stop decision (no launch
-                             between passes). Used where a pass is one fused
-                             kernel and its whole grid fits on the device at
-                             once; otherwise the solve runs as PR_LOOP_GRAPH.
-                             Each wait is bounded (2 s of device time): a wait
-                             that runs out ends the solve with PR_ETIMEOUT and
-                             leaves the context usable */
+                             the CTAs stay resident; at the end of a pass each
+                             CTA waits, on its job's device counter, for the
+                             job's other CTAs, and takes the job's stop
+                             decision itself from all their partials (no
+                             launch between passes, no CTA deciding for the
+                             others). Used where a pass is one fused kernel,
+                             its whole grid fits on the device at once and no
+                             job has more than 256 stopping rules; otherwise
+                             the solve runs as PR_LOOP_GRAPH. Each wait is
+                             bounded (2 s of device time): a wait that runs
+                             out ends the solve with PR_ETIMEOUT and leaves
+                             the context usable */
     PR_LOOP_AUTO = 3      /* default: PR_LOOP_PERSISTENT where it applies, else
                              PR_LOOP_GRAPH */
 } pr_loop;
@@ -220,9 +224,9 @@ typedef struct pr_options {
                                    the context stays usable); 0 (default) =
                                    the largest max_iter + 3 */
     int32_t kernels;            /* pr_kernels; default PR_KERNELS_AUTO */
-    int32_t persist_wait_us;    /* PR_LOOP_PERSISTENT: bound of one wait for a
-                                   pass's decision, microseconds; 0 (default)
-                                   = 2,000,000 */
+    int32_t persist_wait_us;    /* PR_LOOP_PERSISTENT: bound of one wait for the
+                                   other CTAs of a job, microseconds; 0
+                                   (default) = 2,000,000 */
     int32_t reserved[4];        /* zero */
 } pr_options;
 
@@ -513,10 +517,10 @@ pr_status pr_last_solve_loops(int32_t *graph_phases, int32_t *host_phases, int32
 
 /*
  * Test hook for the bounded waits of persistent passes: while `on` is nonzero,
- * solves that run persistent passes never release a pass's decision, so every
- * CTA's wait runs out after persist_wait_us and the solve returns PR_ETIMEOUT
- * (no GPU fault is involved; the context stays usable). Process-wide; always
- * PR_OK.
+ * the CTAs of solves that run persistent passes never announce the end of
+ * their pass, so every CTA's wait for its job's other CTAs runs out after
+ * persist_wait_us and the solve returns PR_ETIMEOUT (no GPU fault is
+ * involved; the context stays usable). Process-wide; always PR_OK.
  */
 pr_status pr_test_hold_decisions(int32_t on);
 

@@ -399,8 +399,9 @@ def pr_solve_batch(insts, *, precision="df64", init=None, loop="auto", stream=No
 
 
 def hold_decisions(on: bool) -> None:
-    """Test hook (pr_test_hold_decisions): while on, persistent passes never
-    release a decision, so their bounded waits run out (PR_ETIMEOUT)."""
+    """Test hook (pr_test_hold_decisions): while on, the CTAs of persistent
+    passes never announce the end of a pass, so their bounded waits run out
+    (PR_ETIMEOUT)."""
     _check(lib().pr_test_hold_decisions(1 if on else 0), "pr_test_hold_decisions")
 
 

@@ -106,8 +106,8 @@ struct SolveRequest {
     SolveStats stats;       // out
 };
 
-// Test hook: while set, persistent passes never release a decision, so that
-// every wait runs out (pr_test_hold_decisions).
+// Test hook: while set, the CTAs of persistent passes never announce the end
+// of a pass, so that every wait runs out (pr_test_hold_decisions).
 bool pr_hold_decisions();
 
 pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out);

@@ -268,17 +268,17 @@ struct GlobalDev {
     int32_t pass_cap;         // hard cap on body executions
     int32_t alive;            // set by the last job to finish a pass
     int32_t error;            // nonzero: a device-side check failed
-    int32_t hold;             // persistent passes, test hook: decisions are never released
+    int32_t hold;             // persistent passes, test hook: CTAs never announce the end of a pass
     unsigned long long cond;  // cudaGraphConditionalHandle (0 in host-loop mode)
     uint32_t body_count;      // iteration launches started (independent loop guard)
-    uint32_t wait_us;         // persistent passes: bound of one wait for a decision (0: kPersistWaitNs)
+    uint32_t wait_us;         // persistent passes: bound of one wait for the job's CTAs (0: kPersistWaitNs)
 };
 
 // Error codes a kernel can leave in GlobalDev::error.
 enum DeviceError { kErrNone = 0, kErrPassCap = 2, kErrLoopGuard = 3, kErrWait = 4 };
 
-// Persistent passes: the longest a CTA waits for a pass's decision (global
-// timer nanoseconds) before it records kErrWait and stops.
+// Persistent passes: the longest a CTA waits for the other CTAs of its job
+// (global timer nanoseconds) before it records kErrWait and stops.
 #ifndef PR_PERSIST_WAIT_NS
 #define PR_PERSIST_WAIT_NS 2000000000ull
 #endif

@@ -59,14 +59,11 @@ template <> __device__ __forceinline__ df64 ld_cg_v<df64>(const df64 *p) {
     return {f.x, f.y};
 }
 
-// Pass counter hand-over of persistent passes (gpu-scope acquire / release).
-__device__ __forceinline__ int32_t ld_acquire_gpu(const int32_t *p) {
-    int32_t v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+// Arrival counters of persistent passes (gpu-scope acquire loads).
+__device__ __forceinline__ uint32_t ld_acquire_gpu_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
-}
-__device__ __forceinline__ void st_release_gpu(int32_t *p, int32_t v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -131,16 +128,17 @@ struct ColView {
     double *copy_dst;
 };
 
+// cs: the column's state (null when the thread's column is past the job's)
 template <typename V>
-__device__ __forceinline__ ColView<V> col_view(const JobDev &job, int col) {
+__device__ __forceinline__ ColView<V> col_view_cs(const JobDev &job, const ColState *csp) {
     ColView<V> cv;
-    cv.has = col < job.ncols;
+    cv.has = csp != nullptr;
     cv.active = false;
     cv.copy_dst = nullptr;
     cv.r_prev = cv.c_prev = nullptr;
     cv.r_new = cv.c_new = nullptr;
     if (cv.has) {
-        const ColState &cs = job.cols[col];
+        const ColState &cs = *csp;
         const int cur = cs.cur;
         cv.active = cs.active;
         cv.alpha = load_raw<V>(cs.v_alpha);
@@ -152,6 +150,10 @@ __device__ __forceinline__ ColView<V> col_view(const JobDev &job, int col) {
         cv.copy_dst = cs.copy_dst;
     }
     return cv;
+}
+template <typename V>
+__device__ __forceinline__ ColView<V> col_view(const JobDev &job, int col) {
+    return col_view_cs<V>(job, col < job.ncols ? &job.cols[col] : nullptr);
 }
 
 // New rank of row v in the thread's column: norms, contribution or dangling
@@ -203,46 +205,81 @@ __device__ __forceinline__ void row_update(const int32_t *__restrict__ outdeg, c
 // ---------------------------------------------------------------- pass bookkeeping
 // CTA partials of the thread accumulators, then the job finalizer (last CTA of
 // the job) and the global decision (last job). Shared by both kernels.
-// kPersist (persistent passes): every store of the CTA's pass is made visible
-// at gpu scope before it arrives, since the job's CTAs read the new
-// contributions in the next pass of the same launch, and the pass counter is
-// released after the decision it announces.
-template <typename V, int W, bool kPersist = false>
-__device__ __noinline__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V> &acc, int local, int mode) {
+// The CTA's partials of the thread accumulators (L1, sum of squares, Linf,
+// dangling sum, sum of ranks per column, in a fixed order over warps) written
+// to dst[c * kPartials + k]; the writers fence them for the CTA that reads them.
+template <typename V, int W>
+__device__ __forceinline__ void cta_partials(RowAcc<V> &acc, double *dst) {
     using N = Num<V>;
     using Acc = typename N::Acc;
     const int tid = threadIdx.x;
     const int col = tid % W;
     __shared__ Acc s_red[kWarps][W][kPartials];
-    __shared__ int s_flag;
-    __shared__ double s_fin[W * kPartials];
-    {
-        Acc a[kPartials] = {acc.l1, acc.l2, acc.linf, acc.dsum, acc.rsum};
-        for (int m = W; m < 32; m <<= 1) {
+    Acc a[kPartials] = {acc.l1, acc.l2, acc.linf, acc.dsum, acc.rsum};
+    for (int m = W; m < 32; m <<= 1) {
 #pragma unroll
-            for (int k = 0; k < kPartials; k++) {
-                Acc o = N::acc_shfl_xor(a[k], m);
-                a[k] = (k == 2) ? N::acc_max(a[k], o) : N::acc_add(a[k], o);
-            }
-        }
-        if ((tid & 31) < W) {
-#pragma unroll
-            for (int k = 0; k < kPartials; k++) s_red[tid >> 5][col][k] = a[k];
-        }
-        __syncthreads();
-        if (tid < W * kPartials) {
-            const int c = tid / kPartials, k = tid % kPartials;
-            Acc t = s_red[0][c][k];
-            for (int w = 1; w < kWarps; w++) t = (k == 2) ? N::acc_max(t, s_red[w][c][k]) : N::acc_add(t, s_red[w][c][k]);
-            job.cta_part[((size_t)local * W + c) * kPartials + k] = N::acc_to_double(t);
-            // only the partials are read by another CTA of this launch (the
-            // job's last); the other stores need not drain before arriving
-            __threadfence();
+        for (int k = 0; k < kPartials; k++) {
+            Acc o = N::acc_shfl_xor(a[k], m);
+            a[k] = (k == 2) ? N::acc_max(a[k], o) : N::acc_add(a[k], o);
         }
     }
+    if ((tid & 31) < W) {
+#pragma unroll
+        for (int k = 0; k < kPartials; k++) s_red[tid >> 5][col][k] = a[k];
+    }
     __syncthreads();
+    if (tid < W * kPartials) {
+        const int c = tid / kPartials, k = tid % kPartials;
+        Acc t = s_red[0][c][k];
+        for (int w = 1; w < kWarps; w++) t = (k == 2) ? N::acc_max(t, s_red[w][c][k]) : N::acc_add(t, s_red[w][c][k]);
+        dst[c * kPartials + k] = N::acc_to_double(t);
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Fixed-order FP64 reduction of a job's CTA partials (cta_count x W x
+// kPartials) into s_fin: partial p by warp p mod kWarps, lane l adding CTAs
+// l, l + 32, ... (four loads in flight), then a fixed butterfly over the
+// lanes; short dependent chains, since every FP64 operation on this GPU has a
+// long latency. Every caller gets the same bits from the same partials.
+template <int W>
+__device__ __forceinline__ void reduce_partials(const double *cta_part, int cta_count, double *s_fin) {
+    constexpr int P = W * kPartials;
+    const int tid = threadIdx.x;
+    const int rl = tid & 31, rw = tid >> 5;
+    for (int p = rw; p < P; p += kWarps) {
+        const bool is_max = (p % kPartials) == 2;
+        double t = 0.0;
+        for (int c = rl; c < cta_count; c += 4 * 32) {
+            double x[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                x[u] = c + 32 * u < cta_count ? ld_cg(cta_part + (size_t)(c + 32 * u) * P + p) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (c + 32 * u < cta_count) t = is_max ? fmax(t, x[u]) : t + x[u];
+        }
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) {
+            const double o = __shfl_xor_sync(0xffffffffu, t, m);
+            t = is_max ? fmax(t, o) : t + o;
+        }
+        if (rl == 0) s_fin[p] = t;
+    }
+    __syncthreads();
+}
+
+template <typename V, int W>
+__device__ __noinline__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *glob, RowAcc<V> &acc, int local, int mode) {
+    using N = Num<V>;
+    const int tid = threadIdx.x;
+    __shared__ int s_flag;
+    __shared__ double s_fin[W * kPartials];
+    // only the partials are read by another CTA of this launch (the job's
+    // last); the other stores need not drain before arriving
+    cta_partials<V, W>(acc, job.cta_part + (size_t)local * W * kPartials);
     if (tid == 0) {
-        if constexpr (kPersist) __threadfence();
         unsigned int old = atomicAdd(&job.arrive, 1u);
         s_flag = (old == (unsigned int)(job.cta_count - 1));
     }
@@ -266,34 +303,7 @@ __device__ __noinline__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *g
     ColState *const cols = job.cols;
     Tap *const taps = job.taps;
     const double *const cta_part = job.cta_part;
-    // fixed-order FP64 reduction over the job's CTAs: partial p by warp
-    // p mod kWarps, lane l adding CTAs l, l + 32, ... (four loads in flight),
-    // then a fixed butterfly over the lanes; short dependent chains, since
-    // every FP64 operation on this GPU has a long latency
-    {
-        constexpr int P = W * kPartials;
-        const int rl = tid & 31, rw = tid >> 5;
-        for (int p = rw; p < P; p += kWarps) {
-            const bool is_max = (p % kPartials) == 2;
-            double t = 0.0;
-            for (int c = rl; c < cta_count; c += 4 * 32) {
-                double x[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    x[u] = c + 32 * u < cta_count ? ld_cg(cta_part + (size_t)(c + 32 * u) * P + p) : 0.0;
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (c + 32 * u < cta_count) t = is_max ? fmax(t, x[u]) : t + x[u];
-            }
-#pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) {
-                const double o = __shfl_xor_sync(0xffffffffu, t, m);
-                t = is_max ? fmax(t, o) : t + o;
-            }
-            if (rl == 0) s_fin[p] = t;
-        }
-        __syncthreads();
-    }
+    reduce_partials<W>(cta_part, cta_count, s_fin);
     // ---- column decisions: one warp per column, its lanes over the column's
     // stopping rules (taps, in order); the column state is staged in shared memory
     static_assert(sizeof(ColState) % 8 == 0, "ColState is copied in 8-byte words");
@@ -422,12 +432,7 @@ __device__ __noinline__ void finish_pass(JobDev *jobs, JobDev &job, GlobalDev *g
                     any = 0;
                 }
                 glob->alive = any;
-                if constexpr (kPersist) {
-                    __threadfence();
-                    if (!*(volatile int32_t *)&glob->hold) st_release_gpu(&glob->pass, g_pass + 1);
-                } else {
-                    glob->pass = g_pass + 1;
-                }
+                glob->pass = g_pass + 1;
                 if (!any && glob->cond) cudaGraphSetConditional((cudaGraphConditionalHandle)glob->cond, 0u);
             } else {
                 glob->alive = any;
@@ -478,35 +483,234 @@ __global__ void __launch_bounds__(kBlock) pr_init_kernel(JobDev *jobs, GlobalDev
 }
 
 // ---------------------------------------------------------------- persistent passes
-// The CTA waits until the decision of pass `pass` (the pass counter moves on)
-// and returns whether another pass runs. Thread 0 polls with a gpu-scope
-// acquire; the CTA barrier then orders every thread's next reads after the
-// stores the decision published. The wait is bounded: after `limit_ns` of the
-// global timer the CTA records kErrWait and stops, and every CTA that reads
-// the error stops too, so a broken hand-over ends the launch with an error the
-// host reports instead of hanging.
-static __device__ __noinline__ bool persist_wait(GlobalDev *glob, int32_t pass, unsigned long long limit_ns) {
-    __shared__ int s_go;
-    if (threadIdx.x == 0) {
-        int go = 0;
+// Every iteration pass of a job in one cooperative launch. Each CTA keeps a
+// copy of the job's column states and stopping rules in shared memory and, at
+// the end of a pass, takes the job's decisions itself: it publishes its
+// partials, arrives on the job's counter, waits until all the job's CTAs have
+// arrived, reduces all partials in the same fixed order as the job finalizer
+// of the other loops, and applies the same stopping rules to its copy. Every
+// CTA of the job therefore computes the same bits, no CTA waits for another to
+// decide, and jobs do not wait for one another. The job's first CTA (the
+// writer) also stores what the host reads back: fired rules, histories, and
+// the column states when the job ends.
+constexpr int kPersistTaps = 256;   // stopping rules per job that persistent passes hold in shared memory
+
+struct PersistTap {
+    double tau;
+    double *out;
+    int32_t norm, max_iter;
+};
+template <int W>
+struct PersistState {
+    ColState cols[W];
+    PersistTap taps[kPersistTaps];
+    uint32_t fired[kPersistTaps / 32];
+    int32_t alive, cur, go, pad;
+};
+struct NoPersistState {
+    int32_t unused;
+};
+template <int W, bool P>
+struct PersistSel {
+    using type = NoPersistState;
+};
+template <int W>
+struct PersistSel<W, true> {
+    using type = PersistState<W>;
+};
+
+// The job's state into shared memory, once per launch (all threads).
+template <int W>
+__device__ __forceinline__ void persist_load(const JobDev &job, PersistState<W> &ps) {
+    static_assert(sizeof(ColState) % 8 == 0, "ColState is copied in 8-byte words");
+    constexpr int kCsWords = (int)(sizeof(ColState) / 8);
+    const int tid = threadIdx.x;
+    const int ncols = min(job.ncols, W);
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(job.cols);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(ps.cols);
+    for (int i = tid; i < ncols * kCsWords; i += kBlock) dst[i] = src[i];
+    __syncthreads();
+    int ntaps = 0;
+    for (int c = 0; c < ncols; c++) ntaps = max(ntaps, ps.cols[c].tap_end);
+    ntaps = min(ntaps, kPersistTaps);   // the host admits jobs of at most kPersistTaps rules
+    for (int q = tid; q < ntaps; q += kBlock) {
+        const Tap &t = job.taps[q];
+        ps.taps[q] = PersistTap{t.tau, t.out, t.norm, t.max_iter};
+    }
+    for (int w = tid; w < kPersistTaps / 32; w += kBlock) {
+        uint32_t bits = 0;
+        for (int b = 0; b < 32; b++)
+            if (w * 32 + b < ntaps && job.taps[w * 32 + b].fired) bits |= 1u << b;
+        ps.fired[w] = bits;
+    }
+    if (tid == 0) {
+        ps.alive = job.alive;
+        ps.cur = job.cur;
+        ps.go = 1;
+    }
+    __syncthreads();
+}
+
+// End of persistent pass `pass` (counted from 0 in this launch); returns
+// whether the job runs another pass. The wait for the job's arrivals is
+// bounded: after wait_ns of the global timer the CTA records kErrWait and
+// stops, and every CTA that sees an error stops too, so that a broken
+// hand-over ends the launch with an error the host reports.
+template <typename V, int W>
+__device__ __noinline__ bool persist_pass(JobDev &job, GlobalDev *glob, RowAcc<V> &acc, int local, PersistState<W> &ps,
+                                          int32_t pass, unsigned long long wait_ns) {
+    using N = Num<V>;
+    constexpr int P = W * kPartials;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cta_count = job.cta_count, ncols = min(job.ncols, W);
+    const bool writer = local == 0;
+    // partials double-buffered by pass parity: a CTA may publish pass p + 1's
+    // while another still reads pass p's
+    double *part = job.cta_part + (size_t)(pass & 1) * cta_count * P;
+    cta_partials<V, W>(acc, part + (size_t)local * P);
+    __shared__ int s_ok;
+    if (tid == 0) {
+        // every store of this pass (iterates, contributions, partials) is
+        // visible at gpu scope before the arrival
+        __threadfence();
+        if (!*(volatile int32_t *)&glob->hold) atomicAdd(&job.arrive, 1u);
+        const uint32_t target = (uint32_t)(pass + 1) * (uint32_t)cta_count;
+        int ok = 0;
         const unsigned long long t0 = global_ns();
         for (unsigned int spin = 0;; spin++) {
-            if (ld_acquire_gpu(&glob->pass) != pass) {
-                __threadfence();
-                go = *(volatile int32_t *)&glob->alive && !*(volatile int32_t *)&glob->error;
+            if (ld_acquire_gpu_u32(&job.arrive) >= target) {
+                ok = 1;
                 break;
             }
             if (*(volatile int32_t *)&glob->error) break;
-            if ((spin & 15u) == 15u && global_ns() - t0 > limit_ns) {
+            if ((spin & 15u) == 15u && global_ns() - t0 > wait_ns) {
                 atomicCAS(&glob->error, kErrNone, kErrWait);
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
-        s_go = go;
+        __threadfence();
+        s_ok = ok;
     }
     __syncthreads();
-    return s_go != 0;
+    if (!s_ok) return false;
+    __shared__ double s_fin[P];
+    reduce_partials<W>(part, cta_count, s_fin);
+    // ---- column decisions, as in finish_pass: one warp per column, its lanes
+    // over the column's stopping rules in order
+    __shared__ int s_colalive[W];
+    Tap *const taps = job.taps;
+    for (int c = warp; c < ncols; c += kWarps) {
+        ColState &cs = ps.cols[c];
+        const double l1 = s_fin[c * kPartials + 0];
+        const double l2 = sqrt(s_fin[c * kPartials + 1]);
+        const double li = s_fin[c * kPartials + 2];
+        const double D = s_fin[c * kPartials + 3];
+        const double S = s_fin[c * kPartials + 4];
+        int col_alive = 0;
+        if (cs.active) {
+            const int it = cs.iters + 1;
+            const double errs[3] = {l1, l2, li};
+            const int tb = cs.tap_begin, te = min(cs.tap_end, kPersistTaps);
+            int primary = -1;
+            double *copy = nullptr;
+            bool pending = false;
+            for (int q0 = tb; q0 < te; q0 += 32) {
+                const int q = q0 + lane;
+                bool fires = false, pend = false;
+                double e = 0.0;
+                double *out = nullptr;
+                if (q < te) {
+                    const PersistTap tp = ps.taps[q];
+                    out = tp.out;
+                    if (!((ps.fired[q >> 5] >> (q & 31)) & 1u)) {
+                        e = errs[tp.norm - 1];
+                        if (e < tp.tau || it >= tp.max_iter) fires = true;
+                        else pend = true;
+                    }
+                    if (fires) {
+                        atomicOr(&ps.fired[q >> 5], 1u << (q & 31));
+                        if (writer) {
+                            taps[q].fired = 1;
+                            taps[q].iters = it;
+                            taps[q].err = e;
+                            taps[q].err_l1 = l1;
+                            taps[q].converged = e < tp.tau;
+                        }
+                    }
+                }
+                const unsigned int fm = __ballot_sync(0xffffffffu, fires);
+                if (__any_sync(0xffffffffu, pend)) pending = true;
+                if (fm) {
+                    const int first = __ffs(fm) - 1;
+                    double *first_out = reinterpret_cast<double *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(out), first));
+                    if (primary < 0) {
+                        primary = q0 + first;
+                        copy = first_out;
+                    }
+                    if (fires && writer) taps[q].alias_of = q == primary ? -1 : primary;
+                }
+            }
+            bool active = pending;
+            if (cs.switch_norm && !cs.switched && errs[cs.switch_norm - 1] <= cs.switch_tol) active = false;
+            col_alive = active || copy != nullptr;
+            __syncwarp();
+            if (lane == 0) {
+                cs.iters = it;
+                cs.cur ^= 1;
+                cs.last_err[0] = l1; cs.last_err[1] = l2; cs.last_err[2] = li;
+                cs.last_sum = S;
+                if (writer && cs.hist && it <= cs.hist_cap) {
+                    cs.hist[3 * (it - 1) + 0] = l1;
+                    cs.hist[3 * (it - 1) + 1] = l2;
+                    cs.hist[3 * (it - 1) + 2] = li;
+                }
+                cs.copy_dst = copy;
+                if (cs.switch_norm && !cs.switched && errs[cs.switch_norm - 1] <= cs.switch_tol)
+                    cs.switched = 1;   // hand over to the refinement phase
+                cs.active = active ? 1 : 0;
+                cs.c0 = fma(cs.c0_coef, D, cs.c0_base);
+                store_raw<V>(cs.v_c0, N::from_double(cs.c0));
+            }
+        } else {
+            __syncwarp();
+            if (lane == 0) cs.copy_dst = nullptr;
+        }
+        if (lane == 0) s_colalive[c] = col_alive;
+        __syncwarp();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int alive = 0;
+        for (int c = 0; c < ncols; c++) alive |= s_colalive[c];
+        ps.cur ^= 1;   // parity shared by the columns still active
+        if (*(volatile int32_t *)&glob->error) alive = 0;
+        if (alive && pass + 1 >= glob->pass_cap) {
+            // the same pass budget as the other loops (every CTA of the job
+            // stops here; the writer records why)
+            if (writer) atomicCAS(&glob->error, kErrNone, kErrPassCap);
+            alive = 0;
+        }
+        ps.alive = alive;
+        ps.go = alive;
+    }
+    __syncthreads();
+    if (ps.go) return true;
+    if (writer) {
+        // what the host reads back: the column states, the job's flags and
+        // the passes run (the launch's pass count is the longest job's)
+        constexpr int kCsWords = (int)(sizeof(ColState) / 8);
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(ps.cols);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(job.cols);
+        for (int i = tid; i < ncols * kCsWords; i += kBlock) dst[i] = src[i];
+        if (tid == 0) {
+            job.alive = ps.alive;
+            job.cur = ps.cur;
+            atomicMax(&glob->pass, pass + 1);
+        }
+    }
+    return false;
 }
 
 // ---------------------------------------------------------------- the iteration kernel
@@ -573,22 +777,33 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
         }
     }
     // persistent passes: the pass below repeats in this launch until the
-    // stopping decision (the CTA's tiles stay the same in every pass)
-    int32_t my_pass = 0;
+    // job's stopping decision (the CTA's tiles stay the same in every pass)
+    __shared__ typename PersistSel<W, kPersist>::type ps;
     unsigned long long wait_ns = kPersistWaitNs;
     if constexpr (kPersist) {
-        my_pass = *(volatile int32_t *)&glob->pass;
         if (glob->wait_us) wait_ns = 1000ull * glob->wait_us;
+        persist_load<W>(job, ps);
     }
-    for (;;) {
-        const ColView<V> cv = col_view<V>(job, col);
+    for (int32_t pass = 0;; pass++) {
+        ColView<V> cv;
+        if constexpr (kPersist) cv = col_view_cs<V>(job, col < job.ncols ? &ps.cols[col] : nullptr);
+        else cv = col_view<V>(job, col);
         const bool need_prev = cv.has && (cv.active || cv.copy_dst);
         RowAcc<V> acc;
         acc.init();
-        const bool work = job.alive && !*(volatile int32_t *)&glob->error;
+        bool job_alive;
+        int32_t job_cur;
+        if constexpr (kPersist) {
+            job_alive = ps.alive;
+            job_cur = ps.cur;
+        } else {
+            job_alive = job.alive;
+            job_cur = job.cur;
+        }
+        const bool work = job_alive && !*(volatile int32_t *)&glob->error;
         // several columns: the active columns read the job's shared buffer parity
         const unsigned int act_mask = __ballot_sync(0xffffffffu, cv.active);
-        const V *c_all = reinterpret_cast<const V *>(job.contrib[job.cur]);
+        const V *c_all = reinterpret_cast<const V *>(job.contrib[job_cur]);
         auto gather1 = [&](int32_t u) -> V { return cv.c_prev[(size_t)u * W + col]; };
 
         if (work) {
@@ -874,10 +1089,12 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                 }
             }
         }
-        if constexpr (!kGather) finish_pass<V, W, kPersist>(jobs, job, glob, acc, local, kPassIterate);
-        if constexpr (!kPersist) break;
-        if (!persist_wait(glob, my_pass, wait_ns)) break;
-        my_pass++;
+        if constexpr (kPersist) {
+            if (!persist_pass<V, W>(job, glob, acc, local, ps, pass, wait_ns)) break;
+        } else {
+            if constexpr (!kGather) finish_pass<V, W>(jobs, job, glob, acc, local, kPassIterate);
+            break;
+        }
     }
 }
 

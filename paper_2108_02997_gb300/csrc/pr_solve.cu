@@ -601,7 +601,7 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
         PR_CUDA(cudaMemcpyAsync(&back, d_glob, sizeof(back), cudaMemcpyDeviceToHost, st));
         PR_CUDA(cudaStreamSynchronize(st));
         stats.passes += back.pass;
-        if (back.error == kErrWait) return pr_fail(PR_ETIMEOUT, "a persistent pass waited too long for its decision");
+        if (back.error == kErrWait) return pr_fail(PR_ETIMEOUT, "a persistent pass waited too long for its job's CTAs");
         if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
     } else if (loop == PR_LOOP_HOST) {
         hg.cond = 0;
@@ -831,7 +831,8 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
             j.off_c[b] = ar.reserve((n * W + kPad) * vs_max);
         }
         j.off_cp = ar.reserve((size_t)std::max(j.tt->n_chunk_slots, 1) * W * vs_max);
-        j.off_part = ar.reserve((size_t)j.cta_count * W * kPartials * sizeof(double));
+        // two sets of CTA partials: persistent passes alternate between them
+        j.off_part = ar.reserve(2 * (size_t)j.cta_count * W * kPartials * sizeof(double));
         if (split) j.off_rowsum = ar.reserve((n * W + kPad) * vs_max);
         for (int c : j.cols) j.ntaps += (int)req.cols[c].taps.size();
         for (int c : j.cols) j.hist_total += req.cols[c].hist_host ? req.cols[c].hist_cap : 0;
@@ -985,7 +986,10 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
                 if ((s = persist_setup(PR_PREC_DF64, W, &op2)) != PR_OK) return s;
                 op = std::min(op, op2);
             }
-            if (op > 0 && total_ctas <= sms * op) loop = PR_LOOP_PERSISTENT;
+            // every CTA of a job holds the job's stopping rules in shared memory
+            bool taps_fit = true;
+            for (auto &j : jobs) taps_fit = taps_fit && j.ntaps <= kPersistTaps;
+            if (op > 0 && taps_fit && total_ctas <= sms * op) loop = PR_LOOP_PERSISTENT;
         }
     }
     // ---- phase 1 (or the only phase)

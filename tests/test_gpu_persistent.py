@@ -1,10 +1,11 @@
 """Persistent passes (PR_LOOP_PERSISTENT): Section 2's iteration run inside one
-cooperative launch, the CTAs waiting on a device counter for each pass's
-stopping decision. The passes do the same arithmetic in the same order as the
-CUDA-graph loop, so every result is bit-identical to it (and so to the oracle
-within the FP64 parity bound); solves whose passes are split fall back to the
-graph loop; a wait that never gets its decision ends the solve with
-PR_ETIMEOUT instead of hanging, and the context stays usable."""
+cooperative launch, every CTA of a job waiting on the job's device counter for
+the others and taking the job's stopping decisions itself. The passes do the
+same arithmetic in the same order as the CUDA-graph loop, so every result is
+bit-identical to it (and so to the oracle within the FP64 parity bound);
+solves whose passes are split fall back to the graph loop; a wait that never
+ends ends the solve with PR_ETIMEOUT instead of hanging, and the context stays
+usable."""
 import numpy as np
 import pytest
 
@@ -130,7 +131,7 @@ def test_pass_cap_ends_a_persistent_solve(B, orc, er, er_dev):
 
 
 def test_a_wait_that_runs_out_ends_the_solve(B, orc, er, er_dev):
-    """With the decisions held back (the test hook), every CTA's wait runs out
+    """With the arrivals held back (the test hook), every CTA's wait runs out
     after persist_wait_us of device time: the solve returns PR_ETIMEOUT, and
     the next solve on the same context is correct."""
     x = B.Instance(er_dev, 0.85, 1e-10, 1, 500)
