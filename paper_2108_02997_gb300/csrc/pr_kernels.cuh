@@ -60,6 +60,9 @@ template <> __device__ __forceinline__ df64 ld_cg_v<df64>(const df64 *p) {
 }
 
 // Arrival counters of persistent passes (gpu-scope acquire loads).
+__device__ __forceinline__ void red_release_gpu_add(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ uint32_t ld_acquire_gpu_u32(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -207,8 +210,9 @@ __device__ __forceinline__ void row_update(const int32_t *__restrict__ outdeg, c
 // the job) and the global decision (last job). Shared by both kernels.
 // The CTA's partials of the thread accumulators (L1, sum of squares, Linf,
 // dangling sum, sum of ranks per column, in a fixed order over warps) written
-// to dst[c * kPartials + k]; the writers fence them for the CTA that reads them.
-template <typename V, int W>
+// to dst[c * kPartials + k]; with kFence the writers fence them for the CTA
+// that reads them (otherwise the caller releases all the CTA's stores at once).
+template <typename V, int W, bool kFence = true>
 __device__ __forceinline__ void cta_partials(RowAcc<V> &acc, double *dst) {
     using N = Num<V>;
     using Acc = typename N::Acc;
@@ -233,7 +237,7 @@ __device__ __forceinline__ void cta_partials(RowAcc<V> &acc, double *dst) {
         Acc t = s_red[0][c][k];
         for (int w = 1; w < kWarps; w++) t = (k == 2) ? N::acc_max(t, s_red[w][c][k]) : N::acc_add(t, s_red[w][c][k]);
         dst[c * kPartials + k] = N::acc_to_double(t);
-        __threadfence();
+        if constexpr (kFence) __threadfence();
     }
     __syncthreads();
 }
@@ -567,13 +571,13 @@ __device__ __noinline__ bool persist_pass(JobDev &job, GlobalDev *glob, RowAcc<V
     // partials double-buffered by pass parity: a CTA may publish pass p + 1's
     // while another still reads pass p's
     double *part = job.cta_part + (size_t)(pass & 1) * cta_count * P;
-    cta_partials<V, W>(acc, part + (size_t)local * P);
+    cta_partials<V, W, false>(acc, part + (size_t)local * P);
     __shared__ int s_ok;
     if (tid == 0) {
-        // every store of this pass (iterates, contributions, partials) is
-        // visible at gpu scope before the arrival
-        __threadfence();
-        if (!*(volatile int32_t *)&glob->hold) atomicAdd(&job.arrive, 1u);
+        // a release at gpu scope after the CTA barrier: every store of this
+        // pass (iterates, contributions, partials) is visible to the CTA that
+        // sees the arrival
+        if (!*(volatile int32_t *)&glob->hold) red_release_gpu_add(&job.arrive, 1u);
         const uint32_t target = (uint32_t)(pass + 1) * (uint32_t)cta_count;
         int ok = 0;
         const unsigned long long t0 = global_ns();
@@ -589,7 +593,8 @@ __device__ __noinline__ bool persist_pass(JobDev &job, GlobalDev *glob, RowAcc<V
             }
             __nanosleep(32);
         }
-        __threadfence();
+        // the acquire load above orders this CTA's later reads (the barrier
+        // below extends it to the other threads)
         s_ok = ok;
     }
     __syncthreads();
