@@ -820,7 +820,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
             auto rows_tile_vec = [&](const Tile &T) {
                 if constexpr (!kStaged) {
                     const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
-    #pragma unroll
+#pragma unroll
                     for (int k = 0; k < kVecTileEdges / 32; k++) {
                         const int i = lane + 32 * k;
                         if (i < ne) v_src[i] = src[T.e0 + i];
@@ -835,18 +835,18 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                     const int g = 1 << T.glog;
                     const int es = lane & (g - 1);
                     const int rpp = 32 >> T.glog;
-    #pragma unroll 1
+#pragma unroll 1
                     for (int cg = 0; cg < NG; cg++) {
                         if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
-    #pragma unroll
+#pragma unroll
                         for (int k0 = 0; k0 < kVecTileEdges / 32; k0 += kVecGatherBatch) {
                             VV x[kVecGatherBatch];
-    #pragma unroll
+#pragma unroll
                             for (int k = 0; k < kVecGatherBatch; k++) {
                                 const int i = lane + 32 * (k0 + k);
                                 if (i < ne) x[k] = load_vec<V, CP>(c_all + (size_t)v_src[i] * W + cg * CP);
                             }
-    #pragma unroll
+#pragma unroll
                             for (int k = 0; k < kVecGatherBatch; k++) {
                                 const int i = lane + 32 * (k0 + k);
                                 if (i < ne) v_vals[i] = x[k];
@@ -857,17 +857,17 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                             const int r = rb + (lane >> T.glog);
                             const bool valid = r < nr;
                             EdgeSum<V> sum[CP];
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < CP; j++) sum[j].init();
                             if (valid) {
                                 const int lo = v_off[r], hi = v_off[r + 1];
                                 for (int e = lo + es; e < hi; e += g) {
                                     const VV y = v_vals[e];
-    #pragma unroll
+#pragma unroll
                                     for (int j = 0; j < CP; j++) sum[j].add(y.v[j]);
                                 }
                             }
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < CP; j++) {
                                 V sv = sum[j].get();
                                 for (int m = 1; m < g; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
@@ -894,14 +894,14 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                 if constexpr (kStaged) {
                     const int ne = T.e1 - T.e0, nr = T.r1 - T.r0;
                     int32_t u[PER];
-    #pragma unroll
+#pragma unroll
                     for (int k = 0; k < PER; k++) {
                         const int idx = lane + 32 * k;
                         u[k] = (cv.active && idx < ne * W) ? ld_idx(src + T.e0 + idx / W) : -1;
                     }
                     // row offsets relative to e0 in registers: lane l holds rows l, l + 32, ...
                     int32_t o[kOffRegs];
-    #pragma unroll
+#pragma unroll
                     for (int j = 0; j < kOffRegs; j++) {
                         const int i = lane + 32 * j;
                         o[j] = i <= nr ? off[T.r0 + i] - T.e0 : 0;
@@ -914,9 +914,9 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                     }
                     {
                         V x[PER];
-    #pragma unroll
+#pragma unroll
                         for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
-    #pragma unroll
+#pragma unroll
                         for (int k = 0; k < PER; k++)
                             if (u[k] >= 0) s_vals[warp][lane + 32 * k] = x[k];
                     }
@@ -931,7 +931,7 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                         // rows r and r + 1 lie in [rb, rb + 32]: registers j0 and j0 + 1 of their lanes
                         const int j0 = rb >> 5;
                         int32_t oa = o[0], ob = o[kOffRegs > 1 ? 1 : 0];
-    #pragma unroll
+#pragma unroll
                         for (int j = 1; j + 1 < kOffRegs; j++) {
                             if (j0 == j) {
                                 oa = o[j];
@@ -981,11 +981,11 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                     // several columns: per column group, lanes stride over the
                     // chunk's in-edges with vector loads, four in flight
                     const int ne = T.e1 - T.e0;
-    #pragma unroll 1
+#pragma unroll 1
                     for (int cg = 0; cg < NG; cg++) {
                         if (!((act_mask >> (cg * CP)) & ((1u << CP) - 1u))) continue;
                         EdgeSum<V> vs[CP];
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < CP; j++) vs[j].init();
                         const V *cb = c_all + cg * CP;
                         int i = lane;
@@ -994,17 +994,17 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                             const int32_t u2 = src[T.e0 + i + 64], u3 = src[T.e0 + i + 96];
                             const VV x0 = load_vec<V, CP>(cb + (size_t)u0 * W), x1 = load_vec<V, CP>(cb + (size_t)u1 * W);
                             const VV x2 = load_vec<V, CP>(cb + (size_t)u2 * W), x3 = load_vec<V, CP>(cb + (size_t)u3 * W);
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < CP; j++) {
                                 vs[j].add(x0.v[j]); vs[j].add(x1.v[j]); vs[j].add(x2.v[j]); vs[j].add(x3.v[j]);
                             }
                         }
                         for (; i < ne; i += 32) {
                             const VV x0 = load_vec<V, CP>(cb + (size_t)src[T.e0 + i] * W);
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < CP; j++) vs[j].add(x0.v[j]);
                         }
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < CP; j++) {
                             V sv = vs[j].get();
                             for (int m = 1; m < 32; m <<= 1) sv = N::add_pos(sv, N::shfl_xor(sv, m));
@@ -1017,25 +1017,25 @@ __global__ void __launch_bounds__(kBlock, W == 1 ? (Mode == kModeGather ? kGathe
                     // the next step's indices are requested while this step's
                     // gathers are in flight
                     int32_t u[PER];
-    #pragma unroll
+#pragma unroll
                     for (int k = 0; k < PER; k++) {
                         const int idx = lane + 32 * k;
                         u[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
                     }
                     for (int base = lane; base < nv; base += VT) {
                         V x[PER];
-    #pragma unroll
+#pragma unroll
                         for (int k = 0; k < PER; k++) x[k] = u[k] >= 0 ? gather1(u[k]) : N::zero();
                         int32_t un[PER];
-    #pragma unroll
+#pragma unroll
                         for (int k = 0; k < PER; k++) {
                             const int idx = base + VT + 32 * k;
                             un[k] = idx < nv ? ld_idx(src + T.e0 + idx) : -1;
                         }
-    #pragma unroll
+#pragma unroll
                         for (int k = 0; k < PER; k++)
                             if (u[k] >= 0) sum.add(x[k]);
-    #pragma unroll
+#pragma unroll
                         for (int k = 0; k < PER; k++) u[k] = un[k];
                     }
                 }
