@@ -558,8 +558,8 @@ __device__ __forceinline__ void persist_load(const JobDev &job, PersistState<W> 
 // End of persistent pass `pass` (counted from 0 in this launch); returns
 // whether the job runs another pass. The wait for the job's arrivals is
 // bounded: after wait_ns of the global timer the CTA records kErrWait and
-// stops, and every CTA that sees an error stops too, so that a broken
-// hand-over ends the launch with an error the host reports.
+// stops, and every CTA that sees an error stops too, so that a CTA that never
+// arrives ends the launch with an error the host reports.
 template <typename V, int W>
 __device__ __noinline__ bool persist_pass(JobDev &job, GlobalDev *glob, RowAcc<V> &acc, int local, PersistState<W> &ps,
                                           int32_t pass, unsigned long long wait_ns) {

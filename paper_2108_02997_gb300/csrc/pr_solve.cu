@@ -4,11 +4,13 @@
 // and its jobs: columns of one graph, at most 32, whose rank matrices are
 // N x W vertex-major (W = columns padded to a power of two), so that one read
 // of a row's in-edge indices serves W gathers (the planner in pr_plan.cu
-// chooses the jobs). All jobs of a request advance together, one pass per
-// iteration (a gather kernel and an update kernel, or one fused kernel for
-// small requests), inside a CUDA graph whose while-node repeats the pass until
-// the device reports that every column has stopped and every answer has been
-// copied out.
+// chooses the jobs). One pass per iteration: a gather kernel and an update
+// kernel, or one fused kernel for small requests. The passes run inside a CUDA
+// graph whose while-node repeats the pass until the device reports that every
+// column has stopped and every answer has been copied out; or, for fused
+// passes whose grid fits on the device, inside one cooperative launch in which
+// each job's CTAs loop until the job is done (persistent passes); or one
+// launch at a time from the host.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
