@@ -76,29 +76,47 @@ def test_default_loop_is_persistent_where_it_applies(B, er_dev):
     assert _loops(B) == {"graph": 1, "host": 0, "persistent": 0}
 
 
+@pytest.mark.parametrize("group", ["single", "pack"])
 @pytest.mark.parametrize("precision", ["df64", "fp64", "fp32", "mixed"])
-def test_sweep_equals_graph_loop(B, er_dev, precision):
-    """The 330-instance alpha x tau x norm sweep on shared trajectories (jobs
-    of several columns, stopping rules firing at different passes, answers
-    copied out while the other columns go on): persistent and graph loops give
-    the same bits; mixed precision runs both of its phases persistent."""
+def test_sweep_equals_graph_loop(B, er_dev, precision, group):
+    """The alpha x tau x norm sweep on shared trajectories (stopping rules
+    firing at different passes, answers copied out while the other columns go
+    on), as eleven one-column jobs or as one job of all eleven columns (seven
+    taus: 231 rules, within the 256 a job may hold): persistent and graph loops
+    with the same jobs give the same bits; mixed precision runs both of its
+    phases persistent."""
     alphas = [round(0.5 + 0.05 * i, 2) for i in range(11)]
-    taus = [10.0 ** -k for k in range(1, 11)] if precision != "fp32" else [10.0 ** -k for k in range(1, 6)]
+    nt = 10 if group == "single" else 7
+    taus = [10.0 ** -k for k in range(1, nt + 1)] if precision != "fp32" else [10.0 ** -k for k in range(1, 6)]
 
     def insts():
         return [B.Instance(er_dev, a, t, nm, 500) for a in alphas for t in taus for nm in (1, 2, 3)]
-    p, lp = _run(B, insts(), loop="persistent", precision=precision)
+    p, lp = _run(B, insts(), loop="persistent", precision=precision, group=group)
     assert lp["persistent"] == (2 if precision == "mixed" else 1) and lp["graph"] == 0, lp
-    g, lg = _run(B, insts(), loop="graph", precision=precision)
+    g, lg = _run(B, insts(), loop="graph", precision=precision, group=group)
     assert lg["persistent"] == 0 and lg["graph"] >= 1, lg
-    _same(p, g, f"sweep {precision}")
+    _same(p, g, f"sweep {precision} {group}")
     assert p["converged"].all()
+
+
+def test_planner_takes_one_column_jobs_for_small_persistent_sweeps(B, er_dev):
+    """With persistent passes, the planner gives each column of a small
+    graph a job of its own (PR_GROUP_AUTO): the same bits as explicit
+    one-column jobs."""
+    alphas = [round(0.5 + 0.05 * i, 2) for i in range(11)]
+
+    def insts():
+        return [B.Instance(er_dev, a, t, nm, 500) for a in alphas for t in (1e-4, 1e-10) for nm in (1, 3)]
+    a, la = _run(B, insts(), group="auto")
+    s, _ = _run(B, insts(), group="single", loop="persistent")
+    assert la["persistent"] == 1
+    _same(a, s, "auto vs single")
 
 
 @pytest.mark.parametrize("precision", ["df64", "fp32"])
 def test_many_graphs_and_adversarial_rows(B, gg, precision):
     """Several graphs in one launch (one job each, finishing at different
-    passes: dead jobs keep arriving while the others go on) with rows of every
+    passes: a finished job's CTAs leave while the others go on) with rows of every
     tile kind, including rows cut into chunks whose partial sums meet through
     counters that every pass resets; edgeless and single-vertex graphs."""
     from tests.test_gpu_parity import adversarial
@@ -109,9 +127,9 @@ def test_many_graphs_and_adversarial_rows(B, gg, precision):
 
         def insts():
             return [B.Instance(dg, a, tau, nm, 500) for dg in dgs for a in (0.6, 0.85, 0.99) for nm in (1, 3)]
-        p, lp = _run(B, insts(), loop="persistent", precision=precision, kernels="fused")
+        p, lp = _run(B, insts(), loop="persistent", precision=precision, kernels="fused", group="pack")
         assert lp["persistent"] >= 1 and lp["graph"] == 0, lp
-        g, _ = _run(B, insts(), loop="graph", precision=precision, kernels="fused")
+        g, _ = _run(B, insts(), loop="graph", precision=precision, kernels="fused", group="pack")
         _same(p, g, f"adversarial {precision}")
     finally:
         for dg in dgs:
