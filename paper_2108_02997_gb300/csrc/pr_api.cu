@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <unordered_set>
 #include <memory>
 #include <mutex>
 #include <set>
@@ -92,10 +93,15 @@ pr_status check_options(const pr_options &o) {
     return PR_OK;
 }
 
-pr_status check_instance(const pr_instance &in) {
-    if (!pr_graph_valid(in.g)) return pr_fail(PR_ESTATE, "not a live graph handle");
-    int dev = 0;
-    PR_CUDA(cudaGetDevice(&dev));
+// `seen`: graphs of this call already found live (each handle is looked up in
+// the registry once per call); `dev`: the current device, asked for once a
+// live handle has been seen (-1 before).
+pr_status check_instance(const pr_instance &in, int &dev, std::unordered_set<const pr_graph *> &seen) {
+    if (!seen.count(in.g)) {
+        if (!pr_graph_valid(in.g)) return pr_fail(PR_ESTATE, "not a live graph handle");
+        seen.insert(in.g);
+    }
+    if (dev < 0) PR_CUDA(cudaGetDevice(&dev));
     if (in.g->device != dev)
         return pr_fail(PR_EINVAL, "the graph lives on device " + std::to_string(in.g->device) + " but device " +
                                       std::to_string(dev) + " is current");
@@ -124,8 +130,10 @@ static pr_status pr_solve_batch_ex(pr_instance *inst, int32_t count, const pr_op
     pr_status first = PR_OK;
     std::string first_msg;
     std::vector<int> ok;
+    int dev = -1;
+    std::unordered_set<const pr_graph *> seen;
     for (int32_t i = 0; i < count; i++) {
-        s = check_instance(inst[i]);
+        s = check_instance(inst[i], dev, seen);
         if (s == PR_OK && opt.init == PR_INIT_USER && !inst[i].init_vec && !opt.init_vec)
             s = pr_fail(PR_EINVAL, "PR_INIT_USER needs init_vec");
         inst[i].status = s;

@@ -597,6 +597,7 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
         PR_CUDA(cudaMemcpyAsync(d_glob, &hg, sizeof(hg), cudaMemcpyHostToDevice, st));
         PR_CUDA(cudaLaunchKernel(kinit, grid, block, args, 0, st));
         PR_CUDA(cudaLaunchCooperativeKernel(persist_kernel_for(prec, W), grid, block, args, iter_smem, st));
+        PR_CUDA(cudaEventRecord(ev1, st));
         stats.launches += 2;
         GlobalDev back;
         std::memset(&back, 0, sizeof(back));
@@ -643,6 +644,7 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
             }
             if (!back.alive || back.error) break;
         }
+        PR_CUDA(cudaEventRecord(ev1, st));
         stats.passes += back.pass;
         if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
     } else {
@@ -687,6 +689,7 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
         PR_CUDA(cudaGraphAddKernelNode(&n_body, body, split ? &n_gather : nullptr, split ? 1 : 0, &kp));
         PR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
         PR_CUDA(cudaGraphLaunch(exec, st));
+        PR_CUDA(cudaEventRecord(ev1, st));
         GlobalDev back;
         std::memset(&back, 0, sizeof(back));
         PR_CUDA(cudaMemcpyAsync(&back, d_glob, sizeof(back), cudaMemcpyDeviceToHost, st));
@@ -695,7 +698,8 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
         stats.passes += back.pass;
         if (back.error) return pr_fail(PR_ETIMEOUT, "device loop did not finish within its pass cap");
     }
-    PR_CUDA(cudaEventRecord(ev1, st));
+    // ev1 was recorded right after the loop's last launch (the read-back
+    // synchronisation above has already waited for it)
     PR_CUDA(cudaEventSynchronize(ev1));
     float ms = 0.f;
     PR_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
