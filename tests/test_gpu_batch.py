@@ -330,6 +330,23 @@ def test_fp32_split_passes_beyond_the_hub_table(B, orc, gg):
         assert_bound_parity(orc, g, 0.85, 1e-5, 1, 500, x.out, x.iters, x.converged, star.ranks, what="fp32 split")
 
 
+def test_graph_creation_reuses_device_memory(B, gg):
+    """Creating and destroying the same graph many times holds the device's
+    free memory steady: a graph's arrays come from the graph pool and go back
+    to it, and creation's scratch goes back to the workspace pool (the
+    counting sort's block scratch once leaked a few MB per graph)."""
+    import torch
+    g = gg.rmat(16, 16, seed=5)
+    for _ in range(3):
+        B.Graph.from_csr(g).close()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(40):
+        B.Graph.from_csr(g).close()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (8 << 20)
+
+
 def test_workspace_pool_info_and_release(B, er):
     """The workspace pool lends memory only during calls and keeps it reserved
     between them; pr_workspace_release returns the reserve to the device."""
