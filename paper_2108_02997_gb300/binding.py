@@ -332,17 +332,28 @@ class PreparedBatch:
             arr["init_vec"][:n] = inits
         self.arr = arr
         self.n = n
+        self._opts = {}
+        self._arr_ptr = arr.ctypes.data
 
     def solve(self, *, precision="df64", init=None, loop="auto", stream=None, share=True, switch_tol=1e-6,
               mlp=None, check=True, group="auto", max_passes=0, kernels="auto", persist_wait_us=0):
         """One pr_solve_batch call over the prepared instances; returns its status."""
         if stream is None and self.outputs_on_device:
             stream = current_stream_ptr()
-        o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, self.outputs_on_device, mlp,
-                                 group, max_passes, kernels, persist_wait_us)
-        if self.has_init and o.init == PR_INIT_UNIFORM:
-            o.init = PR_INIT_USER
-        st = lib().pr_solve_batch(self.arr.ctypes.data, self.n, C.byref(o))
+        # the options of repeated calls with the same arguments are built once
+        key = None
+        if init is None or isinstance(init, str):
+            key = (precision, init, loop, stream, share, switch_tol, mlp.handle.value if mlp is not None else None,
+                   group, max_passes, kernels, persist_wait_us)
+        o = self._opts.get(key) if key is not None else None
+        if o is None:
+            o, keep2 = _make_options(precision, init, loop, stream, share, switch_tol, self.outputs_on_device, mlp,
+                                     group, max_passes, kernels, persist_wait_us)
+            if self.has_init and o.init == PR_INIT_UNIFORM:
+                o.init = PR_INIT_USER
+            if key is not None:
+                self._opts[key] = o
+        st = lib().pr_solve_batch(self._arr_ptr, self.n, C.byref(o))
         if check:
             _check(st, "pr_solve_batch")
         return st
