@@ -171,3 +171,21 @@ def test_header_describes_the_workspace_pool_and_its_release():
     assert "cudaMalloc with cudaMalloc" not in conv and "releases it\n *     before returning" not in conv
     noalloc = text[text.index("pr_solve_noalloc —"):text.index("pr_status pr_solve_noalloc(")]
     assert "captured" in noalloc and "40 MiB" in noalloc and "device memory of that device" in noalloc
+
+
+def test_loop_modes_and_their_options():
+    """The binding's loop names map to the header's pr_loop values, the
+    persistent wait bound reaches pr_options, and an unknown loop name is
+    refused before any library call."""
+    from paper_2108_02997_gb300 import binding
+    text = (ROOT / "include" / "pagerank.h").read_text()
+    for name, value in (("graph", 0), ("host", 1), ("persistent", 2), ("auto", 3)):
+        assert binding.LOOPS[name] == value
+        assert f"PR_LOOP_{name.upper()} = {value}" in text
+        o, _ = binding._make_options(loop=name, persist_wait_us=1234)
+        assert o.loop == value and o.persist_wait_us == 1234
+    with pytest.raises(ValueError):
+        binding._make_options(loop="spin")
+    # the header states the bound of the waits and the rule-count limit
+    persist = text[text.index("PR_LOOP_PERSISTENT = 2"):text.index("PR_LOOP_AUTO = 3")]
+    assert "2 s" in persist and "256 stopping rules" in persist
