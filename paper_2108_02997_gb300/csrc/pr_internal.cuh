@@ -122,8 +122,23 @@ constexpr int kHubBlock = 1024;
 constexpr int kHubWarps = kHubBlock / 32;
 constexpr int kHubTile = PR_HUB_TILE_VALUES;
 constexpr int kHubBytes = PR_HUB_BYTES;
+// Jobs of two and four columns keep a smaller hub table: their gathers read a
+// whole vector per source, and the L1 that a smaller table leaves serves them
+// better (measured on GB300, df64, R-MAT s24: two columns 1249 -> 1096 us and
+// four columns 2036 -> 1826 us per pass from 96 KB to 32 KB of hubs).
+#ifndef PR_HUB_BYTES_VEC
+#define PR_HUB_BYTES_VEC (32 * 1024)
+#endif
+__host__ __device__ constexpr int hub_bytes(int W) { return W == 1 ? PR_HUB_BYTES : PR_HUB_BYTES_VEC; }
 constexpr int kHubChunkPer = PR_HUB_CHUNK_PER;   // chunk tiles: gathers in flight per lane
 static_assert(kHubTile % 32 == 0 && kHubTile <= 256, "hub tiles hold 32..256 values");
+// Gathers of 32 bytes (four df64 or FP64 columns of a source): one 256-bit
+// load per lane (1) or two 128-bit loads (0). Measured on GB300, df64, four
+// columns: R-MAT s22 554 -> 484 us, s24 2165 -> 2036 us per gather pass.
+#ifndef PR_GATHER_V8
+#define PR_GATHER_V8 1
+#endif
+constexpr bool kGatherV8 = PR_GATHER_V8 != 0;
 #ifndef PR_HUB_TILE_VECTORS
 #define PR_HUB_TILE_VECTORS 128
 #endif

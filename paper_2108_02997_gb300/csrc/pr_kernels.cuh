@@ -1216,11 +1216,20 @@ __device__ __forceinline__ VecV<V, W> ld_gather_vec(const V *p) {
                       sizeof(VecV<V, W>) == 32, "vector size");
     VecV<V, W> r;
     if constexpr (sizeof(VecV<V, W>) == 32) {
-        // one 32-byte sector: two 16-byte loads of the same sector
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-        memcpy(&r, &a, 16);
-        memcpy(reinterpret_cast<unsigned char *>(&r) + 16, &b, 16);
+        if constexpr (kGatherV8) {
+            // one 32-byte sector in one 256-bit load
+            uint32_t w[8];
+            asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                : "l"(p));
+            memcpy(&r, w, 32);
+        } else {
+            // one 32-byte sector: two 16-byte loads of the same sector
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+            memcpy(&r, &a, 16);
+            memcpy(reinterpret_cast<unsigned char *>(&r) + 16, &b, 16);
+        }
     } else if constexpr (sizeof(VecV<V, W>) == 16) {
         const float4 f = __ldg(reinterpret_cast<const float4 *>(p));
         memcpy(&r, &f, 16);
@@ -1264,7 +1273,7 @@ __global__ void __launch_bounds__(kHubBlock, 1) pr_gather_hub_kernel(JobDev *job
     uint32_t *chunk_cnt = job.chunk_cnt;
     const int ntiles = job.ntiles;
     // at most what the launch's shared memory holds for this vector type
-    const int hub_n = min(job.hub_n, kHubBytes / (int)sizeof(VV));
+    const int hub_n = min(job.hub_n, hub_bytes(W) / (int)sizeof(VV));
     extern __shared__ __align__(16) unsigned char pr_hub_smem[];
     VV *s_vals = reinterpret_cast<VV *>(pr_hub_smem) + warp * TV;   // this warp's staged vectors
     VV *s_hub = reinterpret_cast<VV *>(pr_hub_smem) + kHubWarps * TV;

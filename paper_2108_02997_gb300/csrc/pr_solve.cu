@@ -432,10 +432,10 @@ size_t pr_tile_smem_bytes(int prec, int W) {
 }
 // The gather-only kernel's: no previous ranks or out-degrees staged; the hub
 // gather kernel's: every warp's staged vectors, then the hub table (at most
-// kHubBytes of vectors).
+// hub_bytes(W) of vectors).
 size_t gather_smem_bytes(int prec, int W) {
     const int vbytes = prec == PR_PREC_FP32 ? 4 : 8;
-    if (hub_gather(W)) return (size_t)kHubWarps * hub_tile_edges(W) * W * vbytes + (size_t)kHubBytes;
+    if (hub_gather(W)) return (size_t)kHubWarps * hub_tile_edges(W) * W * vbytes + (size_t)hub_bytes(W);
     if (W == 1) return 0;
     return (size_t)kWarps * vec_warp_bytes(vbytes, W, true);
 }
