@@ -39,6 +39,15 @@ constexpr int kPartials = 5;         // L1, sum of squares, Linf, dangling sum, 
 #define PR_UPDATE_MIN_BLOCKS 3
 #endif
 // One-column update kernel: pairs of rows (vector loads) in flight per thread.
+// One column, split passes: the update kernel streams its rows' inputs into
+// shared memory with 1-D bulk copies (1), or loads them per thread (0).
+#ifndef PR_UPDATE_BULK
+#define PR_UPDATE_BULK 1
+#endif
+constexpr bool kUpdateBulk = PR_UPDATE_BULK != 0;
+constexpr int kUpdRows = 1024;     // rows per bulk-copied tile
+constexpr int kUpdStages = 3;      // tiles in flight per CTA
+__host__ __device__ constexpr int upd_stage_bytes(int vbytes) { return kUpdRows * (2 * vbytes + 4); }
 #ifndef PR_UPDATE_PAIRS
 #define PR_UPDATE_PAIRS 2
 #endif

@@ -1197,6 +1197,133 @@ __global__ void __launch_bounds__(kBlock, kUpdateMinBlocks) pr_update_kernel(Job
     finish_pass<V, W>(jobs, job, glob, acc, local, kPassIterate);
 }
 
+// ---------------------------------------------------------------- the update kernel, bulk-copy form
+// The one-column update of a split pass (pr_update_kernel<V, 1>'s work) with
+// the rows' inputs (row sums, previous ranks, out-degrees) streamed into shared
+// memory by 1-D bulk copies: each CTA takes tiles of kUpdRows consecutive rows
+// (tile t = local, local + CTAs, ...), keeps kUpdStages tiles in flight behind
+// one mbarrier each, and its threads update the rows of a tile from shared
+// memory (thread t: rows t, t + 256, ...), so that the bytes in flight per SM do
+// not depend on the threads' registers. A copy starts at a multiple of
+// kUpdRows rows (16-byte aligned) and covers the tile's rows rounded up to four
+// (the arrays are padded). Every wait is bounded: a wait that runs out records
+// kErrWait, waits (bounded) for the CTA's copies still in flight and ends the
+// CTA's row work.
+constexpr unsigned int kUpdSpinLimit = 1u << 22;   // mbarrier polls before a wait is abandoned
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase) {
+    for (unsigned int spin = 0; spin < kUpdSpinLimit; spin++)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_to_shared(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kBlock, kUpdateMinBlocks) pr_update_bulk_kernel(JobDev *jobs, GlobalDev *glob,
+                                                                                   const int32_t *cta_job) {
+    using N = Num<V>;
+    constexpr int kSB = upd_stage_bytes((int)sizeof(V));
+    const int tid = threadIdx.x;
+    JobDev &job = jobs[cta_job[blockIdx.x]];
+    const int local = blockIdx.x - job.cta_begin;
+    if (blockIdx.x == 0 && tid == 0) {
+        unsigned int nb = atomicAdd(&glob->body_count, 1u) + 1u;
+        if (nb > (unsigned int)glob->pass_cap + 8u) {
+            glob->error = kErrLoopGuard;
+            if (glob->cond) cudaGraphSetConditional((cudaGraphConditionalHandle)glob->cond, 0u);
+        }
+    }
+    const ColView<V> cv = col_view<V>(job, 0);
+    RowAcc<V> acc;
+    acc.init();
+    extern __shared__ __align__(128) unsigned char upd_smem[];
+    __shared__ __align__(8) uint64_t s_bar[kUpdStages];
+    const bool work = job.alive && !*(volatile int32_t *)&glob->error;
+    if (work && cv.has && (cv.active || cv.copy_dst)) {
+        const int32_t n = job.n;
+        const int cta_count = job.cta_count;
+        const int ntiles = (int)(((int64_t)n + kUpdRows - 1) / kUpdRows);
+        const int my_tiles = local < ntiles ? (ntiles - 1 - local) / cta_count + 1 : 0;
+        const V *rowsum = reinterpret_cast<const V *>(job.rowsum);
+        const V *r_prev = cv.r_prev;
+        const int32_t *outdeg = job.outdeg;
+        const int32_t *__restrict__ perm = job.perm;
+        if (tid == 0) {
+            for (int st = 0; st < kUpdStages; st++) mbar_init(&s_bar[st], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        // thread 0: the k-th tile of this CTA into stage k mod kUpdStages
+        auto issue = [&](int k) {
+            const int32_t r0 = (local + k * cta_count) * kUpdRows;
+            const int rows = min(kUpdRows, n - r0);
+            const uint32_t rows4 = (uint32_t)((rows + 3) & ~3);
+            unsigned char *stg = upd_smem + (size_t)(k % kUpdStages) * kSB;
+            uint64_t *bar = &s_bar[k % kUpdStages];
+            // the stage's previous contents were read by the threads (generic
+            // proxy) before this copy (async proxy) overwrites them
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, rows4 * (2u * (uint32_t)sizeof(V) + 4u));
+            bulk_to_shared(stg, rowsum + r0, rows4 * (uint32_t)sizeof(V), bar);
+            bulk_to_shared(stg + kUpdRows * sizeof(V), r_prev + r0, rows4 * (uint32_t)sizeof(V), bar);
+            bulk_to_shared(stg + 2 * kUpdRows * sizeof(V), outdeg + r0, rows4 * 4u, bar);
+        };
+        if (tid == 0)
+            for (int k = 0; k < min(kUpdStages, my_tiles); k++) issue(k);
+        for (int k = 0; k < my_tiles; k++) {
+            const int sidx = k % kUpdStages;
+            const uint32_t phase = (uint32_t)(k / kUpdStages) & 1u;
+            const bool ok = mbar_wait_bounded(&s_bar[sidx], phase);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicCAS(&glob->error, kErrNone, kErrWait);
+                    // the copies issued and not yet consumed may still be in flight
+                    for (int k2 = k; k2 < min(k + kUpdStages, my_tiles); k2++)
+                        mbar_wait_bounded(&s_bar[k2 % kUpdStages], (uint32_t)(k2 / kUpdStages) & 1u);
+                }
+                __syncthreads();
+                break;
+            }
+            const unsigned char *stg = upd_smem + (size_t)sidx * kSB;
+            const V *s_rs = reinterpret_cast<const V *>(stg);
+            const V *s_pv = reinterpret_cast<const V *>(stg + kUpdRows * sizeof(V));
+            const int32_t *s_od = reinterpret_cast<const int32_t *>(stg + 2 * kUpdRows * sizeof(V));
+            const int32_t r0 = (local + k * cta_count) * kUpdRows;
+            const int rows = min(kUpdRows, n - r0);
+            for (int i = tid; i < rows; i += kBlock) {
+                const V sv = cv.active ? s_rs[i] : N::zero();
+                row_update_pd<V, 1>(perm, cv, acc, r0 + i, 0, sv, s_pv[i], s_od[i]);
+            }
+            __syncthreads();   // every thread is done with this stage
+            if (tid == 0 && k + kUpdStages < my_tiles) issue(k + kUpdStages);
+        }
+    }
+    finish_pass<V, 1>(jobs, job, glob, acc, local, kPassIterate);
+}
+
 // ---------------------------------------------------------------- the hub gather kernel (split passes)
 // The gather half of a pass (row sums only) for jobs of W columns whose W
 // values of a vertex fill at most one 32-byte L2 sector (one, two or four

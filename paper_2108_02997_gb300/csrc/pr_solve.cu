@@ -266,7 +266,21 @@ void *gather_kernel_for(int prec, int W) {
         default: return gather_ptr<df64>(W);
     }
 }
+// One column: the bulk-copy form of the update kernel (kUpdateBulk), with
+// kUpdStages tiles of dynamic shared memory.
+bool update_bulk(int W) { return kUpdateBulk && W == 1; }
+size_t update_smem_bytes(int prec, int W) {
+    if (!update_bulk(W)) return 0;
+    return (size_t)kUpdStages * upd_stage_bytes(prec == PR_PREC_FP32 ? 4 : 8);
+}
 void *update_kernel_for(int prec, int W) {
+    if (update_bulk(W)) {
+        switch (prec) {
+            case PR_PREC_FP64: return (void *)pr_update_bulk_kernel<double>;
+            case PR_PREC_FP32: return (void *)pr_update_bulk_kernel<float>;
+            default: return (void *)pr_update_bulk_kernel<df64>;
+        }
+    }
     switch (prec) {
         case PR_PREC_FP64: return update_ptr<double>(W);
         case PR_PREC_FP32: return update_ptr<float>(W);
@@ -343,8 +357,10 @@ pr_status setup_split(int prec, int W, int *occ_gather, int *occ_update) {
         PR_CUDA(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         pr_status s = set_carveout(kg, smem, W == 1 || hub_gather(W), gather_block(W));
         if (s != PR_OK) return s;
-        const std::pair<int, int> occ{resident_ctas(kg, smem, gather_block(W)),
-                                      resident_ctas(update_kernel_for(prec, W), 0)};
+        void *ku = update_kernel_for(prec, W);
+        const size_t usmem = update_smem_bytes(prec, W);
+        if (usmem > 0) PR_CUDA(cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem));
+        const std::pair<int, int> occ{resident_ctas(kg, smem, gather_block(W)), resident_ctas(ku, usmem)};
         it = done.emplace(key, occ).first;
     }
     *occ_gather = it->second.first;
@@ -585,7 +601,7 @@ pr_status run_phase(int prec, int W, bool split, std::vector<HostJob> &jobs, Are
     void *args[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_ctajob};
     void *gargs[] = {(void *)&d_jobs, (void *)&d_glob, (void *)&d_gctajob};
     dim3 grid(total_ctas), ggrid(split ? total_gctas : 1), block(kBlock), gblock(gather_block(W));
-    const size_t iter_smem = split ? 0 : smem, gather_smem = split ? gather_smem_bytes(prec, W) : 0;
+    const size_t iter_smem = split ? update_smem_bytes(prec, W) : smem, gather_smem = split ? gather_smem_bytes(prec, W) : 0;
     PR_CUDA(cudaEventRecord(ev0, st));
     if (loop >= PR_LOOP_GRAPH && loop <= PR_LOOP_PERSISTENT) stats.loop_phases[loop]++;
     if (loop == PR_LOOP_PERSISTENT) {
@@ -813,7 +829,9 @@ pr_status pr_run_solve(SolveRequest &req, std::vector<std::vector<Tap>> &tap_out
         int want = (int)std::lround(budget * share);
         if (split) {
             // update kernel: rows grid-stride
-            j.cta_count = std::max(1, std::min<int>(want, (int)(((int64_t)j.g->n * W + kBlock - 1) / kBlock)));
+            // update kernel: rows grid-stride (the bulk-copy form: tiles of kUpdRows rows)
+            const int64_t unit = update_bulk(W) ? kUpdRows : kBlock;
+            j.cta_count = std::max(1, std::min<int>(want, (int)(((int64_t)j.g->n * W + unit - 1) / unit)));
             int gwant = (int)std::lround(gbudget * share);
             const int gcap = hub ? (int)std::max<int64_t>(1, ((int64_t)j.tt->ntiles + kHubWarps - 1) / kHubWarps)
                                  : tile_ctas(j.tt->ntiles);
